@@ -1,0 +1,202 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(no GPU).  Each test checks the oracle against something other than itself:
+the paper's worked examples, a brute-force rank computation, 1D interval
+counting, Euler characteristics, cell counts, symmetries and finite
+differences."""
+import itertools
+
+import numpy as np
+import pytest
+
+from tests.golden.golden_io import read_image_and_bars, read_pairs
+
+
+def nonzero(p):
+    keep = p["birth"] != p["death"]
+    return sorted((int(d), float(b), float(e)) for d, b, e in zip(p["dim"][keep], p["birth"][keep], p["death"][keep]))
+
+
+def cellset(p):
+    return set((int(d), int(b), int(e)) for d, b, e in zip(p["dim"], p["birth_L"], p["death_L"]))
+
+
+def test_ttk_example(oracle_mod):
+    # Rem. 3.2: the 3x3 image with 9 in the centre has the 1-cycle [0, 9)
+    img, bars = read_image_and_bars("ttk_3x3.txt")
+    p = oracle_mod.persistence(img)
+    assert nonzero(p) == sorted((int(b[0]), b[1], b[2]) for b in bars)
+    # hand count including zero-length pairs: 7 (0,0) + 1 (9,9) in H0, 3 (9,9) in H1
+    z = p[p["birth"] == p["death"]]
+    assert sorted((int(a), float(b)) for a, b in zip(z["dim"], z["birth"])) == \
+        [(0, 0.0)] * 7 + [(0, 9.0)] + [(1, 9.0)] * 3
+
+
+def test_fig2_h0(oracle_mod):
+    img, bars = read_image_and_bars("fig2_h0.txt")
+    p = oracle_mod.persistence(img)
+    assert [b for b in nonzero(p) if b[0] == 0] == sorted((0, b[0], b[1]) for b in bars)
+
+
+def _random_images(rng, count, shapes, levels=(1, 2, 3, 5)):
+    out = []
+    for _ in range(count):
+        sh = shapes[rng.integers(len(shapes))]
+        lev = levels[rng.integers(len(levels))]
+        if rng.random() < 0.25:
+            out.append(rng.random(sh).astype(np.float32))
+        else:
+            out.append(rng.integers(0, lev, sh).astype(np.float32))
+    return out
+
+
+@pytest.mark.parametrize("kind", ["1d", "2d", "3d"])
+def test_cell_pairs_equal_rank_function(oracle_mod, kind):
+    # the pairing of a cell-by-cell filtration is fixed by its rank function
+    rng = np.random.default_rng({"1d": 11, "2d": 12, "3d": 13}[kind])
+    shapes = {"1d": [(1,), (2,), (5,), (9,)],
+              "2d": [(1, 1), (1, 4), (4, 1), (2, 2), (3, 3), (2, 4), (3, 4)],
+              "3d": [(2, 2, 2), (1, 2, 3), (2, 1, 3), (2, 3, 2), (2, 2, 3)]}[kind]
+    for img in _random_images(rng, {"1d": 40, "2d": 40, "3d": 12}[kind], shapes):
+        assert cellset(oracle_mod.persistence(img)) == oracle_mod.brute_force_pairs(img), img.tolist()
+
+
+def test_diagram_equals_rank_diagram_3x3(oracle_mod):
+    # a deterministic sample of the 3^9 three-level 3x3 images
+    rng = np.random.default_rng(3)
+    codes = rng.choice(3 ** 9, size=300, replace=False)
+    for c in codes:
+        vals = [(int(c) // 3 ** k) % 3 for k in range(9)]
+        img = np.array(vals, np.float32).reshape(3, 3)
+        assert nonzero(oracle_mod.persistence(img)) == oracle_mod.brute_force_rank_diagram(img)
+
+
+def test_h0_1d_interval_counting(oracle_mod):
+    rng = np.random.default_rng(4)
+    for n in [1, 2, 3, 7, 20, 41]:
+        for lev in [2, 4, 100]:
+            seq = rng.integers(0, lev, n).astype(np.float32)
+            got = [(b, e) for d, b, e in nonzero(oracle_mod.persistence(seq)) if d == 0]
+            assert got == oracle_mod.h0_1d_brute_force(seq)
+
+
+def test_sine_example_golden(oracle_mod):
+    # Sec. 4, Ex. 4.4 input; golden written by tests/golden/make_golden.py
+    x = np.linspace(0, 4 * np.pi, 100)
+    seq = (np.sin(x) + 0.1 * x).astype(np.float32)
+    got = nonzero(oracle_mod.persistence(seq))
+    exp = sorted((d, b, e) for d, b, e, _, _ in read_pairs("sine100_pairs.txt"))
+    assert [(d, np.float32(b), np.float32(e)) for d, b, e in got] == \
+        [(d, np.float32(b), np.float32(e)) for d, b, e in exp]
+    # and it agrees with interval counting
+    assert [(b, e) for d, b, e in got] == oracle_mod.h0_1d_brute_force(seq)
+
+
+@pytest.mark.parametrize("shape", [(7,), (5, 6), (3, 4, 5)])
+def test_euler_characteristic_every_threshold(oracle_mod, shape):
+    rng = np.random.default_rng(5)
+    for lev in [3, 50]:
+        img = rng.integers(0, lev, shape).astype(np.float32)
+        p = oracle_mod.persistence(img)
+        for t in sorted(set(img.reshape(-1).tolist())) + [1e9]:
+            alive = (p["birth"] <= t) & (t < p["death"])
+            chi_bars = int(sum((-1) ** int(d) for d in p["dim"][alive]))
+            assert chi_bars == oracle_mod.euler_characteristic(img, t)
+
+
+@pytest.mark.parametrize("shape", [(13,), (6, 9), (4, 5, 6), (1, 5, 6), (3, 1, 4)])
+def test_totals(oracle_mod, shape):
+    rng = np.random.default_rng(6)
+    img = rng.integers(0, 4, shape).astype(np.float32)
+    p = oracle_mod.persistence(img)
+    nz, ny, nx = (1, 1) + shape if len(shape) == 1 else ((1,) + shape if len(shape) == 2 else shape)
+    V = nx * ny * nz
+    E = (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1)
+    F = (nx - 1) * (ny - 1) * nz + (nx - 1) * ny * (nz - 1) + nx * (ny - 1) * (nz - 1)
+    C = (nx - 1) * (ny - 1) * (nz - 1)
+    cnt = [int((p["dim"] == d).sum()) for d in range(3)]
+    ess = p[~np.isfinite(p["death"])]
+    assert len(ess) == 1 and ess["dim"][0] == 0  # beta_0 = 1, higher Betti numbers 0
+    assert cnt[0] == V  # V - 1 finite + 1 essential
+    assert cnt[1] == E - V + 1
+    assert cnt[2] == C
+    assert E - V + 1 == F - C  # chi = 1
+
+
+def test_twist_does_not_change_pairs(oracle_mod):
+    rng = np.random.default_rng(7)
+    for sh in [(6, 7), (3, 4, 5), (30,)]:
+        img = rng.integers(0, 3, sh).astype(np.float32)
+        assert cellset(oracle_mod.persistence(img, twist=True)) == cellset(oracle_mod.persistence(img, twist=False))
+
+
+def test_embedding_and_symmetries(oracle_mod):
+    rng = np.random.default_rng(8)
+    img2 = rng.integers(0, 5, (6, 7)).astype(np.float32)
+    # (1, Ny, Nx) volume = the 2D image, cell for cell (Sec. 2: 2D is the slice k = 0)
+    assert cellset(oracle_mod.persistence(img2[None])) == cellset(oracle_mod.persistence(img2))
+    seq = img2[0]
+    assert cellset(oracle_mod.persistence(seq[None, None])) == cellset(oracle_mod.persistence(seq))
+    assert cellset(oracle_mod.persistence(seq[None])) == cellset(oracle_mod.persistence(seq))
+    base = nonzero(oracle_mod.persistence(img2))
+    for t in [img2[::-1], img2[:, ::-1], img2.T, img2[::-1, ::-1].T]:
+        assert nonzero(oracle_mod.persistence(np.ascontiguousarray(t))) == base
+    vol = rng.integers(0, 4, (3, 4, 5)).astype(np.float32)
+    vb = nonzero(oracle_mod.persistence(vol))
+    for t in [vol[::-1], np.transpose(vol, (2, 0, 1)), np.transpose(vol, (1, 2, 0))[:, ::-1]]:
+        assert nonzero(oracle_mod.persistence(np.ascontiguousarray(t))) == vb
+    # scaling by 2 scales every bar exactly
+    sc = nonzero(oracle_mod.persistence(img2 * 2))
+    assert sc == [(d, 2 * b, 2 * e) for d, b, e in base]
+
+
+def test_nan_and_negative_zero(oracle_mod):
+    img = np.zeros((3, 3), np.float32)
+    img[1, 1] = np.nan
+    with pytest.raises(ValueError):
+        oracle_mod.persistence(img)
+    a = np.array([[0.0, 1.0], [2.0, 0.0]], np.float32)
+    b = a.copy()
+    b[0, 0] = -0.0
+    assert cellset(oracle_mod.persistence(a)) == cellset(oracle_mod.persistence(b))
+
+
+def test_plus_infinity_is_an_ordinary_value(oracle_mod):
+    # Sec. 2: outside a non-rectangular domain the image is extended by a huge value
+    img = np.array([[0, 1, np.inf], [2, np.inf, 0.5], [np.inf, 3, 0]], np.float32)
+    p = oracle_mod.persistence(img)
+    assert cellset(p) == oracle_mod.brute_force_pairs(img)
+
+
+def _loss(oracle_mod, img):
+    p = oracle_mod.persistence(img)
+    fin = np.isfinite(p["death"])
+    d = p["death"][fin].astype(np.float64) - p["birth"][fin].astype(np.float64)
+    return float((d * d).sum())
+
+
+@pytest.mark.parametrize("shape", [(12,), (5, 6), (3, 3, 4)])
+def test_gradient_rule_matches_finite_differences(oracle_mod, shape):
+    # L = sum (d - b)^2; on a tie-free image every bar end is one pixel's value
+    rng = np.random.default_rng(9)
+    img = rng.permutation(np.prod(shape)).reshape(shape).astype(np.float32)
+    p = oracle_mod.persistence(img)
+    fin = np.isfinite(p["death"])
+    life = np.where(fin, p["death"].astype(np.float64) - p["birth"].astype(np.float64), 0.0)
+    g = oracle_mod.gradient(img, p, -2 * life, 2 * life)
+    h = 0.25  # values are integers: +-0.25 keeps the order
+    for idx in itertools.islice(np.ndindex(*shape), 0, None, 3):
+        up, dn = img.copy(), img.copy()
+        up[idx] += h
+        dn[idx] -= h
+        fd = (_loss(oracle_mod, up) - _loss(oracle_mod, dn)) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-9 * max(1.0, abs(fd)), (idx, fd, g[idx])
+
+
+def test_uniform64_golden(oracle_mod):
+    from paper_2005_12692_gb300 import synth
+    p = oracle_mod.persistence(synth.uniform64())
+    got = sorted((int(a), float(b), float(c), int(d), int(e)) for a, b, c, d, e in
+                 zip(p["dim"], p["birth"], p["death"], p["birth_L"], p["death_L"]) if b != c)
+    exp = sorted((d, float(np.float32(b)), float(np.float32(e)), bl, dl) for d, b, e, bl, dl in
+                 read_pairs("uniform64_pairs.txt"))
+    assert got == exp
