@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 persistent-homology path.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Workloads (seeded synthetic fields shaped like the paper's images/volumes):
+  grf1024          one 2D 1024x1024 GRF (sigma 4), H0+H1        -- default; metric cells/s
+  uniform64        one 2D 64x64 U[0,1) image, H0+H1             -- metric cells/s
+  grf256cube_salt  one 3D 256^3 GRF (sigma 3) + 1% salt, H0-H2  -- metric cells/s
+  grf512cube       one 3D 512^3 GRF (sigma 4), H0-H2            -- metric cells/s
+  batch4096        4096 2D GRFs of sides 28..256, batched forward + backward of
+                   sum_H1 lifetime^2                            -- metric images/s
+
+A step is one pass of the whole path over one input resident in HBM.  Between
+timed steps a 256 MiB buffer is written to flush L2 (inputs of the 2D
+workloads fit in L2).  Each step is bracketed by CUDA events on the stream the
+library launches on; the JSON line reports the mean.  ``--impl reference``
+times the CPU oracle on the host cores instead (a bounded sample of the same
+workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "uniform64": dict(kind="single", shape=(64, 64), maxdim=1),
+    "grf1024": dict(kind="single", shape=(1024, 1024), maxdim=1),
+    "grf256cube_salt": dict(kind="single", shape=(256, 256, 256), maxdim=2),
+    "grf512cube": dict(kind="single", shape=(512, 512, 512), maxdim=2),
+    "batch4096": dict(kind="batch", n=4096, maxdim=1),
+}
+
+
+def make_input(name):
+    from paper_2005_12692_gb300 import synth
+    if name == "uniform64":
+        return synth.uniform64()
+    if name == "grf1024":
+        return synth.grf1024()
+    if name == "grf256cube_salt":
+        return synth.grf256cube_salt()
+    if name == "grf512cube":
+        return synth.grf512cube()
+    if name == "batch4096":
+        return synth.batch_images(4096)
+    raise ValueError(name)
+
+
+def num_cells(shape):
+    n = 1
+    for s in shape:
+        n *= 2 * int(s) - 1
+    return n
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# stage profile read from the library
+# ---------------------------------------------------------------------------
+def read_profile(cr):
+    import ctypes
+    L = cr.lib()
+    out = {}
+    name = ctypes.c_char_p()
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    by = ctypes.c_double()
+    for s in range(64):
+        if L.cr_profile_read(s, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(by)) != 0:
+            break
+        if cnt.value:
+            out[name.value.decode()] = {"ms": ms.value, "launches": cnt.value, "bytes": by.value}
+    return out
+
+
+SINGLE_KERNEL_STAGES = ("h0_stencil", "jump", "h0_cross", "dual_stencil", "dual_cross", "h1_scan", "h1_reduce")
+
+
+def roofline_from(stages, peaks, sustained=True):
+    best = None
+    for k in SINGLE_KERNEL_STAGES:
+        s = stages.get(k)
+        if s and (best is None or s["ms"] > stages[best]["ms"]):
+            best = k
+    if best is None:
+        return None
+    s = stages[best]
+    per_launch_s = s["ms"] / 1e3 / s["launches"]
+    per_launch_bytes = s["bytes"] / s["launches"]
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    peak = peaks.get("hbm_gbs")
+    src = "measured"
+    if not peak:
+        peak, src = 6800.0, "fallback"
+    return {"kernel": best, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": src, "traffic": None,
+            "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_s * 1e3}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(name, data):
+    """A bounded sample of the workload for the CPU oracle: (array(s), cells, description)."""
+    from paper_2005_12692_gb300 import synth
+    if name in ("uniform64", "grf1024"):
+        return [data], num_cells(data.shape), "the full %s image" % "x".join(map(str, data.shape))
+    if name == "grf256cube_salt":
+        sub = np.ascontiguousarray(data[:48, :48, :48])
+        return [sub], num_cells(sub.shape), "a 48^3 corner crop of the 256^3 volume"
+    if name == "grf512cube":
+        sub = np.ascontiguousarray(data[:48, :48, :48])
+        return [sub], num_cells(sub.shape), "a 48^3 corner crop of the 512^3 volume"
+    if name == "batch4096":
+        imgs = data[:16]
+        return imgs, len(imgs), "the first 16 of the 4096 images (forward only), scaled to images/s"
+    raise ValueError(name)
+
+
+def run_oracle(name, data):
+    import oracle
+    oracle.build()
+    arrs, units, desc = oracle_sample(name, data)
+    t0 = time.perf_counter()
+    for a in arrs:
+        oracle.persistence(a)
+    dt = time.perf_counter() - t0
+    return units / dt, dt, desc
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="grf1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    W = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    metric = "images/s batched fwd+bwd" if W["kind"] == "batch" else "cells/s full PH"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        data = make_input(args.workload)
+        import oracle  # noqa: F401
+        cores = 1
+        vals = []
+        for i in range(args.warmup + args.steps):
+            v, dt, desc = run_oracle(args.workload, data)
+            if i >= args.warmup:
+                vals.append((v, dt))
+        value = statistics.mean(v for v, _ in vals)
+        line = {"metric": metric, "value": value, "unit": metric.split()[0], "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * statistics.mean(dt for _, dt in vals),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": args.workload},
+                "cpu_baseline": {"value": value, "unit": metric.split()[0], "cores": cores, "kind": "oracle",
+                                 "sample": desc},
+                "e2e": {"value": value, "unit": metric.split()[0], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    import paper_2005_12692_gb300 as cr
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cr.build()
+    L = cr.lib()
+
+    data = make_input(args.workload)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # -------- the step --------
+    if W["kind"] == "single":
+        img = torch.from_numpy(data).to(dev)
+        units = num_cells(data.shape)
+
+        def step():
+            return cr.cr_persistence(img, maxdim=W["maxdim"])
+    else:
+        shapes = [tuple(a.shape) for a in data]
+        offs = [0]
+        for a in data:
+            offs.append(offs[-1] + a.size)
+        flat = torch.from_numpy(np.concatenate([a.reshape(-1) for a in data])).to(dev)
+        units = len(data)
+
+        def step():
+            bp = cr.cr_persistence_batched(flat, maxdim=1, shapes=shapes, offsets=offs)
+            p = bp.pairs
+            sel = (p.dim == 1) & torch.isfinite(p.death)
+            life = torch.where(sel, p.death - p.birth, torch.zeros_like(p.birth))
+            g = cr.cr_backward_batched(flat, shapes, offs, bp, -2 * life, 2 * life)
+            return g
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # -------- timed region (device-resident input) --------
+    L.cr_profile_reset()
+    L.cr_profile_enable(1)
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    launches0 = int(L.cr_launch_count())
+    step_ms = []
+    barrier()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    barrier()
+    clk = clocks.stop()
+    L.cr_profile_enable(0)
+    launches = int(L.cr_launch_count()) - launches0
+    stages = read_profile(cr)
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = units * world / (ms_per_step / 1e3)
+
+    # -------- end to end through host buffers --------
+    e2e_ms = []
+    if W["kind"] == "single":
+        host = torch.from_numpy(data).pin_memory()
+        h2d = host.numel() * 4
+        d2h = 0
+        for i in range(args.warmup + max(3, args.steps // 2)):
+            flush.fill_(1)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            dimg = host.to(dev, non_blocking=True)
+            p = cr.cr_persistence(dimg, maxdim=W["maxdim"])
+            out = p.raw.cpu()
+            torch.cuda.synchronize(dev)
+            if i >= args.warmup:
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            d2h = out.numel()
+    else:
+        hflat = flat.cpu().pin_memory()
+        h2d = hflat.numel() * 4
+        d2h = 0
+        for i in range(args.warmup + max(2, args.steps // 2)):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            dflat = hflat.to(dev, non_blocking=True)
+            bp = cr.cr_persistence_batched(dflat, maxdim=1, shapes=shapes, offsets=offs)
+            p = bp.pairs
+            sel = (p.dim == 1) & torch.isfinite(p.death)
+            life = torch.where(sel, p.death - p.birth, torch.zeros_like(p.birth))
+            g = cr.cr_backward_batched(dflat, shapes, offs, bp, -2 * life, 2 * life)
+            gh = g.cpu()
+            torch.cuda.synchronize(dev)
+            if i >= args.warmup:
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            d2h = gh.numel() * 4
+    e2e_value = units * world / (statistics.mean(e2e_ms) / 1e3)
+
+    peaks = load_peaks()
+    roof = roofline_from(stages, peaks)
+
+    line = {"metric": metric, "value": value, "unit": metric.split()[0], "n_gpus": args.gpus * 0 + world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload,
+                       "shape": list(data.shape) if W["kind"] == "single" else "4096 x U{28..256}^2",
+                       "maxdim": W["maxdim"], "cells": num_cells(data.shape) if W["kind"] == "single" else None,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between steps (256 MiB write)"},
+            "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": metric.split()[0], "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": roof,
+            "stages": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+                       for k, v in stages.items()}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, desc = run_oracle(args.workload, data)
+        line["cpu_baseline"] = {"value": v, "unit": metric.split()[0], "cores": 1, "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * cr.h -- C ABI of libcr.so: persistent homology of cubical images on one GPU.
+ *
+ * The library computes Z/2 persistent homology of the sublevel filtration of a
+ * 1D, 2D or 3D float32 array under the V-construction (Kaji, Sudo, Ahara,
+ * "Cubical Ripser", Sec. 2): every pixel/voxel is a 0-cube with its value, and
+ * every higher cube takes the maximum of the values of its vertices.  Pairs
+ * are the persistence pairs of one fixed total order on the cubes:
+ *
+ *   ascending value, then ascending dimension, then descending
+ *   L = ((m*Nz + z)*Ny + y)*Nx + x,
+ *
+ * which is the reverse of the paper's (-birth, m, z, y, x) cohomology order
+ * (Sec. 2).  Cube types m: 1-cubes m=0,1,2 step in x, y, z; 2-cubes m=0,1,2
+ * span {x,y}, {x,z}, {y,z}; 0- and 3-cubes have m=0.  Arrays are C-order with
+ * x the fastest index (Sec. 2, Fig. 1: the cell "to the right" is x+1); a 2D
+ * array is (Ny, Nx), a 1D array (Nx).
+ *
+ * Conventions shared by every entry point:
+ *   - All pointers named *_dev, and img/imgs/pairs_out/grad_* are DEVICE
+ *     pointers owned by the caller; shape arrays and n_pairs are HOST memory.
+ *   - ws/ws_bytes: caller-owned device workspace; size it with the matching
+ *     *_workspace_size call.  The library allocates no device memory.
+ *   - Work is enqueued on `stream`; the call returns after the stream reaches
+ *     the point where the host must read a count (it synchronises `stream`).
+ *   - Return value: CR_OK or a negative CR_ERR_* code; the library never
+ *     aborts the process.  After CR_ERR_CUDA the CUDA error is also returned
+ *     by cudaGetLastError on the calling thread.
+ *   - -0.0 is treated as +0.0; +inf is an ordinary (largest) value; NaN
+ *     anywhere is rejected with CR_ERR_NAN.
+ */
+#ifndef CR_H_
+#define CR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cr_stream_t; /* same object as cudaStream_t */
+
+/* ---- error codes ---- */
+#define CR_OK 0
+#define CR_ERR_INVALID_ARG (-1) /* bad ndim/shape/pointer/flag */
+#define CR_ERR_NAN (-2)         /* NaN in the input */
+#define CR_ERR_TOO_LARGE (-3)   /* 3 * voxels of one image >= 2^32, or all images >= 2^31 voxels */
+#define CR_ERR_CAPACITY (-4)    /* pairs_out too small; *n_pairs = pairs needed */
+#define CR_ERR_WORKSPACE (-5)   /* ws_bytes too small, or a data-dependent buffer overflowed */
+#define CR_ERR_CUDA (-6)        /* a CUDA runtime call failed */
+#define CR_ERR_TIMEOUT (-7)     /* a bounded device-side wait or iteration cap expired */
+#define CR_ERR_INTERNAL (-8)    /* an internal consistency check failed */
+
+/* ---- flags ---- */
+#define CR_KEEP_ZERO 1u   /* also emit pairs with death == birth */
+#define CR_TOPDIM_ONLY 2u /* only the (ndim-1)-dimensional pairs, by duality (Sec. 2, Rem. 2.1) */
+
+/* A persistence pair [birth, death) of dimension `dim` (Sec. 1: a d-cycle
+ * born at `birth`, killed at `death`).  birth_cell is the L index of the
+ * dim-cube that creates the class, death_cell the L index of the
+ * (dim+1)-cube that kills it (its location is the paper's "location of the
+ * cell giving birth", Sec. 4, Ex. 4.6).  Essential classes: death = +inf,
+ * death_cell = -1.  32 bytes. */
+typedef struct {
+    int32_t dim;
+    float birth;
+    float death;
+    uint32_t flags; /* bit 0: essential */
+    int64_t birth_cell;
+    int64_t death_cell;
+} cr_pair;
+
+#define CR_PAIR_ESSENTIAL 1u
+
+/* Device workspace (bytes) for cr_persistence on one image of this shape,
+ * maxdim and flags.  Host-only; no GPU work.
+ *   cr_workspace_size          a bound that the union-find stages, the
+ *                              residual-column lists and the output sort
+ *                              cannot exceed for any input of this shape;
+ *   cr_workspace_size_typical  a smaller size that suffices for smooth or
+ *                              noisy fields; an input that needs more makes
+ *                              the call return CR_ERR_WORKSPACE (nothing else
+ *                              is wrong; retry with the bound).
+ * The column arena of the 3D reduction is data-dependent: it takes what is
+ * left of the workspace and reports CR_ERR_WORKSPACE if that is exceeded. */
+int cr_workspace_size(int ndim, const int64_t *shape, int maxdim, uint32_t flags, size_t *bytes);
+int cr_workspace_size_typical(int ndim, const int64_t *shape, int maxdim, uint32_t flags, size_t *bytes);
+
+/*
+ * Persistent homology of one image (Sec. 2; Sec. 4, Ex. 4.1 `computePH`).
+ *   img       device float32[prod(shape)], C-order.
+ *   ndim      1, 2 or 3; shape[ndim] host array of extents >= 1.
+ *   maxdim    pairs of dimension 0..maxdim are computed (Ex. 4.1 `maxdim`);
+ *             maxdim >= ndim-1 includes the top dimension via duality.
+ *   pairs_out device cr_pair[capacity]; on success sorted by
+ *             (dim, birth, birth_cell).
+ *   n_pairs   host; number of pairs written (or needed, on CR_ERR_CAPACITY).
+ *   flags     CR_KEEP_ZERO | CR_TOPDIM_ONLY.
+ */
+int cr_persistence(const float *img, int ndim, const int64_t *shape, int maxdim, cr_pair *pairs_out,
+                   int64_t capacity, int64_t *n_pairs, void *ws, size_t ws_bytes, cr_stream_t stream,
+                   uint32_t flags);
+
+/* Workspace for cr_persistence_batched over these images (shapes: host
+ * int32[n_images * ndim], each row the extents of one image). */
+int cr_workspace_size_batched(const int32_t *shapes, int n_images, int ndim, int maxdim, uint32_t flags,
+                              size_t *bytes);
+int cr_workspace_size_batched_typical(const int32_t *shapes, int n_images, int ndim, int maxdim, uint32_t flags,
+                                      size_t *bytes);
+
+/*
+ * Many images of possibly different shapes in one pass: the persistence of
+ * each image, independently, with every stage run once over all images.
+ *   imgs         device float32, images packed back to back.
+ *   img_offsets  host int64[n_images+1]; image i is imgs[img_offsets[i] ..
+ *                img_offsets[i+1]); must equal the running product of shapes.
+ *   shapes       host int32[n_images * ndim].
+ *   pairs_out    device cr_pair[capacity], grouped by image, each group
+ *                sorted as in cr_persistence.
+ *   pair_offsets device int64[n_images+1]; pairs of image i are
+ *                pairs_out[pair_offsets[i] .. pair_offsets[i+1]).
+ *   n_pairs      host; total pairs.
+ */
+int cr_persistence_batched(const float *imgs, const int64_t *img_offsets, const int32_t *shapes, int n_images,
+                           int ndim, int maxdim, cr_pair *pairs_out, int64_t capacity, int64_t *pair_offsets,
+                           int64_t *n_pairs, void *ws, size_t ws_bytes, cr_stream_t stream, uint32_t flags);
+
+/* Workspace for cr_backward (n_images = 1) / cr_backward_batched with
+ * n_pairs pairs.  Host-only. */
+int cr_backward_workspace_size(int64_t n_pairs, int n_images, size_t *bytes);
+
+/*
+ * Gradient of a loss L(diagram) with respect to the image.  A pair's birth
+ * (death) is the value of its birth (death) cube, which is the value of the
+ * cube's latest vertex in the filtration order (largest value; among equal
+ * values the smallest linear index).  dL/dbirth and dL/ddeath are therefore
+ * added to the image gradient at that vertex (V-construction, Sec. 2).
+ * Essential deaths contribute nothing.  Contributions to one pixel are summed
+ * in double precision in a fixed order (by pair index), then rounded once to
+ * float32, so the result is deterministic.
+ *   pairs       device cr_pair[n_pairs] as returned by cr_persistence.
+ *   grad_birth  device float32[n_pairs]; grad_death device float32[n_pairs].
+ *   grad_img    device float32[prod(shape)], overwritten (zeroed by callee).
+ */
+int cr_backward(const float *img, int ndim, const int64_t *shape, const cr_pair *pairs, int64_t n_pairs,
+                const float *grad_birth, const float *grad_death, float *grad_img, void *ws, size_t ws_bytes,
+                cr_stream_t stream);
+
+/* Batched gradient: pairs/pair_offsets as returned by
+ * cr_persistence_batched (pair_offsets is a device array), img_offsets and
+ * shapes as passed to it; grad_imgs is packed like imgs. */
+int cr_backward_batched(const float *imgs, const int64_t *img_offsets, const int32_t *shapes, int n_images,
+                        int ndim, const cr_pair *pairs, const int64_t *pair_offsets, int64_t n_pairs,
+                        const float *grad_birth, const float *grad_death, float *grad_imgs, void *ws,
+                        size_t ws_bytes, cr_stream_t stream);
+
+/* Anchor (x, y, z) and type m of the cube (dim, L) of an image of this shape
+ * (the paper's cell tuple (x, y, z, m, d), Sec. 2).  Host-only. */
+int cr_cell_location(int64_t L, int dim, int ndim, const int64_t *shape, int *m, int64_t *x, int64_t *y,
+                     int64_t *z);
+
+/* Diagnostics for benchmarks.  With profiling on, every stage of a call is
+ * bracketed by CUDA events recorded on the caller's stream; totals per stage
+ * are read with cr_profile_read (stage 0..15; name, total milliseconds,
+ * number of timed launches, algorithmic bytes the stage must move).  Returns
+ * CR_ERR_INVALID_ARG past the last stage.  cr_launch_count is the number of
+ * kernels the library has launched since it was loaded.  Host-only. */
+int cr_profile_enable(int on);
+void cr_profile_reset(void);
+int cr_profile_read(int stage, const char **name, double *total_ms, int64_t *count, double *bytes);
+int64_t cr_launch_count(void);
+
+/* Static description of an error code. */
+const char *cr_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CR_H_ */

@@ -1,0 +1,655 @@
+// cr_api.cu -- the C ABI of libcr (declared in include/cr.h): validation,
+// workspace layout, the order of the stages, the canonical output order and
+// the backward scatter.
+//
+// Stages of one call (all images of a batch at once):
+//   H0      union-find with the elder rule on the pixel graph (Sec. 2);
+//   H1 (3D) apparent pairs + lock-free coboundary reduction (Sec. 2);
+//   top     union-find on the dual graph in the reversed order (Sec. 2,
+//           Rem. 2.1): dimension 1 of a 2D image, dimension 2 of a volume;
+//   output  pairs sorted by (image, dim, birth, birth cell).
+#include "cr_internal.cuh"
+#include <vector>
+#include <cmath>
+
+namespace cr {
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+struct HostPlan {
+    std::vector<Seg> segs;
+    int64_t vtot = 0, ctot = 0, cells = 0;
+    int64_t max_face_per_image = 0;
+    bool any_h0 = false, any_dual = false, any_mid = false;
+    int nseg_bits = 0;
+};
+
+static int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+static int64_t cube_count(int64_t nz, int64_t ny, int64_t nx) {
+    // all cubes of the full grid: prod over axes of (n + (n-1)) = prod (2n - 1)
+    return (2 * nz - 1) * (2 * ny - 1) * (2 * nx - 1);
+}
+
+static int plan_images(const int64_t *const *shapes_rows, int n, int ndim, int maxdim, uint32_t flags, HostPlan &P) {
+    if (n < 1 || ndim < 1 || ndim > 3 || maxdim < 0) return CR_ERR_INVALID_ARG;
+    if (flags & ~(CR_KEEP_ZERO | CR_TOPDIM_ONLY)) return CR_ERR_INVALID_ARG;
+    P.segs.resize(n);
+    int64_t voff = 0, coff = 0;
+    for (int i = 0; i < n; i++) {
+        const int64_t *sh = shapes_rows[i];
+        int64_t nz = 1, ny = 1, nx = 1;
+        if (ndim == 1) nx = sh[0];
+        else if (ndim == 2) { ny = sh[0]; nx = sh[1]; }
+        else { nz = sh[0]; ny = sh[1]; nx = sh[2]; }
+        if (nz < 1 || ny < 1 || nx < 1) return CR_ERR_INVALID_ARG;
+        int64_t v = nz * ny * nx;
+        if (nz > 65535 * 32 || ny > 65535 * 32 || nx > 65535 * 32 || 3 * v >= ((int64_t)1 << 32))
+            return CR_ERR_TOO_LARGE;
+        Seg &S = P.segs[i];
+        S.voff = voff;
+        S.loff = 3 * voff;
+        S.nx = (int32_t)nx;
+        S.ny = (int32_t)ny;
+        S.nz = (int32_t)nz;
+        S.edim = nz > 1 ? 3 : (ny > 1 ? 2 : (nx > 1 ? 1 : 0));
+        int top = S.edim >= 1 ? S.edim - 1 : 0;
+        bool topdim = (flags & CR_TOPDIM_ONLY) != 0;
+        bool want_h0 = maxdim >= 0 && (!topdim || top == 0);
+        bool want_dual = S.edim >= 2 && (topdim || maxdim >= S.edim - 1);
+        bool want_mid = S.edim == 3 && !topdim && maxdim >= 1;
+        int64_t ncell = 0;
+        if (want_dual) ncell = S.edim == 3 ? (nx - 1) * (ny - 1) * (nz - 1) : (nx - 1) * (ny - 1);
+        S.coff = coff;
+        S.ncell = ncell;
+        P.any_h0 |= want_h0 || want_mid;
+        P.any_dual |= ncell > 0;
+        P.any_mid |= want_mid;
+        int64_t faces = 3 * v;
+        if (faces > P.max_face_per_image) P.max_face_per_image = faces;
+        voff += v;
+        coff += ncell + 1;
+        P.cells += cube_count(nz, ny, nx);
+    }
+    P.vtot = voff;
+    P.ctot = coff;
+    if (P.vtot >= ((int64_t)1 << 31) - 2 || P.ctot >= ((int64_t)1 << 31) - 2 || 3 * P.vtot >= ((int64_t)1 << 40))
+        return CR_ERR_TOO_LARGE;
+    int b = 0;
+    while (((int64_t)1 << b) < n) b++;
+    P.nseg_bits = b;
+    return CR_OK;
+}
+
+// scratch geometry of the reduction
+static void red_geometry(const HostPlan &P, int64_t &nwarps, int &maxlen) {
+    nwarps = (int64_t)num_sms() * 16;
+    int64_t ml = P.max_face_per_image + 32;
+    if (ml > 32768) ml = 32768;
+    maxlen = (int)((ml + 31) & ~31);
+}
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// fixed part of the workspace
+static size_t fixed_bytes(const HostPlan &P) {
+    size_t b = 0;
+    b += al(P.segs.size() * sizeof(Seg));
+    b += al(64 * sizeof(unsigned long long));  // status + counters
+    int64_t nodes = P.vtot > P.ctot ? P.vtot : P.ctot;
+    b += al((size_t)nodes * sizeof(uint32_t));  // labels
+    b += al((size_t)P.vtot);                    // primal hooks
+    b += al((size_t)P.ctot);                    // dual hooks
+    b += al((size_t)((3 * P.vtot + 31) / 32) * sizeof(uint32_t));  // extra H0 edge mask
+    return b;
+}
+
+// region shared by the stages; `worst` gives a bound that the union-find and
+// sorting stages never exceed
+static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
+    int64_t nodes = P.vtot > P.ctot ? P.vtot : P.ctot;
+    size_t uf, h1 = 0, out;
+    if (worst) {
+        uf = al((size_t)nodes * 33) + al((size_t)(3 * P.vtot) * 32) + (1 << 20);
+    } else {
+        uf = al((size_t)nodes * 16) + al((size_t)P.vtot * 48) + (8 << 20);
+    }
+    if (P.any_mid) {
+        int64_t nw;
+        int ml;
+        red_geometry(P, nw, ml);
+        int64_t cols = worst ? 3 * P.vtot : (3 * P.vtot) / 8 + 4096;
+        int64_t arena = worst ? 12 * P.vtot : 2 * P.vtot + (1 << 20);
+        h1 = al((size_t)cols * 32) + al(radix_temp_bytes(cols)) + al((size_t)(3 * P.vtot) * 4) +
+             al((size_t)arena * 8) + al((size_t)nw * 2 * ml * 8) + (1 << 20);
+    }
+    int64_t maxpairs = (flags & CR_KEEP_ZERO) ? P.cells / 2 + (int64_t)P.segs.size() + 16
+                                              : (worst ? P.cells / 2 + (int64_t)P.segs.size() + 16
+                                                       : P.vtot / 4 + 4096);
+    out = al((size_t)maxpairs * (24 + 32)) + al(radix_temp_bytes(maxpairs)) + al((size_t)P.segs.size() * 4 + 64) +
+          al(scan_temp_bytes((int64_t)P.segs.size() + 1)) + (1 << 20);
+    size_t r = uf;
+    if (h1 > r) r = h1;
+    if (out > r) r = out;
+    return r;
+}
+
+static size_t total_bytes(const HostPlan &P, uint32_t flags, bool worst) {
+    size_t w = fixed_bytes(P) + region_bytes(P, flags, true) + 1024;
+    if (worst) return w;
+    size_t t = fixed_bytes(P) + region_bytes(P, flags, false) + 1024;
+    return t < w ? t : w;
+}
+
+// ---------------------------------------------------------------------------
+// output: sort by (image, dim, birth, birth cell), write pair offsets
+// ---------------------------------------------------------------------------
+__global__ void k_out_keys(cr_pair *pairs, int64_t np, uint64_t *keys, uint32_t *vals, uint32_t *segc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    cr_pair p = pairs[i];
+    keys[i] = ((uint64_t)ord32(p.birth) << 32) | (uint64_t)(uint32_t)p.birth_cell;
+    vals[i] = (uint32_t)i;
+    if (segc) atomicAdd(&segc[p.flags >> 8], 1u);
+}
+__global__ void k_out_rekey(const cr_pair *pairs, int64_t np, const uint32_t *vals, uint64_t *keys, int what) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const cr_pair &p = pairs[vals[i]];
+    keys[i] = what == 0 ? (uint64_t)p.dim : (uint64_t)(p.flags >> 8);
+}
+__global__ void k_out_gather(const cr_pair *src, int64_t np, const uint32_t *vals, cr_pair *dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    cr_pair p = src[vals[i]];
+    p.flags &= 0xFFu;
+    dst[i] = p;
+}
+__global__ void k_out_offsets(const uint32_t *scanned, int n, int64_t np, int64_t *offs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) offs[i] = (int64_t)scanned[i];
+    if (i == n) offs[n] = np;
+}
+static inline unsigned nbk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// the pipeline
+// ---------------------------------------------------------------------------
+static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, cr_pair *pairs_out, int64_t capacity,
+                    int64_t *pair_offsets, int64_t *n_pairs, void *ws, size_t ws_bytes, cudaStream_t st) {
+    (void)maxdim;
+    const int n = (int)P.segs.size();
+    size_t need_min = fixed_bytes(P) + 1024;
+    if (!ws || ws_bytes < need_min) return CR_ERR_WORKSPACE;
+    Carver C(ws, ws_bytes);
+    Seg *segs = C.take<Seg>(n);
+    unsigned long long *cnt = C.take<unsigned long long>(64);
+    int64_t nodes = P.vtot > P.ctot ? P.vtot : P.ctot;
+    uint32_t *lab = C.take<uint32_t>(nodes);
+    uint8_t *dd = C.take<uint8_t>(P.vtot);
+    uint8_t *ddc = C.take<uint8_t>(P.ctot);
+    int64_t mask_words = (3 * P.vtot + 31) / 32;
+    uint32_t *extra = C.take<uint32_t>(mask_words);
+    if (!C.ok) return CR_ERR_WORKSPACE;
+    char *region = (char *)ws + ((C.used + 255) & ~(size_t)255);
+    size_t region_cap = ws_bytes - ((C.used + 255) & ~(size_t)255);
+    int *status = (int *)&cnt[0];
+    unsigned long long *pair_count = &cnt[1];
+
+    cudaMemcpyAsync(segs, P.segs.data(), n * sizeof(Seg), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(cnt, 0, 64 * sizeof(unsigned long long), st);
+    if (P.any_mid) cudaMemsetAsync(extra, 0, (size_t)mask_words * 4, st);
+
+    PairBuf pb;
+    pb.pairs = pairs_out;
+    pb.capacity = capacity;
+    pb.count = pair_count;
+
+    unsigned long long hc[4];
+    int rc = CR_OK;
+
+    // ---- H0 ----
+    if (P.any_h0) {
+        Carver R(region, region_cap);
+        UF u;
+        u.lab = lab;
+        u.dd = dd;
+        u.cnt = &cnt[8];
+        u.hcnt = hc;
+        // groups: the number of roots is not known yet; give the union-find a
+        // share of the region proportional to the node count and the rest to edges
+        int64_t max_groups = P.vtot;
+        size_t gbytes = (size_t)max_groups * 33 + 6 * 256;
+        if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 33) - 64;
+        if (max_groups < 1) return CR_ERR_WORKSPACE;
+        u.gkey = R.take<uint64_t>(max_groups);
+        u.minE = R.take<uint64_t>(max_groups);
+        u.groot = R.take<uint32_t>(max_groups);
+        u.gseg = R.take<uint32_t>(max_groups);
+        u.tgt = R.take<uint32_t>(max_groups);
+        u.hook = R.take<uint32_t>(max_groups);
+        u.gdead = R.take<uint8_t>(max_groups);
+        u.max_groups = max_groups;
+        size_t left = R.cap > R.used ? R.cap - R.used : 0;
+        int64_t max_edges = (int64_t)(left / 32) - 64;
+        if (max_edges > 3 * P.vtot + 1) max_edges = 3 * P.vtot + 1;
+        if (max_edges < 1 || !R.ok) return CR_ERR_WORKSPACE;
+        for (int b = 0; b < 2; b++) {
+            u.ek[b] = R.take<uint64_t>(max_edges);
+            u.ea[b] = R.take<uint32_t>(max_edges);
+            u.eb[b] = R.take<uint32_t>(max_edges);
+        }
+        u.max_edges = max_edges;
+        if (!R.ok) return CR_ERR_WORKSPACE;
+        rc = run_h0(imgs, segs, n, P.vtot, u, pb, flags, P.any_mid ? extra : nullptr, status, st);
+        if (rc) return rc;
+    }
+
+    // ---- middle dimension of volumes ----
+    if (P.any_mid) {
+        Carver R(region, region_cap);
+        H1Bufs B;
+        int64_t nw;
+        int ml;
+        red_geometry(P, nw, ml);
+        B.nwarps = nw;
+        B.maxlen = ml;
+        B.P_len = 3 * P.vtot;
+        B.P = R.take<int>(B.P_len);
+        B.scratch = R.take<uint64_t>((size_t)nw * 2 * ml);
+        B.cnt = &cnt[16];
+        if (!R.ok) return CR_ERR_WORKSPACE;
+        size_t left = R.cap - R.used;
+        // columns (32 B each + sort temp) get up to half of what is left, the arena the rest
+        int64_t max_cols = (int64_t)((left / 2) / 40) - 1024;
+        if (max_cols > 3 * P.vtot + 1) max_cols = 3 * P.vtot + 1;
+        if (max_cols < 1) return CR_ERR_WORKSPACE;
+        B.colkey = R.take<uint64_t>(max_cols);
+        B.colkey_tmp = R.take<uint64_t>(max_cols);
+        B.colseg = R.take<uint32_t>(max_cols);
+        B.colseg_tmp = R.take<uint32_t>(max_cols);
+        B.cur = R.take<unsigned long long>(max_cols);
+        B.sort_temp_bytes = radix_temp_bytes(max_cols);
+        B.sort_temp = R.take<char>(B.sort_temp_bytes);
+        B.max_cols = max_cols;
+        if (!R.ok) return CR_ERR_WORKSPACE;
+        left = R.cap - R.used;
+        B.arena_cap = (int64_t)(left / 8) - 64;
+        if (B.arena_cap < 64) return CR_ERR_WORKSPACE;
+        B.arena = R.take<uint64_t>(B.arena_cap);
+        int64_t ncols = 0;
+        rc = run_h1(imgs, dd, extra, segs, n, P.vtot, B, pb, flags, status, &ncols, st);
+        if (rc) return rc;
+    }
+
+    // ---- top dimension by duality ----
+    if (P.any_dual) {
+        Carver R(region, region_cap);
+        UF u;
+        u.lab = lab;
+        u.dd = ddc;
+        u.cnt = &cnt[24];
+        u.hcnt = hc;
+        int64_t max_groups = P.ctot;
+        size_t gbytes = (size_t)max_groups * 33 + 6 * 256;
+        if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 33) - 64;
+        if (max_groups < 1) return CR_ERR_WORKSPACE;
+        u.gkey = R.take<uint64_t>(max_groups);
+        u.minE = R.take<uint64_t>(max_groups);
+        u.groot = R.take<uint32_t>(max_groups);
+        u.gseg = R.take<uint32_t>(max_groups);
+        u.tgt = R.take<uint32_t>(max_groups);
+        u.hook = R.take<uint32_t>(max_groups);
+        u.gdead = R.take<uint8_t>(max_groups);
+        u.max_groups = max_groups;
+        size_t left = R.cap > R.used ? R.cap - R.used : 0;
+        int64_t max_edges = (int64_t)(left / 32) - 64;
+        if (max_edges > 3 * P.vtot + 1) max_edges = 3 * P.vtot + 1;
+        if (max_edges < 1 || !R.ok) return CR_ERR_WORKSPACE;
+        for (int b = 0; b < 2; b++) {
+            u.ek[b] = R.take<uint64_t>(max_edges);
+            u.ea[b] = R.take<uint32_t>(max_edges);
+            u.eb[b] = R.take<uint32_t>(max_edges);
+        }
+        u.max_edges = max_edges;
+        if (!R.ok) return CR_ERR_WORKSPACE;
+        rc = run_dual(imgs, segs, n, P.vtot, P.ctot, u, pb, flags, status, st);
+        if (rc) return rc;
+    }
+
+    // ---- count, status ----
+    int hstatus = 0;
+    cudaMemcpyAsync(hc, pair_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
+    if (hstatus) return hstatus;
+    int64_t np = (int64_t)hc[0];
+    *n_pairs = np;
+    if (np > capacity) return CR_ERR_CAPACITY;
+
+    // ---- canonical order ----
+    {
+        Carver R(region, region_cap);
+        uint64_t *k0 = R.take<uint64_t>(np + 1), *k1 = R.take<uint64_t>(np + 1);
+        uint32_t *v0 = R.take<uint32_t>(np + 1), *v1 = R.take<uint32_t>(np + 1);
+        cr_pair *tmp = R.take<cr_pair>(np + 1);
+        size_t rt = radix_temp_bytes(np + 1);
+        void *rtemp = R.take<char>(rt);
+        uint32_t *segc = R.take<uint32_t>(n + 1);
+        uint32_t *part = R.take<uint32_t>(scan_temp_bytes(n + 1) / 4 + 1);
+        if (!R.ok) return CR_ERR_WORKSPACE;
+        if (np > 0) {
+            prof_begin(st, STAGE_OUT_SORT);
+            if (pair_offsets) cudaMemsetAsync(segc, 0, (n + 1) * sizeof(uint32_t), st);
+            CR_NOTE_LAUNCH();
+            k_out_keys<<<nbk(np), 256, 0, st>>>(pairs_out, np, k0, v0, pair_offsets ? segc : nullptr);
+            if (radix_sort_u64(k0, v0, k1, v1, np, 0, 64, rtemp, rt, st) != cudaSuccess) return CR_ERR_CUDA;
+            CR_NOTE_LAUNCH();
+            k_out_rekey<<<nbk(np), 256, 0, st>>>(pairs_out, np, v0, k0, 0);
+            if (radix_sort_u64(k0, v0, k1, v1, np, 0, 2, rtemp, rt, st) != cudaSuccess) return CR_ERR_CUDA;
+            if (n > 1) {
+                CR_NOTE_LAUNCH();
+                k_out_rekey<<<nbk(np), 256, 0, st>>>(pairs_out, np, v0, k0, 1);
+                if (radix_sort_u64(k0, v0, k1, v1, np, 0, P.nseg_bits, rtemp, rt, st) != cudaSuccess)
+                    return CR_ERR_CUDA;
+            }
+            cudaMemcpyAsync(tmp, pairs_out, (size_t)np * sizeof(cr_pair), cudaMemcpyDeviceToDevice, st);
+            CR_NOTE_LAUNCH();
+            k_out_gather<<<nbk(np), 256, 0, st>>>(tmp, np, v0, pairs_out);
+            prof_end(st, STAGE_OUT_SORT, 3.0 * 24.0 * np + 64.0 * np);
+        }
+        if (pair_offsets) {
+            if (np == 0) cudaMemsetAsync(segc, 0, (n + 1) * sizeof(uint32_t), st);
+            if (exclusive_scan_u32(segc, n, part, st) != cudaSuccess) return CR_ERR_CUDA;
+            CR_NOTE_LAUNCH();
+            k_out_offsets<<<nbk(n + 1), 256, 0, st>>>(segc, n, np, pair_offsets);
+        }
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
+    prof_flush();
+    return CR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t argmax_vertex(const float *img, const Seg &S, int dim, uint32_t L) {
+    int c[3];
+    c[0] = (int)(L % (uint32_t)S.nx);
+    uint32_t r = L / (uint32_t)S.nx;
+    c[1] = (int)(r % (uint32_t)S.ny);
+    r /= (uint32_t)S.ny;
+    c[2] = (int)(r % (uint32_t)S.nz);
+    int m = (int)(r / (uint32_t)S.nz);
+    int span = 0;  // bits x=1, y=2, z=4
+    if (dim == 1) span = 1 << m;
+    else if (dim == 2) span = m == 0 ? 3 : (m == 1 ? 5 : 6);
+    else if (dim == 3) span = 7;
+    uint64_t best = 0;
+    int64_t bv = -1;
+    for (int dz = 0; dz <= ((span >> 2) & 1); dz++)
+        for (int dy = 0; dy <= ((span >> 1) & 1); dy++)
+            for (int dx = 0; dx <= (span & 1); dx++) {
+                int64_t lv = ((int64_t)(c[2] + dz) * S.ny + (c[1] + dy)) * S.nx + (c[0] + dx);
+                uint64_t k = make_key(ord32(img[S.voff + lv]), (uint32_t)lv);
+                if (bv < 0 || k > best) { best = k; bv = S.voff + lv; }
+            }
+    return bv;
+}
+
+__global__ void k_bw_contrib(const float *img, const Seg *segs, int nseg, const cr_pair *pairs, int64_t np,
+                             const int64_t *pair_offsets, const float *gb, const float *gd, uint64_t *keys,
+                             uint32_t *vals) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    int si = 0;
+    if (pair_offsets && nseg > 1) {
+        int lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (pair_offsets[mid] <= k) lo = mid; else hi = mid - 1;
+        }
+        si = lo;
+    }
+    const Seg S = segs[si];
+    cr_pair p = pairs[k];
+    int64_t vb = argmax_vertex(img, S, p.dim, (uint32_t)p.birth_cell);
+    keys[2 * k] = ((uint64_t)vb << 32) | (uint64_t)(2 * k);
+    vals[2 * k] = __float_as_uint(gb[k]);
+    if (p.death_cell >= 0) {
+        int64_t vd = argmax_vertex(img, S, p.dim + 1, (uint32_t)p.death_cell);
+        keys[2 * k + 1] = ((uint64_t)vd << 32) | (uint64_t)(2 * k + 1);
+        vals[2 * k + 1] = __float_as_uint(gd[k]);
+    } else {
+        keys[2 * k + 1] = ~0ull;
+        vals[2 * k + 1] = 0;
+    }
+}
+
+__global__ void k_bw_sum(const uint64_t *keys, const uint32_t *vals, int64_t nc, float *grad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    uint64_t k = keys[i];
+    if (k == ~0ull) return;
+    uint32_t pix = (uint32_t)(k >> 32);
+    if (i > 0 && (uint32_t)(keys[i - 1] >> 32) == pix && keys[i - 1] != ~0ull) return;
+    double s = 0.0;
+    for (int64_t j = i; j < nc; j++) {
+        uint64_t kj = keys[j];
+        if (kj == ~0ull || (uint32_t)(kj >> 32) != pix) break;
+        s += (double)__uint_as_float(vals[j]);
+    }
+    grad[pix] = (float)s;
+}
+
+static size_t backward_bytes(int64_t np, int n) {
+    int64_t nc = 2 * np + 1;
+    return al((size_t)n * sizeof(Seg)) + 2 * al((size_t)nc * 8) + 2 * al((size_t)nc * 4) + al(radix_temp_bytes(nc)) +
+           1024;
+}
+
+static int backward_impl(const float *imgs, HostPlan &P, const cr_pair *pairs, const int64_t *pair_offsets,
+                         int64_t np, const float *gb, const float *gd, float *grad, void *ws, size_t ws_bytes,
+                         cudaStream_t st) {
+    const int n = (int)P.segs.size();
+    if (np < 0 || (np > 0 && (!pairs || !gb || !gd)) || !grad) return CR_ERR_INVALID_ARG;
+    if (np >= ((int64_t)1 << 30)) return CR_ERR_TOO_LARGE;
+    if (!ws || ws_bytes < backward_bytes(np, n)) return CR_ERR_WORKSPACE;
+    Carver C(ws, ws_bytes);
+    Seg *segs = C.take<Seg>(n);
+    int64_t nc = 2 * np;
+    uint64_t *k0 = C.take<uint64_t>(nc + 1), *k1 = C.take<uint64_t>(nc + 1);
+    uint32_t *v0 = C.take<uint32_t>(nc + 1), *v1 = C.take<uint32_t>(nc + 1);
+    size_t rt = radix_temp_bytes(nc + 1);
+    void *rtemp = C.take<char>(rt);
+    if (!C.ok) return CR_ERR_WORKSPACE;
+    cudaMemcpyAsync(segs, P.segs.data(), n * sizeof(Seg), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(grad, 0, (size_t)P.vtot * sizeof(float), st);
+    if (np > 0) {
+        prof_begin(st, STAGE_BW_CONTRIB);
+        CR_NOTE_LAUNCH();
+        k_bw_contrib<<<nbk(np), 256, 0, st>>>(imgs, segs, n, pairs, np, pair_offsets, gb, gd, k0, v0);
+        int bits = 1;
+        while (((int64_t)1 << bits) <= P.vtot) bits++;
+        // the pixel sits in the high word; a stable sort on it keeps pair order inside a pixel
+        if (radix_sort_u64(k0, v0, k1, v1, nc, 32, 32 + (bits > 32 ? 32 : bits + 1), rtemp, rt, st) !=
+            cudaSuccess)
+            return CR_ERR_CUDA;
+        CR_NOTE_LAUNCH();
+        k_bw_sum<<<nbk(nc), 256, 0, st>>>(k0, v0, nc, grad);
+        prof_end(st, STAGE_BW_CONTRIB, 4.0 * P.vtot + 32.0 * np + 12.0 * nc);
+    }
+    if (cudaGetLastError() != cudaSuccess) return CR_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
+    return CR_OK;
+}
+
+}  // namespace cr
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace cr;
+
+static int plan_single(int ndim, const int64_t *shape, int maxdim, uint32_t flags, HostPlan &P) {
+    if (!shape || ndim < 1 || ndim > 3) return CR_ERR_INVALID_ARG;
+    const int64_t *rows[1] = {shape};
+    return plan_images(rows, 1, ndim, maxdim, flags, P);
+}
+
+static int plan_batched(const int32_t *shapes, int n_images, int ndim, int maxdim, uint32_t flags, HostPlan &P) {
+    if (!shapes || n_images < 1 || ndim < 1 || ndim > 3) return CR_ERR_INVALID_ARG;
+    if (n_images > (1 << 24) - 1) return CR_ERR_TOO_LARGE;
+    std::vector<int64_t> buf((size_t)n_images * ndim);
+    std::vector<const int64_t *> rows(n_images);
+    for (int i = 0; i < n_images; i++) {
+        for (int d = 0; d < ndim; d++) buf[(size_t)i * ndim + d] = shapes[(size_t)i * ndim + d];
+        rows[i] = &buf[(size_t)i * ndim];
+    }
+    return plan_images(rows.data(), n_images, ndim, maxdim, flags, P);
+}
+
+extern "C" {
+
+int cr_workspace_size(int ndim, const int64_t *shape, int maxdim, uint32_t flags, size_t *bytes) {
+    if (!bytes) return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_single(ndim, shape, maxdim, flags, P);
+    if (rc) return rc;
+    *bytes = total_bytes(P, flags, true);
+    return CR_OK;
+}
+
+int cr_workspace_size_typical(int ndim, const int64_t *shape, int maxdim, uint32_t flags, size_t *bytes) {
+    if (!bytes) return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_single(ndim, shape, maxdim, flags, P);
+    if (rc) return rc;
+    *bytes = total_bytes(P, flags, false);
+    return CR_OK;
+}
+
+int cr_workspace_size_batched(const int32_t *shapes, int n_images, int ndim, int maxdim, uint32_t flags,
+                              size_t *bytes) {
+    if (!bytes) return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_batched(shapes, n_images, ndim, maxdim, flags, P);
+    if (rc) return rc;
+    *bytes = total_bytes(P, flags, true);
+    return CR_OK;
+}
+
+int cr_workspace_size_batched_typical(const int32_t *shapes, int n_images, int ndim, int maxdim, uint32_t flags,
+                                      size_t *bytes) {
+    if (!bytes) return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_batched(shapes, n_images, ndim, maxdim, flags, P);
+    if (rc) return rc;
+    *bytes = total_bytes(P, flags, false);
+    return CR_OK;
+}
+
+int cr_persistence(const float *img, int ndim, const int64_t *shape, int maxdim, cr_pair *pairs_out,
+                   int64_t capacity, int64_t *n_pairs, void *ws, size_t ws_bytes, cr_stream_t stream,
+                   uint32_t flags) {
+    if (!img || !n_pairs || capacity < 0 || (capacity > 0 && !pairs_out)) return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_single(ndim, shape, maxdim, flags, P);
+    if (rc) return rc;
+    rc = pipeline(img, P, maxdim, flags, pairs_out, capacity, nullptr, n_pairs, ws, ws_bytes, (cudaStream_t)stream);
+    if (rc == CR_ERR_CUDA) return rc;
+    return rc;
+}
+
+int cr_persistence_batched(const float *imgs, const int64_t *img_offsets, const int32_t *shapes, int n_images,
+                           int ndim, int maxdim, cr_pair *pairs_out, int64_t capacity, int64_t *pair_offsets,
+                           int64_t *n_pairs, void *ws, size_t ws_bytes, cr_stream_t stream, uint32_t flags) {
+    if (!imgs || !img_offsets || !n_pairs || !pair_offsets || capacity < 0 || (capacity > 0 && !pairs_out))
+        return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_batched(shapes, n_images, ndim, maxdim, flags, P);
+    if (rc) return rc;
+    for (int i = 0; i < n_images; i++)
+        if (img_offsets[i] != P.segs[i].voff) return CR_ERR_INVALID_ARG;
+    if (img_offsets[n_images] != P.vtot) return CR_ERR_INVALID_ARG;
+    return pipeline(imgs, P, maxdim, flags, pairs_out, capacity, pair_offsets, n_pairs, ws, ws_bytes,
+                    (cudaStream_t)stream);
+}
+
+int cr_backward_workspace_size(int64_t n_pairs, int n_images, size_t *bytes) {
+    if (!bytes || n_pairs < 0 || n_images < 1) return CR_ERR_INVALID_ARG;
+    *bytes = backward_bytes(n_pairs, n_images);
+    return CR_OK;
+}
+
+int cr_backward(const float *img, int ndim, const int64_t *shape, const cr_pair *pairs, int64_t n_pairs,
+                const float *grad_birth, const float *grad_death, float *grad_img, void *ws, size_t ws_bytes,
+                cr_stream_t stream) {
+    if (!img) return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_single(ndim, shape, 0, 0, P);
+    if (rc) return rc;
+    return backward_impl(img, P, pairs, nullptr, n_pairs, grad_birth, grad_death, grad_img, ws, ws_bytes,
+                         (cudaStream_t)stream);
+}
+
+int cr_backward_batched(const float *imgs, const int64_t *img_offsets, const int32_t *shapes, int n_images,
+                        int ndim, const cr_pair *pairs, const int64_t *pair_offsets, int64_t n_pairs,
+                        const float *grad_birth, const float *grad_death, float *grad_imgs, void *ws,
+                        size_t ws_bytes, cr_stream_t stream) {
+    if (!imgs || !img_offsets || !pair_offsets) return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_batched(shapes, n_images, ndim, 0, 0, P);
+    if (rc) return rc;
+    for (int i = 0; i < n_images; i++)
+        if (img_offsets[i] != P.segs[i].voff) return CR_ERR_INVALID_ARG;
+    if (img_offsets[n_images] != P.vtot) return CR_ERR_INVALID_ARG;
+    return backward_impl(imgs, P, pairs, pair_offsets, n_pairs, grad_birth, grad_death, grad_imgs, ws, ws_bytes,
+                         (cudaStream_t)stream);
+}
+
+int cr_cell_location(int64_t L, int dim, int ndim, const int64_t *shape, int *m, int64_t *x, int64_t *y,
+                     int64_t *z) {
+    if (!shape || !m || !x || !y || !z || ndim < 1 || ndim > 3 || dim < 0 || dim > 3 || L < 0)
+        return CR_ERR_INVALID_ARG;
+    int64_t nz = 1, ny = 1, nx = 1;
+    if (ndim == 1) nx = shape[0];
+    else if (ndim == 2) { ny = shape[0]; nx = shape[1]; }
+    else { nz = shape[0]; ny = shape[1]; nx = shape[2]; }
+    if (nx < 1 || ny < 1 || nz < 1) return CR_ERR_INVALID_ARG;
+    *x = L % nx;
+    int64_t r = L / nx;
+    *y = r % ny;
+    r /= ny;
+    *z = r % nz;
+    *m = (int)(r / nz);
+    int maxm = (dim == 1 || dim == 2) ? 2 : 0;
+    if (*m > maxm) return CR_ERR_INVALID_ARG;
+    return CR_OK;
+}
+
+const char *cr_error_string(int code) {
+    switch (code) {
+    case CR_OK: return "success";
+    case CR_ERR_INVALID_ARG: return "invalid argument";
+    case CR_ERR_NAN: return "NaN in input";
+    case CR_ERR_TOO_LARGE: return "input too large for 32-bit cell indices";
+    case CR_ERR_CAPACITY: return "pairs_out capacity too small (n_pairs holds the count needed)";
+    case CR_ERR_WORKSPACE: return "workspace too small";
+    case CR_ERR_CUDA: return "CUDA runtime error";
+    case CR_ERR_TIMEOUT: return "a bounded device-side wait or iteration limit expired";
+    case CR_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown error code";
+    }
+}
+
+}  // extern "C"

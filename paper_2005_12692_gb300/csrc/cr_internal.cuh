@@ -1,0 +1,181 @@
+// cr_internal.cuh -- internal declarations shared by the libcr translation units.
+//
+// Notation (Kaji, Sudo, Ahara, "Cubical Ripser", Sec. 2): a cube is
+// (x, y, z, m, d); its value is the maximum over its vertices (V-construction);
+// within one dimension cubes are totally ordered by the 64-bit key
+//     key = ord32(value) << 32 | (0xFFFFFFFF - L),  L = ((m*Nz+z)*Ny+y)*Nx+x,
+// where ord32 maps float bits to an unsigned integer with the same order
+// (Herf's radix-sort trick: flip all bits of negatives, set the sign bit of
+// non-negatives).  A smaller key enters the filtration earlier.  The tie part
+// puts larger L first, which is the reverse of the paper's (-birth, m, z, y, x)
+// order of Sec. 2.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <cstring>
+#include <atomic>
+#include <cuda_runtime.h>
+#include "../../include/cr.h"
+
+namespace cr {
+
+// ---------------------------------------------------------------------------
+// image segments (a single image is a batch of one)
+// ---------------------------------------------------------------------------
+struct Seg {
+    int64_t voff;  // first vertex of this image in the packed vertex space
+    int64_t loff;  // offset of this image's L-space (3 * voff) in L-indexed arrays
+    int64_t coff;  // first dual node (top cube) of this image; its outer node is coff + ncell
+    int64_t ncell; // number of top cubes of this image
+    int32_t nx, ny, nz;
+    int32_t edim;  // effective dimension (leading unit extents dropped), 0..3
+};
+
+// ---------------------------------------------------------------------------
+// keys
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t ord32(float f) {
+#ifdef __CUDA_ARCH__
+    uint32_t b = __float_as_uint(f);
+#else
+    uint32_t b;
+    memcpy(&b, &f, 4);
+#endif
+    if (b == 0x80000000u) b = 0u;  // -0.0 is +0.0
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__host__ __device__ __forceinline__ float unord32(uint32_t o) {
+    uint32_t b = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint64_t make_key(uint32_t ordv, uint32_t L) {
+    return ((uint64_t)ordv << 32) | (uint64_t)(0xFFFFFFFFu - L);
+}
+__host__ __device__ __forceinline__ uint32_t key_L(uint64_t k) { return 0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu); }
+__host__ __device__ __forceinline__ float key_value(uint64_t k) { return unord32((uint32_t)(k >> 32)); }
+
+// L index of a cube of type m anchored at (x, y, z)
+__host__ __device__ __forceinline__ uint32_t cube_L(const Seg &s, int m, int x, int y, int z) {
+    return (uint32_t)((((int64_t)m * s.nz + z) * s.ny + y) * s.nx + x);
+}
+
+// ---------------------------------------------------------------------------
+// status word (device int) -- first error wins
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
+
+// ---------------------------------------------------------------------------
+// workspace carving
+// ---------------------------------------------------------------------------
+struct Carver {
+    char *base;
+    size_t cap, used;
+    bool ok;
+    Carver(void *b, size_t c) : base((char *)b), cap(c), used(0), ok(true) {}
+    template <class T>
+    T *take(size_t n) {
+        size_t off = (used + 255) & ~(size_t)255;
+        size_t bytes = n * sizeof(T);
+        if (off + bytes > cap) { ok = false; used = off + bytes; return nullptr; }
+        used = off + bytes;
+        return base ? (T *)(base + off) : nullptr;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// pair record used inside the pipeline (before the final sort)
+// ---------------------------------------------------------------------------
+struct PairBuf {
+    cr_pair *pairs;     // capacity entries (the caller's output buffer)
+    int64_t capacity;
+    unsigned long long *count;  // device counter
+};
+
+// While the pipeline runs, bits 8..31 of cr_pair.flags hold the image index;
+// the final gather clears them.
+__device__ __forceinline__ void emit_pair(const PairBuf &pb, uint32_t seg, int dim, float birth, float death,
+                                          int64_t bcell, int64_t dcell, uint32_t flags) {
+    unsigned long long i = atomicAdd(pb.count, 1ull);
+    if ((int64_t)i < pb.capacity) {
+        cr_pair p;
+        p.dim = dim;
+        p.birth = birth;
+        p.death = death;
+        p.flags = (flags & 0xFFu) | (seg << 8);
+        p.birth_cell = bcell;
+        p.death_cell = dcell;
+        pb.pairs[i] = p;
+    }
+}
+
+// union-find buffers (cr_uf.cu)
+struct UF {
+    uint32_t *lab;   // node -> parent, then node -> group
+    uint8_t *dd;     // node -> stencil hook code (0 = root)
+    uint64_t *gkey;  // group -> age key of its root (smaller = older)
+    uint32_t *groot, *gseg;
+    uint8_t *gdead;
+    uint64_t *minE;
+    uint32_t *tgt, *hook;
+    uint64_t *ek[2];
+    uint32_t *ea[2], *eb[2];
+    int64_t max_edges, max_groups;
+    unsigned long long *cnt;   // device counters [0] groups, [1] edges, [2] edges after a round
+    unsigned long long *hcnt;  // host mirror
+};
+int run_h0(const float *img, const Seg *segs, int nseg, int64_t vtot, UF &u, const PairBuf &pb, uint32_t flags,
+           uint32_t *extra_mask, int *status, cudaStream_t st);
+int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, UF &u, const PairBuf &pb,
+             uint32_t flags, int *status, cudaStream_t st);
+
+// middle-dimension buffers (cr_h1.cu)
+struct H1Bufs {
+    uint64_t *colkey, *colkey_tmp;
+    uint32_t *colseg, *colseg_tmp;
+    int64_t max_cols;
+    void *sort_temp;
+    size_t sort_temp_bytes;
+    int *P;
+    int64_t P_len;
+    unsigned long long *cur;
+    uint64_t *arena;
+    int64_t arena_cap;
+    uint64_t *scratch;
+    int64_t nwarps;
+    int maxlen;
+    unsigned long long *cnt;  // [0] columns, [1] arena top, [2] work counter
+};
+int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, int nseg, int64_t vtot,
+           H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status, int64_t *ncols_out, cudaStream_t st);
+
+// radix sort of (u64 key, u32 value) by bits [lo, hi) of the key, stable, LSD.
+// tmp buffers must hold n entries each.  Returns cudaError.
+size_t radix_temp_bytes(int64_t n);
+cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp, uint32_t *vals_tmp, int64_t n,
+                           int lo, int hi, void *temp, size_t temp_bytes, cudaStream_t st);
+cudaError_t exclusive_scan_u32(uint32_t *a, int64_t n, uint32_t *part, cudaStream_t st);
+size_t scan_temp_bytes(int64_t n);
+
+// ---------------------------------------------------------------------------
+// launch accounting / stage timing (cr_prof.cu)
+// ---------------------------------------------------------------------------
+enum Stage {
+    STAGE_H0_STENCIL, STAGE_JUMP, STAGE_ROOTS, STAGE_RELABEL, STAGE_H0_CROSS, STAGE_UF_ROUND,
+    STAGE_DUAL_STENCIL, STAGE_DUAL_CROSS, STAGE_H1_SCAN, STAGE_H1_SORT, STAGE_H1_REDUCE, STAGE_H1_EMIT,
+    STAGE_OUT_SORT, STAGE_BW_CONTRIB, STAGE_BW_SORT, STAGE_BW_SUM, STAGE_COUNT
+};
+extern std::atomic<long long> g_launch_count;
+void prof_begin(cudaStream_t st, int stage);
+void prof_end(cudaStream_t st, int stage, double bytes);
+void prof_flush();
+#define CR_NOTE_LAUNCH() (::cr::g_launch_count.fetch_add(1, std::memory_order_relaxed))
+
+}  // namespace cr

@@ -1,0 +1,671 @@
+// cr_uf.cu -- 0-dimensional persistence by union-find (Sec. 2: "computed
+// efficiently by the union-find algorithm"; elder rule: the component with
+// the larger birth is killed) and the top dimension by union-find on the dual
+// graph in the reversed order (Sec. 2, Rem. 2.1, Alexander duality).
+//
+// Both are one algorithm on a graph whose nodes carry an age key (smaller =
+// older) and whose edges carry a key (smaller = earlier); node and edge keys
+// are unique.  The pairs are those of Kruskal's algorithm with the elder rule.
+// Parallel form used here (Boruvka rounds over groups of nodes):
+//   * every group G knows m(G), its minimum outgoing edge, and the group H at
+//     its other end;
+//   * if H's root is older than G's root, G's root dies at m(G), and G is
+//     contracted into H (the "safe hook");  when m(G) = m(H) (mutual), the
+//     younger root is the one that hooks, so mutual pairs are covered;
+//   * otherwise G waits for a later round.
+// Invariant that makes both rules exact: for every group and every edge e
+// leaving it at member x, the tree path from x to the group root uses only
+// edges smaller than e.  Hence, just before m(G), G's Kruskal component lies
+// inside G and contains its root, and H's contains H's root.
+//
+// Round 0 runs on the image itself without materialising any edge: a node's
+// minimum incident edge is found by a stencil, hooks become parent pointers,
+// pointer jumping yields basins, and only edges between different basins are
+// written out for the later rounds.
+#include "cr_internal.cuh"
+
+namespace cr {
+
+__device__ __forceinline__ int seg_of(const Seg *segs, int n, int64_t gv) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].voff <= gv) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int seg_of_node(const Seg *segs, int n, int64_t gc) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].coff <= gc) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// warp-aggregated append; every lane of the warp must call it
+__device__ __forceinline__ int64_t warp_append(bool pred, unsigned long long *counter) {
+    unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+    if (!mask) return -1;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (!pred) return -1;
+    return (int64_t)(base + __popc(mask & ((1u << lane) - 1u)));
+}
+
+// ===========================================================================
+// primal H0, round 0: each vertex's minimum incident edge
+// direction codes: 1 -x, 2 +x, 3 -y, 4 +y, 5 -z, 6 +z, 0 = no hook
+// ===========================================================================
+__global__ void k_h0_stencil(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t vtot,
+                             uint32_t *__restrict__ parent, uint8_t *__restrict__ dd, int *status, PairBuf pb,
+                             uint32_t flags) {
+    int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gv >= vtot) return;
+    const int si = seg_of(segs, nseg, gv);
+    const Seg S = segs[si];
+    int64_t lv = gv - S.voff;
+    int x = (int)(lv % S.nx);
+    int y = (int)((lv / S.nx) % S.ny);
+    int z = (int)(lv / ((int64_t)S.nx * S.ny));
+    float fv = img[gv];
+    if (isnan(fv)) set_status(status, CR_ERR_NAN);
+    uint32_t ov = ord32(fv);
+    uint64_t kv = make_key(ov, (uint32_t)lv);
+    uint64_t best = ~0ull;
+    int bestdir = 0;
+    uint32_t bestou = 0, bestlu = 0;
+    int64_t bestu = gv;
+#pragma unroll
+    for (int d = 0; d < 6; d++) {
+        int ax = d >> 1, sgn = (d & 1) ? 1 : -1;
+        int nxp = x + (ax == 0 ? sgn : 0), nyp = y + (ax == 1 ? sgn : 0), nzp = z + (ax == 2 ? sgn : 0);
+        if (nxp < 0 || nxp >= S.nx || nyp < 0 || nyp >= S.ny || nzp < 0 || nzp >= S.nz) continue;
+        int64_t du = ax == 0 ? 1 : (ax == 1 ? (int64_t)S.nx : (int64_t)S.nx * S.ny);
+        int64_t u = gv + sgn * du;
+        uint32_t ou = ord32(img[u]);
+        int axp = sgn > 0 ? x : nxp, ayp = sgn > 0 ? y : nyp, azp = sgn > 0 ? z : nzp;
+        uint64_t ek = make_key(ov > ou ? ov : ou, cube_L(S, ax, axp, ayp, azp));
+        if (ek < best) {
+            best = ek;
+            bestdir = d + 1;
+            bestu = u;
+            bestou = ou;
+            bestlu = (uint32_t)(lv + sgn * du);
+        }
+    }
+    if (bestdir && make_key(bestou, bestlu) < kv) {
+        parent[gv] = (uint32_t)bestu;
+        dd[gv] = (uint8_t)bestdir;
+        if (flags & CR_KEEP_ZERO)
+            emit_pair(pb, (uint32_t)si, 0, unord32(ov), key_value(best), lv, key_L(best), 0);
+    } else {
+        parent[gv] = (uint32_t)gv;
+        dd[gv] = 0;
+    }
+}
+
+// ===========================================================================
+// pointer jumping.  Pass 1 halves paths in place (every write stores an
+// ancestor, so the forest stays valid); pass 2 lets each node chase to its
+// root and write only its own entry, so no later write can replace a root by
+// a non-root ancestor.
+// ===========================================================================
+__global__ void k_halve(uint32_t *__restrict__ p, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t a = (uint32_t)i;
+    for (int it = 0; it < 64; it++) {
+        uint32_t b = p[a];
+        if (b == a) return;
+        uint32_t c = p[b];
+        if (c == b) return;
+        p[a] = c;
+        a = c;
+    }
+}
+
+__global__ void k_find_root(uint32_t *__restrict__ p, int64_t n, int *status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t a = p[i];
+    int64_t it = 0;
+    for (;;) {
+        uint32_t b = p[a];
+        if (b == a) break;
+        a = b;
+        if (++it > n) { set_status(status, CR_ERR_INTERNAL); return; }
+    }
+    p[i] = a;
+}
+
+// roots get a group id (kept in the label slot with the top bit set)
+__global__ void k_h0_roots(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t vtot,
+                           uint32_t *__restrict__ lab, unsigned long long *ngroups, int64_t max_groups,
+                           uint64_t *__restrict__ gkey, uint32_t *__restrict__ groot, uint32_t *__restrict__ gseg,
+                           int *status) {
+    int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool isroot = gv < vtot && lab[gv] == (uint32_t)gv;
+    int64_t g = warp_append(isroot, ngroups);
+    if (!isroot) return;
+    if (g >= max_groups) { set_status(status, CR_ERR_WORKSPACE); lab[gv] = 0x80000000u; return; }
+    int si = seg_of(segs, nseg, gv);
+    int64_t lv = gv - segs[si].voff;
+    gkey[g] = make_key(ord32(img[gv]), (uint32_t)lv);
+    groot[g] = (uint32_t)gv;
+    gseg[g] = (uint32_t)si;
+    lab[gv] = 0x80000000u | (uint32_t)g;
+}
+
+// label[v] <- group of its root
+__global__ void k_relabel(uint32_t *__restrict__ lab, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t a = lab[i];
+    if (a & 0x80000000u) return;  // a root: cleared in the second kernel
+    lab[i] = lab[a] & 0x7FFFFFFFu;
+}
+__global__ void k_unmark(uint32_t *__restrict__ lab, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    lab[i] &= 0x7FFFFFFFu;
+}
+
+// edges between different basins; an edge is a stencil (round-0) hook iff
+// one of its endpoints points at the other through it
+__global__ void k_h0_cross(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t vtot,
+                           const uint32_t *__restrict__ lab, const uint8_t *__restrict__ dd,
+                           uint64_t *__restrict__ ek, uint32_t *__restrict__ ea, uint32_t *__restrict__ eb,
+                           unsigned long long *ne, int64_t max_edges, const unsigned long long *ngroups,
+                           int *status) {
+    const uint32_t ng = (uint32_t)*ngroups;
+    int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool in = gv < vtot;
+    Seg S;
+    int64_t lv = 0;
+    int x = 0, y = 0, z = 0;
+    uint32_t ov = 0, la = 0;
+    if (in) {
+        S = segs[seg_of(segs, nseg, gv)];
+        lv = gv - S.voff;
+        x = (int)(lv % S.nx);
+        y = (int)((lv / S.nx) % S.ny);
+        z = (int)(lv / ((int64_t)S.nx * S.ny));
+        ov = ord32(img[gv]);
+        la = lab[gv];
+    }
+    for (int ax = 0; ax < 3; ax++) {
+        bool emit = false;
+        uint64_t key = 0;
+        uint32_t lb = 0;
+        if (in) {
+            int ext = ax == 0 ? S.nx : (ax == 1 ? S.ny : S.nz);
+            int c = ax == 0 ? x : (ax == 1 ? y : z);
+            if (c + 1 < ext) {
+                int64_t du = ax == 0 ? 1 : (ax == 1 ? (int64_t)S.nx : (int64_t)S.nx * S.ny);
+                int64_t u = gv + du;
+                bool stencil = dd[gv] == (uint8_t)(2 * ax + 2) || dd[u] == (uint8_t)(2 * ax + 1);
+                lb = lab[u];
+                if (!stencil && lb != la) {
+                    uint32_t ou = ord32(img[u]);
+                    key = make_key(ov > ou ? ov : ou, cube_L(S, ax, x, y, z));
+                    emit = true;
+                }
+            }
+        }
+        if (emit && (la >= ng || lb >= ng)) {
+            set_status(status, CR_ERR_INTERNAL);
+            emit = false;
+        }
+        int64_t i = warp_append(emit, ne);
+        if (emit) {
+            if (i < max_edges) {
+                ek[i] = key;
+                ea[i] = la;
+                eb[i] = lb;
+            } else {
+                set_status(status, CR_ERR_WORKSPACE);
+            }
+        }
+    }
+}
+
+// ===========================================================================
+// dual graph (top cubes + one outer node per image), reversed order
+// facet codes: 2D 1 -y, 2 +y, 3 -x, 4 +x;  3D 1 -z, 2 +z, 3 -y, 4 +y, 5 -x, 6 +x
+// ===========================================================================
+struct CellPos {
+    int x, y, z;
+};
+
+__device__ __forceinline__ CellPos cell_pos(const Seg &S, int64_t c) {
+    CellPos p;
+    int cx = S.nx - 1, cy = S.ny - 1;
+    p.x = (int)(c % cx);
+    p.y = (int)((c / cx) % cy);
+    p.z = S.edim == 3 ? (int)(c / ((int64_t)cx * cy)) : 0;
+    return p;
+}
+
+__device__ __forceinline__ int64_t cell_index(const Seg &S, int x, int y, int z) {
+    return ((int64_t)z * (S.ny - 1) + y) * (S.nx - 1) + x;
+}
+
+__device__ __forceinline__ uint32_t vmax_ord(const float *img, const Seg &S, int x, int y, int z, int sx, int sy,
+                                             int sz) {
+    uint32_t m = 0;
+    for (int dz = 0; dz <= sz; dz++)
+        for (int dy = 0; dy <= sy; dy++)
+            for (int dx = 0; dx <= sx; dx++) {
+                uint32_t o = ord32(img[S.voff + ((int64_t)(z + dz) * S.ny + (y + dy)) * S.nx + (x + dx)]);
+                m = o > m ? o : m;
+            }
+    return m;
+}
+
+// key of a top cube
+__device__ __forceinline__ uint64_t top_key(const float *img, const Seg &S, int x, int y, int z) {
+    if (S.edim == 3) return make_key(vmax_ord(img, S, x, y, z, 1, 1, 1), cube_L(S, 0, x, y, z));
+    return make_key(vmax_ord(img, S, x, y, 0, 1, 1, 0), cube_L(S, 0, x, y, 0));
+}
+
+// facet f (0-based code) of the top cube at (x,y,z): its key and the cube on the other side
+__device__ __forceinline__ uint64_t facet_key(const float *img, const Seg &S, int x, int y, int z, int f, int &ox,
+                                              int &oy, int &oz) {
+    ox = x; oy = y; oz = z;
+    if (S.edim == 2) {
+        // 0: x-edge at (x,y) [-y], 1: x-edge at (x,y+1) [+y], 2: y-edge at (x,y) [-x], 3: y-edge at (x+1,y) [+x]
+        if (f < 2) {
+            int yy = y + f;
+            oy = f ? y + 1 : y - 1;
+            return make_key(vmax_ord(img, S, x, yy, 0, 1, 0, 0), cube_L(S, 0, x, yy, 0));
+        }
+        int xx = x + (f - 2);
+        ox = (f - 2) ? x + 1 : x - 1;
+        return make_key(vmax_ord(img, S, xx, y, 0, 0, 1, 0), cube_L(S, 1, xx, y, 0));
+    }
+    // 3D: 0/1 face {x,y} (m=0) at z / z+1; 2/3 face {x,z} (m=1) at y / y+1; 4/5 face {y,z} (m=2) at x / x+1
+    int ax = 2 - (f >> 1);  // 0,1 -> z(2); 2,3 -> y(1); 4,5 -> x(0)
+    int up = f & 1;
+    int ax_x = x, ax_y = y, ax_z = z;
+    if (ax == 2) { ax_z += up; oz = up ? z + 1 : z - 1; return make_key(vmax_ord(img, S, ax_x, ax_y, ax_z, 1, 1, 0), cube_L(S, 0, ax_x, ax_y, ax_z)); }
+    if (ax == 1) { ax_y += up; oy = up ? y + 1 : y - 1; return make_key(vmax_ord(img, S, ax_x, ax_y, ax_z, 1, 0, 1), cube_L(S, 1, ax_x, ax_y, ax_z)); }
+    ax_x += up; ox = up ? x + 1 : x - 1;
+    return make_key(vmax_ord(img, S, ax_x, ax_y, ax_z, 0, 1, 1), cube_L(S, 2, ax_x, ax_y, ax_z));
+}
+
+__device__ __forceinline__ bool cell_in(const Seg &S, int x, int y, int z) {
+    if (x < 0 || y < 0 || z < 0 || x >= S.nx - 1 || y >= S.ny - 1) return false;
+    if (S.edim == 3) return z < S.nz - 1;
+    return z == 0;
+}
+
+__global__ void k_dual_stencil(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t ctot,
+                               uint32_t *__restrict__ parent, uint8_t *__restrict__ dd, PairBuf pb, uint32_t flags) {
+    int64_t gc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gc >= ctot) return;
+    int si = seg_of_node(segs, nseg, gc);
+    const Seg S = segs[si];
+    int64_t c = gc - S.coff;
+    if (c >= S.ncell) {  // the outer node
+        parent[gc] = (uint32_t)gc;
+        dd[gc] = 0;
+        return;
+    }
+    CellPos p = cell_pos(S, c);
+    uint64_t kc = top_key(img, S, p.x, p.y, p.z);
+    int nf = S.edim == 3 ? 6 : 4;
+    uint64_t best = 0;
+    int bf = -1, bx = 0, by = 0, bz = 0;
+    for (int f = 0; f < nf; f++) {
+        int ox, oy, oz;
+        uint64_t fk = facet_key(img, S, p.x, p.y, p.z, f, ox, oy, oz);
+        if (bf < 0 || fk > best) { best = fk; bf = f; bx = ox; by = oy; bz = oz; }
+    }
+    bool hook;
+    int64_t other;
+    if (!cell_in(S, bx, by, bz)) {
+        hook = true;  // the outer node is the oldest
+        other = S.coff + S.ncell;
+    } else {
+        uint64_t ko = top_key(img, S, bx, by, bz);
+        hook = ko > kc;  // larger key = older in the reversed order
+        other = S.coff + cell_index(S, bx, by, bz);
+    }
+    if (hook) {
+        parent[gc] = (uint32_t)other;
+        dd[gc] = (uint8_t)(bf + 1);
+        if (flags & CR_KEEP_ZERO)
+            emit_pair(pb, (uint32_t)si, S.edim - 1, key_value(best), key_value(kc), key_L(best), key_L(kc), 0);
+    } else {
+        parent[gc] = (uint32_t)gc;
+        dd[gc] = 0;
+    }
+}
+
+__global__ void k_dual_roots(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t ctot,
+                             uint32_t *__restrict__ lab, unsigned long long *ngroups, int64_t max_groups,
+                             uint64_t *__restrict__ gkey, uint32_t *__restrict__ groot, uint32_t *__restrict__ gseg,
+                             int *status) {
+    int64_t gc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool isroot = gc < ctot && lab[gc] == (uint32_t)gc;
+    int64_t g = warp_append(isroot, ngroups);
+    if (!isroot) return;
+    if (g >= max_groups) { set_status(status, CR_ERR_WORKSPACE); lab[gc] = 0x80000000u; return; }
+    int si = seg_of_node(segs, nseg, gc);
+    const Seg S = segs[si];
+    int64_t c = gc - S.coff;
+    uint64_t age = 0;  // outer node: oldest
+    if (c < S.ncell) {
+        CellPos p = cell_pos(S, c);
+        age = ~top_key(img, S, p.x, p.y, p.z);
+    }
+    gkey[g] = age;
+    groot[g] = (uint32_t)gc;
+    gseg[g] = (uint32_t)si;
+    lab[gc] = 0x80000000u | (uint32_t)g;
+}
+
+// dual edges = facets of the top cubes, iterated over the L-space of type m
+__global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t vtot,
+                             const uint32_t *__restrict__ lab, const uint8_t *__restrict__ dd,
+                             uint64_t *__restrict__ ek, uint32_t *__restrict__ ea, uint32_t *__restrict__ eb,
+                             unsigned long long *ne, int64_t max_edges, const unsigned long long *ngroups,
+                             int *status) {
+    const uint32_t ng = (uint32_t)*ngroups;
+    int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool in = gv < vtot;
+    Seg S;
+    int x = 0, y = 0, z = 0;
+    if (in) {
+        S = segs[seg_of(segs, nseg, gv)];
+        if (S.ncell == 0) in = false;
+        int64_t lv = gv - S.voff;
+        x = (int)(lv % S.nx);
+        y = (int)((lv / S.nx) % S.ny);
+        z = (int)(lv / ((int64_t)S.nx * S.ny));
+    }
+    for (int m = 0; m < 3; m++) {
+        bool emit = false;
+        uint64_t key = 0;
+        uint32_t la = 0, lb = 0;
+        if (in && (S.edim == 3 || m < 2)) {
+            // the two sides (a = "minus" side cube, b = "plus" side cube) and the facet code on each side
+            int ax, ay, az, bx = x, by = y, bz = z, fa, fb;
+            bool exists;
+            uint64_t fk = 0;
+            if (S.edim == 2) {
+                if (m == 0) {  // x-edge at (x,y)
+                    exists = x + 1 < S.nx;
+                    ax = x; ay = y - 1; az = 0; fa = 1; fb = 0;
+                    if (exists) fk = make_key(vmax_ord(img, S, x, y, 0, 1, 0, 0), cube_L(S, 0, x, y, 0));
+                } else {  // y-edge at (x,y)
+                    exists = y + 1 < S.ny;
+                    ax = x - 1; ay = y; az = 0; fa = 3; fb = 2;
+                    if (exists) fk = make_key(vmax_ord(img, S, x, y, 0, 0, 1, 0), cube_L(S, 1, x, y, 0));
+                }
+            } else {
+                if (m == 0) {  // face {x,y}
+                    exists = x + 1 < S.nx && y + 1 < S.ny;
+                    ax = x; ay = y; az = z - 1; fa = 1; fb = 0;
+                    if (exists) fk = make_key(vmax_ord(img, S, x, y, z, 1, 1, 0), cube_L(S, 0, x, y, z));
+                } else if (m == 1) {  // face {x,z}
+                    exists = x + 1 < S.nx && z + 1 < S.nz;
+                    ax = x; ay = y - 1; az = z; fa = 3; fb = 2;
+                    if (exists) fk = make_key(vmax_ord(img, S, x, y, z, 1, 0, 1), cube_L(S, 1, x, y, z));
+                } else {  // face {y,z}
+                    exists = y + 1 < S.ny && z + 1 < S.nz;
+                    ax = x - 1; ay = y; az = z; fa = 5; fb = 4;
+                    if (exists) fk = make_key(vmax_ord(img, S, x, y, z, 0, 1, 1), cube_L(S, 2, x, y, z));
+                }
+            }
+            if (exists) {
+                int64_t outer = S.coff + S.ncell;
+                bool ina = cell_in(S, ax, ay, az), inb = cell_in(S, bx, by, bz);
+                int64_t na = ina ? S.coff + cell_index(S, ax, ay, az) : outer;
+                int64_t nb = inb ? S.coff + cell_index(S, bx, by, bz) : outer;
+                bool stencil = (ina && dd[na] == (uint8_t)(fa + 1)) || (inb && dd[nb] == (uint8_t)(fb + 1));
+                if (!stencil) {
+                    la = lab[na];
+                    lb = lab[nb];
+                    if (la != lb) {
+                        emit = true;
+                        key = ~fk;
+                    }
+                }
+            }
+        }
+        if (emit && (la >= ng || lb >= ng)) {
+            set_status(status, CR_ERR_INTERNAL);
+            emit = false;
+        }
+        int64_t i = warp_append(emit, ne);
+        if (emit) {
+            if (i < max_edges) {
+                ek[i] = key;
+                ea[i] = la;
+                eb[i] = lb;
+            } else {
+                set_status(status, CR_ERR_WORKSPACE);
+            }
+        }
+    }
+}
+
+// ===========================================================================
+// Boruvka rounds with the elder rule
+// ===========================================================================
+__global__ void k_be_init(uint64_t *__restrict__ minE, int64_t ng) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng) minE[g] = ~0ull;
+}
+
+__global__ void k_be_min(const uint64_t *__restrict__ ek, const uint32_t *__restrict__ ea,
+                         const uint32_t *__restrict__ eb, int64_t ne, unsigned long long *__restrict__ minE) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    unsigned long long k = ek[i];
+    uint32_t a = ea[i], b = eb[i];
+    if (minE[a] > k) atomicMin(&minE[a], k);
+    if (minE[b] > k) atomicMin(&minE[b], k);
+}
+
+__global__ void k_be_tgt(const uint64_t *__restrict__ ek, const uint32_t *__restrict__ ea,
+                         const uint32_t *__restrict__ eb, int64_t ne, const uint64_t *__restrict__ minE,
+                         uint32_t *__restrict__ tgt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    uint64_t k = ek[i];
+    uint32_t a = ea[i], b = eb[i];
+    if (minE[a] == k) tgt[a] = b;
+    if (minE[b] == k) tgt[b] = a;
+}
+
+// mode 0: primal (dim 0 pairs; mark dying edges in extra_mask);
+// mode 1: dual (pairs of dimension edim-1 between a facet and a top cube)
+__global__ void k_be_hook(int64_t ng, const uint64_t *__restrict__ minE, const uint32_t *__restrict__ tgt,
+                          const uint64_t *__restrict__ gkey, const uint32_t *__restrict__ gseg,
+                          uint32_t *__restrict__ hook, uint8_t *__restrict__ gdead, const Seg *__restrict__ segs,
+                          int mode, PairBuf pb, uint32_t flags, uint32_t *__restrict__ extra_mask) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    uint64_t m = minE[g];
+    if (m == ~0ull) { hook[g] = (uint32_t)g; return; }
+    uint32_t t = tgt[g];
+    if (gkey[t] < gkey[g]) {
+        hook[g] = t;
+        gdead[g] = 1;
+        uint32_t si = gseg[g];
+        if (mode == 0) {
+            uint64_t kb = gkey[g];
+            float b = key_value(kb), d = key_value(m);
+            if ((flags & CR_KEEP_ZERO) || b != d) emit_pair(pb, si, 0, b, d, key_L(kb), key_L(m), 0);
+            if (extra_mask) {
+                int64_t bit = segs[si].loff + key_L(m);
+                atomicOr(&extra_mask[bit >> 5], 1u << (bit & 31));
+            }
+        } else {
+            uint64_t kf = ~m, kc = ~gkey[g];
+            float b = key_value(kf), d = key_value(kc);
+            if ((flags & CR_KEEP_ZERO) || b != d)
+                emit_pair(pb, si, segs[si].edim - 1, b, d, key_L(kf), key_L(kc), 0);
+        }
+    } else {
+        hook[g] = (uint32_t)g;
+    }
+}
+
+__global__ void k_be_jump(uint32_t *__restrict__ hook, int64_t ng) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    uint32_t a = (uint32_t)g, b = hook[a];
+    int it = 0;
+    while (b != a && it++ < (1 << 24)) {
+        a = b;
+        b = hook[a];
+    }
+    hook[g] = a;
+}
+
+__global__ void k_be_relabel(const uint64_t *__restrict__ ek, const uint32_t *__restrict__ ea,
+                             const uint32_t *__restrict__ eb, int64_t ne, const uint32_t *__restrict__ hook,
+                             uint64_t *__restrict__ ok, uint32_t *__restrict__ oa, uint32_t *__restrict__ ob,
+                             unsigned long long *nout) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool keep = false;
+    uint32_t a = 0, b = 0;
+    uint64_t k = 0;
+    if (i < ne) {
+        a = hook[ea[i]];
+        b = hook[eb[i]];
+        k = ek[i];
+        keep = a != b;
+    }
+    int64_t j = warp_append(keep, nout);
+    if (keep) {
+        ok[j] = k;
+        oa[j] = a;
+        ob[j] = b;
+    }
+}
+
+// essential class of each image: the group that never died (primal only)
+__global__ void k_h0_essential(int64_t ng, const uint8_t *__restrict__ gdead, const uint64_t *__restrict__ gkey,
+                               const uint32_t *__restrict__ gseg, PairBuf pb) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng || gdead[g]) return;
+    uint64_t k = gkey[g];
+    emit_pair(pb, gseg[g], 0, key_value(k), __int_as_float(0x7f800000), key_L(k), -1, CR_PAIR_ESSENTIAL);
+}
+
+// ===========================================================================
+// host drivers
+// ===========================================================================
+
+static inline unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+static int rounds_loop(UF &u, int64_t ng, int64_t ne, const Seg *segs, int mode, const PairBuf &pb,
+                       uint32_t flags, uint32_t *extra_mask, int *status, cudaStream_t st) {
+    int cur = 0;
+    int rounds = 0;
+    cudaMemsetAsync(u.gdead, 0, (size_t)ng, st);
+    while (ne > 0) {
+        if (++rounds > 100000) return CR_ERR_TIMEOUT;
+        prof_begin(st, STAGE_UF_ROUND);
+        CR_NOTE_LAUNCH();
+        k_be_init<<<nb(ng), 256, 0, st>>>(u.minE, ng);
+        CR_NOTE_LAUNCH();
+        k_be_min<<<nb(ne), 256, 0, st>>>(u.ek[cur], u.ea[cur], u.eb[cur], ne, (unsigned long long *)u.minE);
+        CR_NOTE_LAUNCH();
+        k_be_tgt<<<nb(ne), 256, 0, st>>>(u.ek[cur], u.ea[cur], u.eb[cur], ne, u.minE, u.tgt);
+        CR_NOTE_LAUNCH();
+        k_be_hook<<<nb(ng), 256, 0, st>>>(ng, u.minE, u.tgt, u.gkey, u.gseg, u.hook, u.gdead, segs, mode, pb, flags,
+                                          extra_mask);
+        CR_NOTE_LAUNCH();
+        k_be_jump<<<nb(ng), 256, 0, st>>>(u.hook, ng);
+        cudaMemsetAsync(&u.cnt[2], 0, sizeof(unsigned long long), st);
+        CR_NOTE_LAUNCH();
+        k_be_relabel<<<nb(ne), 256, 0, st>>>(u.ek[cur], u.ea[cur], u.eb[cur], ne, u.hook, u.ek[cur ^ 1],
+                                             u.ea[cur ^ 1], u.eb[cur ^ 1], &u.cnt[2]);
+        prof_end(st, STAGE_UF_ROUND, 3.0 * 16.0 * ne + 40.0 * ng);
+        cudaMemcpyAsync(&u.hcnt[2], &u.cnt[2], sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
+        ne = (int64_t)u.hcnt[2];
+        cur ^= 1;
+    }
+    return CR_OK;
+}
+
+int run_h0(const float *img, const Seg *segs, int nseg, int64_t vtot, UF &u, const PairBuf &pb, uint32_t flags,
+           uint32_t *extra_mask, int *status, cudaStream_t st) {
+    cudaMemsetAsync(u.cnt, 0, 3 * sizeof(unsigned long long), st);
+    prof_begin(st, STAGE_H0_STENCIL);
+    CR_NOTE_LAUNCH();
+    k_h0_stencil<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, u.dd, status, pb, flags);
+    prof_end(st, STAGE_H0_STENCIL, 9.0 * vtot);
+    prof_begin(st, STAGE_JUMP);
+    CR_NOTE_LAUNCH();
+    k_halve<<<nb(vtot), 256, 0, st>>>(u.lab, vtot);
+    CR_NOTE_LAUNCH();
+    k_find_root<<<nb(vtot), 256, 0, st>>>(u.lab, vtot, status);
+    prof_end(st, STAGE_JUMP, 8.0 * vtot);
+    CR_NOTE_LAUNCH();
+    k_h0_roots<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, &u.cnt[0], u.max_groups, u.gkey, u.groot,
+                                         u.gseg, status);
+    CR_NOTE_LAUNCH();
+    k_relabel<<<nb(vtot), 256, 0, st>>>(u.lab, vtot);
+    CR_NOTE_LAUNCH();
+    k_unmark<<<nb(vtot), 256, 0, st>>>(u.lab, vtot);
+    prof_begin(st, STAGE_H0_CROSS);
+    CR_NOTE_LAUNCH();
+    k_h0_cross<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, u.dd, u.ek[0], u.ea[0], u.eb[0], &u.cnt[1],
+                                         u.max_edges, &u.cnt[0], status);
+    prof_end(st, STAGE_H0_CROSS, 9.0 * vtot);
+    cudaMemcpyAsync(u.hcnt, u.cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
+    int64_t ng = (int64_t)u.hcnt[0], ne = (int64_t)u.hcnt[1];
+    if (ng > u.max_groups || ne > u.max_edges) return CR_ERR_WORKSPACE;
+    int rc = rounds_loop(u, ng, ne, segs, 0, pb, flags, extra_mask, status, st);
+    if (rc) return rc;
+    CR_NOTE_LAUNCH();
+    k_h0_essential<<<nb(ng), 256, 0, st>>>(ng, u.gdead, u.gkey, u.gseg, pb);
+    return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+}
+
+int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, UF &u, const PairBuf &pb,
+             uint32_t flags, int *status, cudaStream_t st) {
+    cudaMemsetAsync(u.cnt, 0, 3 * sizeof(unsigned long long), st);
+    prof_begin(st, STAGE_DUAL_STENCIL);
+    CR_NOTE_LAUNCH();
+    k_dual_stencil<<<nb(ctot), 256, 0, st>>>(img, segs, nseg, ctot, u.lab, u.dd, pb, flags);
+    prof_end(st, STAGE_DUAL_STENCIL, 4.0 * vtot + 5.0 * ctot);
+    prof_begin(st, STAGE_JUMP);
+    CR_NOTE_LAUNCH();
+    k_halve<<<nb(ctot), 256, 0, st>>>(u.lab, ctot);
+    CR_NOTE_LAUNCH();
+    k_find_root<<<nb(ctot), 256, 0, st>>>(u.lab, ctot, status);
+    prof_end(st, STAGE_JUMP, 8.0 * ctot);
+    CR_NOTE_LAUNCH();
+    k_dual_roots<<<nb(ctot), 256, 0, st>>>(img, segs, nseg, ctot, u.lab, &u.cnt[0], u.max_groups, u.gkey, u.groot,
+                                           u.gseg, status);
+    CR_NOTE_LAUNCH();
+    k_relabel<<<nb(ctot), 256, 0, st>>>(u.lab, ctot);
+    CR_NOTE_LAUNCH();
+    k_unmark<<<nb(ctot), 256, 0, st>>>(u.lab, ctot);
+    prof_begin(st, STAGE_DUAL_CROSS);
+    CR_NOTE_LAUNCH();
+    k_dual_cross<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, u.dd, u.ek[0], u.ea[0], u.eb[0], &u.cnt[1],
+                                           u.max_edges, &u.cnt[0], status);
+    prof_end(st, STAGE_DUAL_CROSS, 4.0 * vtot + 5.0 * ctot);
+    cudaMemcpyAsync(u.hcnt, u.cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
+    int64_t ng = (int64_t)u.hcnt[0], ne = (int64_t)u.hcnt[1];
+    if (ng > u.max_groups || ne > u.max_edges) return CR_ERR_WORKSPACE;
+    return rounds_loop(u, ng, ne, segs, 1, pb, flags, nullptr, status, st);
+}
+
+}  // namespace cr
