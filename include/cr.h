@@ -160,6 +160,34 @@ int cr_backward_batched(const float *imgs, const int64_t *img_offsets, const int
 int cr_cell_location(int64_t L, int dim, int ndim, const int64_t *shape, int *m, int64_t *x, int64_t *y,
                      int64_t *z);
 
+/*
+ * cr_persistence_noalloc -- cr_persistence for callers that cannot allocate
+ * device memory.  (The paper has no counterpart; this is a deployment
+ * convenience.)  Some callers cannot call cudaMalloc: code running inside a
+ * host framework's fixed device-memory pool (inference plugins, embedded
+ * hosts) where an allocation would break the host's memory accounting or
+ * synchronise the device at a forbidden point.  They still pass their input
+ * and output buffers; the workspace is a file-scope static device array of
+ * CR_NOALLOC_SCRATCH_BYTES, reserved when the library is loaded and held by
+ * every GPU that loads it until the process exits.  The call itself makes no
+ * cudaMalloc, cudaFree or other allocating call.
+ *   - Serves 1D and 2D images (a 3D array is accepted only with a leading
+ *     extent of 1) whose cr_workspace_size bound fits the array (about
+ *     490,000 pixels, e.g. 512x512 with maxdim 1); larger inputs return
+ *     CR_ERR_TOO_LARGE, volumes CR_ERR_INVALID_ARG, before any GPU work.
+ *   - The first call on a device resolves the array's device address with
+ *     cudaGetSymbolAddress while that device is current; make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one array, which keeps the contents of
+ *     the last call; the call clears everything it relies on being zero.
+ *     Calls that overlap on the GPU (other streams, other host threads) race
+ *     on the array: serialise them.
+ * Arguments and results are those of cr_persistence without ws/ws_bytes.
+ */
+#define CR_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int cr_persistence_noalloc(const float *img, int ndim, const int64_t *shape, int maxdim, cr_pair *pairs_out,
+                           int64_t capacity, int64_t *n_pairs, cr_stream_t stream, uint32_t flags);
+
 /* Diagnostics for benchmarks.  With profiling on, every stage of a call is
  * bracketed by CUDA events recorded on the caller's stream; totals per stage
  * are read with cr_profile_read (stage 0..15; name, total milliseconds,
