@@ -198,9 +198,18 @@ int cr_profile_enable(int on);
 void cr_profile_reset(void);
 int cr_profile_read(int stage, const char **name, double *total_ms, int64_t *count, double *bytes);
 int64_t cr_launch_count(void);
+/* Counters of the last 3D reduction on this process (out[0..n)): residual
+ * columns, loop iterations, apparent-column additions, column additions,
+ * merged entries, pivot takeovers, lost races and stale reads, long-column
+ * buffer growths, most iterations spent on one column.  Host-only. */
+int cr_h1_last_stats(int64_t *out, int n);
 
 /* Static description of an error code. */
 const char *cr_error_string(int code);
+
+/* After CR_ERR_WORKSPACE on this host thread: the name of the buffer that
+ * was too small ("" if none).  Host-only. */
+const char *cr_last_error_detail(void);
 
 #ifdef __cplusplus
 }

@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
         L.cr_profile_read.restype = ctypes.c_int
         L.cr_launch_count.argtypes = []
         L.cr_launch_count.restype = ctypes.c_int64
+        L.cr_last_error_detail.restype = ctypes.c_char_p
+        L.cr_last_error_detail.argtypes = []
         L.cr_error_string.restype = ctypes.c_char_p
         L.cr_error_string.argtypes = [ctypes.c_int]
         for f in ("cr_workspace_size", "cr_workspace_size_typical", "cr_workspace_size_batched",
@@ -104,7 +106,10 @@ def lib() -> ctypes.CDLL:
 
 def _check(rc: int):
     if rc != CR_OK:
-        raise CRError(rc, lib().cr_error_string(rc).decode())
+        msg = lib().cr_error_string(rc).decode()
+        if rc == CR_ERR_WORKSPACE:
+            msg += " (" + lib().cr_last_error_detail().decode() + ")"
+        raise CRError(rc, msg)
 
 
 def error_string(code: int) -> str:

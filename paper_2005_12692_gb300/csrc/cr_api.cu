@@ -14,6 +14,9 @@
 
 namespace cr {
 
+static thread_local int g_detail = 0;
+void set_host_detail(int site) { g_detail = site; }
+
 // ---------------------------------------------------------------------------
 // planning
 // ---------------------------------------------------------------------------
@@ -94,7 +97,7 @@ static int plan_images(const int64_t *const *shapes_rows, int n, int ndim, int m
 static void red_geometry(const HostPlan &P, int64_t &nwarps, int &maxlen) {
     nwarps = (int64_t)num_sms() * 16;
     int64_t ml = P.max_face_per_image + 32;
-    if (ml > 32768) ml = 32768;
+    if (ml > 4096) ml = 4096;  // longer columns move to buffers grown from the pool
     maxlen = (int)((ml + 31) & ~31);
 }
 
@@ -129,8 +132,10 @@ static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
         red_geometry(P, nw, ml);
         int64_t cols = worst ? 3 * P.vtot : (3 * P.vtot) / 8 + 4096;
         int64_t arena = worst ? 12 * P.vtot : 2 * P.vtot + (1 << 20);
+        int64_t pool = worst ? 8 * P.vtot : P.vtot + (1 << 20);
         h1 = al((size_t)cols * 32) + al(radix_temp_bytes(cols)) + al((size_t)(3 * P.vtot) * 4) +
-             al((size_t)arena * 8) + al((size_t)nw * 2 * ml * 8) + (1 << 20);
+             al((size_t)((3 * P.vtot + 31) / 32) * 4) +
+             al((size_t)arena * 8) + al((size_t)pool * 8) + al((size_t)nw * 2 * ml * 8) + (1 << 20);
     }
     int64_t maxpairs = (flags & CR_KEEP_ZERO) ? P.cells / 2 + (int64_t)P.segs.size() + 16
                                               : (worst ? P.cells / 2 + (int64_t)P.segs.size() + 16
@@ -188,8 +193,9 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
                     int64_t *pair_offsets, int64_t *n_pairs, void *ws, size_t ws_bytes, cudaStream_t st) {
     (void)maxdim;
     const int n = (int)P.segs.size();
+    g_detail = 0;
     size_t need_min = fixed_bytes(P) + 1024;
-    if (!ws || ws_bytes < need_min) return CR_ERR_WORKSPACE;
+    if (!ws || ws_bytes < need_min) { g_detail = SITE_FIXED; return CR_ERR_WORKSPACE; }
     Carver C(ws, ws_bytes);
     Seg *segs = C.take<Seg>(n);
     unsigned long long *cnt = C.take<unsigned long long>(64);
@@ -230,7 +236,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         int64_t max_groups = P.vtot;
         size_t gbytes = (size_t)max_groups * 33 + 6 * 256;
         if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 33) - 64;
-        if (max_groups < 1) return CR_ERR_WORKSPACE;
+        if (max_groups < 1) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
         u.gkey = R.take<uint64_t>(max_groups);
         u.minE = R.take<uint64_t>(max_groups);
         u.groot = R.take<uint32_t>(max_groups);
@@ -242,7 +248,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         size_t left = R.cap > R.used ? R.cap - R.used : 0;
         int64_t max_edges = (int64_t)(left / 32) - 64;
         if (max_edges > 3 * P.vtot + 1) max_edges = 3 * P.vtot + 1;
-        if (max_edges < 1 || !R.ok) return CR_ERR_WORKSPACE;
+        if (max_edges < 1 || !R.ok) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
         for (int b = 0; b < 2; b++) {
             u.ek[b] = R.take<uint64_t>(max_edges);
             u.ea[b] = R.take<uint32_t>(max_edges);
@@ -265,6 +271,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         B.maxlen = ml;
         B.P_len = 3 * P.vtot;
         B.P = R.take<int>(B.P_len);
+        B.appmask = R.take<uint32_t>((3 * P.vtot + 31) / 32);
         B.scratch = R.take<uint64_t>((size_t)nw * 2 * ml);
         B.cnt = &cnt[16];
         if (!R.ok) return CR_ERR_WORKSPACE;
@@ -272,7 +279,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         // columns (32 B each + sort temp) get up to half of what is left, the arena the rest
         int64_t max_cols = (int64_t)((left / 2) / 40) - 1024;
         if (max_cols > 3 * P.vtot + 1) max_cols = 3 * P.vtot + 1;
-        if (max_cols < 1) return CR_ERR_WORKSPACE;
+        if (max_cols < 1) { g_detail = SITE_H1_CARVE; return CR_ERR_WORKSPACE; }
         B.colkey = R.take<uint64_t>(max_cols);
         B.colkey_tmp = R.take<uint64_t>(max_cols);
         B.colseg = R.take<uint32_t>(max_cols);
@@ -283,9 +290,14 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         B.max_cols = max_cols;
         if (!R.ok) return CR_ERR_WORKSPACE;
         left = R.cap - R.used;
-        B.arena_cap = (int64_t)(left / 8) - 64;
-        if (B.arena_cap < 64) return CR_ERR_WORKSPACE;
+        // the rest: 60% arena of published columns, 40% pool for long columns
+        B.arena_cap = (int64_t)((left / 8) * 3 / 5) - 64;
+        if (B.arena_cap < 64) { set_host_detail(SITE_H1_CARVE); return CR_ERR_WORKSPACE; }
         B.arena = R.take<uint64_t>(B.arena_cap);
+        left = R.cap > R.used ? R.cap - R.used : 0;
+        B.pool_cap = (int64_t)(left / 8) - 64;
+        if (B.pool_cap < 64) { set_host_detail(SITE_H1_CARVE); return CR_ERR_WORKSPACE; }
+        B.pool = R.take<uint64_t>(B.pool_cap);
         int64_t ncols = 0;
         rc = run_h1(imgs, dd, extra, segs, n, P.vtot, B, pb, flags, status, &ncols, st);
         if (rc) return rc;
@@ -297,12 +309,12 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         UF u;
         u.lab = lab;
         u.dd = ddc;
-        u.cnt = &cnt[24];
+        u.cnt = &cnt[48];
         u.hcnt = hc;
         int64_t max_groups = P.ctot;
         size_t gbytes = (size_t)max_groups * 33 + 6 * 256;
         if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 33) - 64;
-        if (max_groups < 1) return CR_ERR_WORKSPACE;
+        if (max_groups < 1) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
         u.gkey = R.take<uint64_t>(max_groups);
         u.minE = R.take<uint64_t>(max_groups);
         u.groot = R.take<uint32_t>(max_groups);
@@ -314,7 +326,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         size_t left = R.cap > R.used ? R.cap - R.used : 0;
         int64_t max_edges = (int64_t)(left / 32) - 64;
         if (max_edges > 3 * P.vtot + 1) max_edges = 3 * P.vtot + 1;
-        if (max_edges < 1 || !R.ok) return CR_ERR_WORKSPACE;
+        if (max_edges < 1 || !R.ok) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
         for (int b = 0; b < 2; b++) {
             u.ek[b] = R.take<uint64_t>(max_edges);
             u.ea[b] = R.take<uint32_t>(max_edges);
@@ -327,11 +339,14 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     }
 
     // ---- count, status ----
-    int hstatus = 0;
+    int hstatus[16] = {0};
     cudaMemcpyAsync(hc, pair_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hstatus, status, 16 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
-    if (hstatus) return hstatus;
+    if (hstatus[0]) {
+        g_detail = hstatus[8];
+        return hstatus[0];
+    }
     int64_t np = (int64_t)hc[0];
     *n_pairs = np;
     if (np > capacity) return CR_ERR_CAPACITY;
@@ -346,7 +361,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         void *rtemp = R.take<char>(rt);
         uint32_t *segc = R.take<uint32_t>(n + 1);
         uint32_t *part = R.take<uint32_t>(scan_temp_bytes(n + 1) / 4 + 1);
-        if (!R.ok) return CR_ERR_WORKSPACE;
+        if (!R.ok) { g_detail = SITE_OUT_CARVE; return CR_ERR_WORKSPACE; }
         if (np > 0) {
             prof_begin(st, STAGE_OUT_SORT);
             if (pair_offsets) cudaMemsetAsync(segc, 0, (n + 1) * sizeof(uint32_t), st);
@@ -635,6 +650,27 @@ int cr_cell_location(int64_t L, int dim, int ndim, const int64_t *shape, int *m,
     int maxm = (dim == 1 || dim == 2) ? 2 : 0;
     if (*m > maxm) return CR_ERR_INVALID_ARG;
     return CR_OK;
+}
+
+int cr_h1_last_stats(int64_t *out, int n) {
+    if (!out || n < 1) return CR_ERR_INVALID_ARG;
+    return cr::h1_stats(out, n);
+}
+
+const char *cr_last_error_detail(void) {
+    switch (cr::g_detail) {
+    case cr::SITE_NONE: return "";
+    case cr::SITE_GROUPS: return "union-find groups";
+    case cr::SITE_EDGES: return "cross-basin edge list";
+    case cr::SITE_COLUMNS: return "residual column list";
+    case cr::SITE_ARENA: return "column arena";
+    case cr::SITE_POOL: return "long-column pool";
+    case cr::SITE_UF_CARVE: return "union-find region";
+    case cr::SITE_H1_CARVE: return "reduction region";
+    case cr::SITE_OUT_CARVE: return "output sort region";
+    case cr::SITE_FIXED: return "fixed part of the workspace";
+    default: return "unknown";
+    }
 }
 
 const char *cr_error_string(int code) {

@@ -28,6 +28,7 @@ struct Img3 {
     const float *img;
     const uint8_t *dd;       // primal stencil hooks
     const uint32_t *extra;   // edges that died in later union-find rounds (L-space bits)
+    uint32_t *appmask;       // faces that are the pivot of an apparent pair (L-space bits)
 };
 
 __device__ __forceinline__ uint32_t vord(const Img3 &I, const Seg &S, const int *c) {
@@ -179,6 +180,8 @@ __global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, int64_
                 int ea, ec[3];
                 uint64_t top = face_max_facet(I, S, fm, fc, ea, ec);
                 if (top == sk) {
+                    int64_t bit = S.loff + key_L(t);
+                    atomicOr(&I.appmask[bit >> 5], 1u << (bit & 31));
                     if (flags & CR_KEEP_ZERO)
                         emit_pair(pb, (uint32_t)si, 1, key_value(sk), key_value(t), key_L(sk), key_L(t), 0);
                 } else {
@@ -198,7 +201,7 @@ __global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, int64_
                     colkey[i] = ~sk;  // sorted ascending below = cohomology order
                     colseg[i] = (uint32_t)si;
                 } else {
-                    set_status(status, CR_ERR_WORKSPACE);
+                    fail_ws(status, SITE_COLUMNS);
                 }
             }
         }
@@ -221,21 +224,26 @@ struct RedParams {
     int64_t arena_cap;
     uint64_t *scratch;        // 2 * maxlen per warp
     int maxlen;
+    uint64_t *pool;           // buffers for columns that outgrow the per-warp scratch
+    unsigned long long *pool_top;
+    int64_t pool_cap;
     unsigned long long *next; // work counter
+    unsigned long long *stats;
     int *status;
 };
 
 __device__ __forceinline__ uint64_t ld_cg(const uint64_t *p) { return __ldcg((const unsigned long long *)p); }
 
 // out = A xor B (sorted, distinct), warp-cooperative; returns length or -1 if it exceeds cap
-__device__ int warp_xor(const uint64_t *A, int na, const uint64_t *B, int nb, uint64_t *out, int cap, bool bcg) {
+template <bool ACG, bool BCG>
+__device__ int warp_xor(const uint64_t *A, int na, const uint64_t *B, int nb, uint64_t *out, int cap) {
     const int lane = threadIdx.x & 31;
     const int T = na + nb;
     if (T <= 32) {
         uint64_t v = ~0ull;
         bool valid = lane < T;
-        if (lane < na) v = A[lane];
-        else if (valid) v = bcg ? ld_cg(B + lane - na) : B[lane - na];
+        if (lane < na) v = ACG ? ld_cg(A + lane) : A[lane];
+        else if (valid) v = BCG ? ld_cg(B + lane - na) : B[lane - na];
         unsigned same = __match_any_sync(0xFFFFFFFFu, v);
         bool keep = valid && __popc(same) == 1;
         int rank = 0;
@@ -257,7 +265,7 @@ __device__ int warp_xor(const uint64_t *A, int na, const uint64_t *B, int nb, ui
     int lo = max(0, s - nb), hi = min(s, na);
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        uint64_t am = A[mid], bm = bcg ? ld_cg(B + s - 1 - mid) : B[s - 1 - mid];
+        uint64_t am = ACG ? ld_cg(A + mid) : A[mid], bm = BCG ? ld_cg(B + s - 1 - mid) : B[s - 1 - mid];
         if (am <= bm) lo = mid + 1; else hi = mid;
     }
     const int i0 = lo, j0 = s - lo;
@@ -265,7 +273,7 @@ __device__ int warp_xor(const uint64_t *A, int na, const uint64_t *B, int nb, ui
     uint64_t prev = 0;
     bool hasprev = false;
     if (s > 0) {
-        uint64_t pa = i0 > 0 ? A[i0 - 1] : 0, pb = j0 > 0 ? (bcg ? ld_cg(B + j0 - 1) : B[j0 - 1]) : 0;
+        uint64_t pa = i0 > 0 ? (ACG ? ld_cg(A + i0 - 1) : A[i0 - 1]) : 0, pb = j0 > 0 ? (BCG ? ld_cg(B + j0 - 1) : B[j0 - 1]) : 0;
         prev = pa > pb ? pa : pb;
         hasprev = true;
     }
@@ -290,8 +298,8 @@ __device__ int warp_xor(const uint64_t *A, int na, const uint64_t *B, int nb, ui
         bool have = false;
         auto take = [&](uint64_t &x) -> bool {
             if (i + j >= T) return false;
-            uint64_t av = i < na ? A[i] : ~0ull;
-            uint64_t bv = j < nb ? (bcg ? ld_cg(B + j) : B[j]) : ~0ull;
+            uint64_t av = i < na ? (ACG ? ld_cg(A + i) : A[i]) : ~0ull;
+            uint64_t bv = j < nb ? (BCG ? ld_cg(B + j) : B[j]) : ~0ull;
             if (j >= nb || (i < na && av <= bv)) { x = av; i++; }
             else { x = bv; j++; }
             return true;
@@ -350,95 +358,547 @@ __device__ __forceinline__ void load_version(const RedParams &R, int64_t o, unsi
     len = (int)(v & 0xFFFFFFull);
 }
 
-__global__ void __launch_bounds__(256) k_h1_reduce(RedParams R) {
+constexpr int DMAX = 256;
+constexpr int RED_WARPS = 4;
+
+struct WarpSmem {
+    uint64_t d[2][DMAX];
+    uint64_t c[DMAX + 1];
+    int q[DMAX];
+    int pc[DMAX + 1];
+    uint64_t win[32];    // base[wbeg .. wbeg+32): cached head of the base
+    uint32_t nv[64];     // ord32 values of the 4x4x4 vertices around a face (0 = outside)
+    uint8_t ndd[64];     // their primal hook codes
+    uint32_t xm[4];      // later-round H0 death bits of the face's four edges
+};
+
+// ---------------------------------------------------------------------------
+// Apparent-pair test of a pivot face with one parallel load: lanes fetch the
+// 4x4x4 vertices around the face (values and hook codes) and the death bits
+// of the face's four edges; everything else is computed from shared memory.
+// ---------------------------------------------------------------------------
+struct NbView {
+    const uint32_t *nv;
+    const uint8_t *ndd;
+    int c[3];  // face anchor; the box starts at c - 1
+};
+__device__ __forceinline__ uint32_t nb_val(const NbView &N, int x, int y, int z) {
+    return N.nv[(x - N.c[0] + 1) + 4 * (y - N.c[1] + 1) + 16 * (z - N.c[2] + 1)];
+}
+__device__ __forceinline__ uint8_t nb_dd(const NbView &N, int x, int y, int z) {
+    return N.ndd[(x - N.c[0] + 1) + 4 * (y - N.c[1] + 1) + 16 * (z - N.c[2] + 1)];
+}
+__device__ __forceinline__ uint64_t nb_edge_key(const NbView &N, const Seg &S, int a, const int *c) {
+    int d[3] = {c[0], c[1], c[2]};
+    d[a] += 1;
+    uint32_t u = nb_val(N, c[0], c[1], c[2]), v = nb_val(N, d[0], d[1], d[2]);
+    return make_key(u > v ? u : v, cube_L(S, a, c[0], c[1], c[2]));
+}
+__device__ __forceinline__ uint64_t nb_face_key(const NbView &N, const Seg &S, int a, int b, const int *c) {
+    uint32_t m = 0;
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++) {
+            int d[3] = {c[0], c[1], c[2]};
+            d[a] += i;
+            d[b] += j;
+            uint32_t o = nb_val(N, d[0], d[1], d[2]);
+            m = o > m ? o : m;
+        }
+    return make_key(m, cube_L(S, a + b - 1, c[0], c[1], c[2]));
+}
+
+// returns the apparent edge key (0 if p is not an apparent pivot); on success
+// col[0..k) holds that edge's cofacets, sorted.  The scan marked every
+// apparent pivot face, so a miss costs one load; a hit loads the 4x4x4
+// vertices around the face in one parallel step.
+__device__ uint64_t apparent_warp(const Img3 &I, const Seg &S, uint64_t fk, WarpSmem &sm, uint64_t *col, int &k) {
     const int lane = threadIdx.x & 31;
+    int fm, c[3];
+    decode_L(S, key_L(fk), fm, c);
+    {
+        int64_t bit = S.loff + key_L(fk);
+        if (!((__ldcg(&I.appmask[bit >> 5]) >> (bit & 31)) & 1u)) return 0;
+    }
+    int a = fm == 2 ? 1 : 0, b = fm == 0 ? 1 : 2;
+    __syncwarp();
+    for (int v = lane; v < 64; v += 32) {
+        int x = c[0] - 1 + (v & 3), y = c[1] - 1 + ((v >> 2) & 3), z = c[2] - 1 + (v >> 4);
+        bool in = x >= 0 && y >= 0 && z >= 0 && x < S.nx && y < S.ny && z < S.nz;
+        int64_t gv = S.voff + ((int64_t)z * S.ny + y) * S.nx + x;
+        sm.nv[v] = in ? ord32(I.img[gv]) : 0u;
+    }
+    __syncwarp();
+    NbView N{sm.nv, sm.ndd, {c[0], c[1], c[2]}};
+    // the face's latest facet: the apparent edge
+    uint64_t best = 0;
+    int ea = 0, ec[3] = {0, 0, 0};
+    for (int q = 0; q < 4; q++) {
+        int ax = q < 2 ? a : b, other = q < 2 ? b : a;
+        int d[3] = {c[0], c[1], c[2]};
+        d[other] += (q & 1);
+        uint64_t key = nb_edge_key(N, S, ax, d);
+        if (q == 0 || key > best) {
+            best = key;
+            ea = ax;
+            ec[0] = d[0]; ec[1] = d[1]; ec[2] = d[2];
+        }
+    }
+    // its cofacets (the face itself is the earliest of them)
+    int n = 0;
+    for (int bb = 0; bb < 3; bb++) {
+        if (bb == ea) continue;
+        int lo = ea < bb ? ea : bb, hi = ea < bb ? bb : ea;
+        if (ec[bb] + 1 < ext_of(S, bb)) col[n++] = nb_face_key(N, S, lo, hi, ec);
+        if (ec[bb] >= 1) {
+            int d[3] = {ec[0], ec[1], ec[2]};
+            d[bb] -= 1;
+            col[n++] = nb_face_key(N, S, lo, hi, d);
+        }
+    }
+    sort4(col, n);
+    k = n;
+    return best;
+}
+
+// ---------------------------------------------------------------------------
+// Working column of one warp.  Entries below the current pivot are always
+// cancelled (an added column shares the pivot, all its other entries are
+// larger), so the column is kept as
+//   base[start..nb)  sorted, in global memory (consumed from the front), and
+//   delta[dh..nd)    sorted, in shared memory (recent additions),
+// whose symmetric difference is the column.  A small addition is a
+// shared-memory merge into delta; base is rebuilt only when delta fills.
+// ---------------------------------------------------------------------------
+struct Work {
+    uint64_t *g[2];  // this warp's global buffers (base lives in g[bown])
+    int cap;
+    int bown;
+    int nb, start;
+    int sb, dh, nd;
+    int wbeg;        // start of the cached window of the base (-1: none)
+};
+
+// diagnostic counters (cnt[8..15]): iterations, apparent additions, column
+// additions, merged entries, takeovers, stale or lost races, base rebuilds,
+// max iterations spent on one column
+struct RedStats {
+    unsigned long long it = 0, app = 0, add = 0, merged = 0, take = 0, retry = 0, flush = 0, maxit = 0;
+    unsigned long long t[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // cycles per phase (diagnostic builds)
+};
+#ifdef CR_H1_TIMING
+#define TMARK(v) long long v = clock64()
+#define TADD(st, i, v) (st).t[i] += (unsigned long long)(clock64() - (v))
+#else
+#define TMARK(v)
+#define TADD(st, i, v)
+#endif
+__device__ void flush_stats(const RedParams &R, const RedStats &s) {
+    if ((threadIdx.x & 31) != 0) return;
+    unsigned long long *c = R.stats;
+    atomicAdd(&c[0], s.it);
+    atomicAdd(&c[1], s.app);
+    atomicAdd(&c[2], s.add);
+    atomicAdd(&c[3], s.merged);
+    atomicAdd(&c[4], s.take);
+    atomicAdd(&c[5], s.retry);
+    atomicAdd(&c[6], s.flush);
+    atomicMax(&c[7], s.maxit);
+    for (int i = 0; i < 8; i++) atomicAdd(&c[8 + i], s.t[i]);
+}
+
+// new buffer pair of at least `need` entries from the shared pool (the old
+// buffers stay readable); false when the pool is exhausted
+__device__ bool grow_to(const RedParams &R, Work &W, int64_t need) {
+    const int lane = threadIdx.x & 31;
+    int64_t nc = W.cap;
+    while (nc < need) nc *= 2;
+    if (nc > (1 << 28)) return false;
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(R.pool_top, (unsigned long long)(2 * nc));
+    off = __shfl_sync(0xFFFFFFFFu, off, 0);
+    if ((int64_t)(off + 2 * nc) > R.pool_cap) return false;
+    W.g[0] = R.pool + off;
+    W.g[1] = R.pool + off + nc;
+    W.cap = (int)nc;
+    W.bown = 1;  // the next write goes to g[0]; the old base is in the old buffers
+    return true;
+}
+
+__device__ __forceinline__ int warp_excl_scan(int x, int &total) {
+    const int lane = threadIdx.x & 31;
+    int incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    return incl - x;
+}
+
+// out = A xor D with D sorted in shared memory; A in global memory (read
+// through L2, AG = true) or in shared memory.  One pass over A: the insertion
+// points of D are found by binary search, then A is streamed in chunks of
+// 256 with each entry shifted by the insertions and cancellations before it.
+template <bool AG>
+__device__ __forceinline__ uint64_t ld_a(const uint64_t *A, int i) {
+    return AG ? ld_cg(A + i) : A[i];
+}
+
+template <bool AG>
+__device__ int insert_merge(const uint64_t *A, int na, const uint64_t *D, int nD, uint64_t *out, WarpSmem &sm) {
+    const int lane = threadIdx.x & 31;
+    // 1. insertion positions of D in A and cancellations
+    for (int k = lane; k < nD; k += 32) {
+        uint64_t x = D[k];
+        int lo = 0, hi = na;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (ld_a<AG>(A, mid) < x) lo = mid + 1; else hi = mid;
+        }
+        sm.q[k] = lo;
+        sm.pc[k + 1] = (lo < na && ld_a<AG>(A, lo) == x) ? 1 : 0;
+    }
+    __syncwarp();
+    // 2. exclusive prefix counts of cancellations: pc[k] = cancelled among D[0..k)
+    int run = 0;
+    for (int base = 0; base < nD; base += 32) {
+        int k = base + lane;
+        int f = k < nD ? sm.pc[k + 1] : 0;
+        int tot;
+        int ex = warp_excl_scan(f, tot);
+        __syncwarp();
+        if (k < nD) sm.pc[k] = run + ex;
+        run += tot;
+        __syncwarp();
+    }
+    if (lane == 0) sm.pc[nD] = run;
+    __syncwarp();
+    const int cancelled = run;
+    // 3. the surviving entries of D
+    for (int k = lane; k < nD; k += 32) {
+        bool eq = sm.pc[k + 1] - sm.pc[k];
+        if (!eq) out[sm.q[k] + k - 2 * sm.pc[k]] = D[k];
+    }
+    // 4. stream A
+    for (int c0 = 0; c0 < na; c0 += 256) {
+        // insertion points that fall into this chunk: q in [c0, c0 + 256)
+        int lo = 0, hi = nD;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (sm.q[mid] < c0) lo = mid + 1; else hi = mid;
+        }
+        const int klo = lo;
+        hi = nD;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (sm.q[mid] < c0 + 256) lo = mid + 1; else hi = mid;
+        }
+        const int khi = lo;
+        uint64_t v[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            int i = c0 + lane + 32 * t;
+            v[t] = i < na ? ld_a<AG>(A, i) : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            int i = c0 + lane + 32 * t;
+            if (i >= na) break;
+            int kk = klo;  // #{k : q[k] <= i}
+            while (kk < khi && sm.q[kk] <= i) kk++;
+            bool cancel = kk > 0 && sm.q[kk - 1] == i && (sm.pc[kk] - sm.pc[kk - 1]);
+            if (!cancel) out[i + kk - 2 * sm.pc[kk]] = v[t];
+        }
+    }
+    __syncwarp();
+    return na + nD - 2 * cancelled;
+}
+
+// fold delta into base (base <- base[start..nb) xor delta[dh..nd))
+__device__ bool flush_delta(const RedParams &R, Work &W, WarpSmem &sm, RedStats &st) {
+    int nd = W.nd - W.dh;
+    if (nd == 0) return true;
+    int na = W.nb - W.start;
+    const uint64_t *A = W.g[W.bown] + W.start;
+    if ((int64_t)na + nd > W.cap && !grow_to(R, W, (int64_t)na + nd)) return false;
+    int x = W.bown ^ 1;
+    TMARK(tf);
+    int n = insert_merge<true>(A, na, &sm.d[W.sb][W.dh], nd, W.g[x], sm);
+    TADD(st, 5, tf);
+    __threadfence_block();
+    W.bown = x;
+    W.nb = n;
+    W.start = 0;
+    W.dh = W.nd = 0;
+    W.wbeg = -1;
+    st.flush++;
+    st.merged += (unsigned long long)(na + nd);
+    return true;
+}
+
+// the pivot (earliest face) of the working column, cancelling equal heads; ~0 if empty
+__device__ __forceinline__ uint64_t base_head(Work &W, WarpSmem &sm) {
+    if (W.start >= W.nb) return ~0ull;
+    if (W.wbeg < 0 || W.start >= W.wbeg + 32) {
+        const int lane = threadIdx.x & 31;
+        int i = W.start + lane;
+        __syncwarp();
+        sm.win[lane] = i < W.nb ? ld_cg(W.g[W.bown] + i) : ~0ull;
+        __syncwarp();
+        W.wbeg = W.start;
+    }
+    return sm.win[W.start - W.wbeg];
+}
+
+__device__ uint64_t pivot_of(Work &W, WarpSmem &sm, bool &from_base) {
+    for (;;) {
+        uint64_t hb = base_head(W, sm);
+        uint64_t hd = W.dh < W.nd ? sm.d[W.sb][W.dh] : ~0ull;
+        if (hb == hd) {
+            if (hb == ~0ull) return ~0ull;
+            W.start++;
+            W.dh++;
+            continue;
+        }
+        from_base = hb < hd;
+        return from_base ? hb : hd;
+    }
+}
+
+// add the column staged in sm.c[0..m) whose first entry is the current pivot
+__device__ bool add_staged(const RedParams &R, Work &W, WarpSmem &sm, bool from_base, int m, RedStats &st) {
+    if (from_base) W.start++; else W.dh++;
+    int mc = m - 1;
+    if (W.nd - W.dh + mc > DMAX) {
+        if (!flush_delta(R, W, sm, st)) return false;
+    }
+    int n = insert_merge<false>(&sm.d[W.sb][W.dh], W.nd - W.dh, &sm.c[1], mc, sm.d[W.sb ^ 1], sm);
+    W.sb ^= 1;
+    W.dh = 0;
+    W.nd = n;
+    return true;
+}
+
+// add a short column x0 < x1 < x2 < x3 (k <= 4 entries, x0 = current pivot;
+// unused entries are ~0): one pass over delta, no scratch arrays.  Lane e
+// locates entry e+1 in delta; the results are broadcast by shuffles.
+__device__ bool add_small(const RedParams &R, Work &W, WarpSmem &sm, bool from_base, uint64_t x1, uint64_t x2,
+                          uint64_t x3, int k, RedStats &st) {
+    const int lane = threadIdx.x & 31;
+    if (from_base) W.start++; else W.dh++;
+    const int m = k - 1;
+    if (W.nd - W.dh + m > DMAX) {
+        if (!flush_delta(R, W, sm, st)) return false;
+    }
+    const uint64_t *D = &sm.d[W.sb][W.dh];
+    uint64_t *out = sm.d[W.sb ^ 1];
+    const int nd = W.nd - W.dh;
+    uint64_t mine = lane == 0 ? x1 : (lane == 1 ? x2 : x3);
+    int myq = 0, myeq = 0;
+    if (lane < m) {
+        int lo = 0, hi = nd;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (D[mid] < mine) lo = mid + 1; else hi = mid;
+        }
+        myq = lo;
+        myeq = (lo < nd && D[lo] == mine) ? 1 : 0;
+    }
+    const int eq0 = __shfl_sync(0xFFFFFFFFu, myeq, 0), eq1 = __shfl_sync(0xFFFFFFFFu, myeq, 1),
+              eq2 = __shfl_sync(0xFFFFFFFFu, myeq, 2);
+    const uint64_t v0 = m > 0 ? x1 : ~0ull, v1 = m > 1 ? x2 : ~0ull, v2 = m > 2 ? x3 : ~0ull;
+    for (int i = lane; i < nd; i += 32) {
+        uint64_t d = D[i];
+        int ins = 0, can = 0;
+        if (v0 < d) { if (eq0) can++; else ins++; }
+        if (v1 < d) { if (eq1) can++; else ins++; }
+        if (v2 < d) { if (eq2) can++; else ins++; }
+        bool drop = (v0 == d) | (v1 == d) | (v2 == d);
+        if (!drop) out[i + ins - can] = d;
+    }
+    if (lane < m && !myeq) {
+        int before_c = (lane > 0 ? eq0 : 0) + (lane > 1 ? eq1 : 0);
+        int before_nc = lane - before_c;
+        out[myq + before_nc - before_c] = mine;
+    }
+    __syncwarp();
+    W.sb ^= 1;
+    W.dh = 0;
+    W.nd = nd + m - 2 * (eq0 + (m > 1 ? eq1 : 0) + (m > 2 ? eq2 : 0));
+    return true;
+}
+
+// add a published column (arena, length len, first entry = current pivot)
+__device__ bool add_arena(const RedParams &R, Work &W, WarpSmem &sm, bool from_base, const uint64_t *C, int len,
+                          RedStats &st) {
+    const int lane = threadIdx.x & 31;
+    if (len - 1 <= DMAX) {
+        for (int k = lane; k < len; k += 32) sm.c[k] = ld_cg(C + k);
+        __syncwarp();
+        return add_staged(R, W, sm, from_base, len, st);
+    }
+    // a long column: fold delta into base, then merge base with the column's tail
+    if (from_base) W.start++; else W.dh++;
+    if (!flush_delta(R, W, sm, st)) return false;
+    int na = W.nb - W.start;
+    const uint64_t *A = W.g[W.bown] + W.start;
+    if ((int64_t)na + len - 1 > W.cap && !grow_to(R, W, (int64_t)na + len - 1)) return false;
+    int x = W.bown ^ 1;
+    int n = warp_xor<true, true>(A, na, C + 1, len - 1, W.g[x], W.cap);
+    __threadfence_block();
+    if (n < 0) return false;
+    W.bown = x;
+    W.nb = n;
+    W.start = 0;
+    W.wbeg = -1;
+    st.merged += (unsigned long long)(na + len);
+    return true;
+}
+
+// publish the working column as column j's current version
+__device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &sm, RedStats &st) {
+    const int lane = threadIdx.x & 31;
+    if (W.nb - W.start > 0 && W.nd - W.dh > 0)
+        if (!flush_delta(R, W, sm, st)) return false;
+    int nbase = W.nb - W.start, nd = W.nd - W.dh;
+    int n = nbase + nd;
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(R.arena_top, (unsigned long long)n);
+    off = __shfl_sync(0xFFFFFFFFu, off, 0);
+    if ((int64_t)(off + n) > R.arena_cap) return false;
+    if (nbase > 0) {
+        const uint64_t *A = W.g[W.bown] + W.start;
+        for (int k = lane; k < nbase; k += 32) __stcg((unsigned long long *)&R.arena[off + k], ld_cg(A + k));
+    } else {
+        for (int k = lane; k < nd; k += 32) __stcg((unsigned long long *)&R.arena[off + k], sm.d[W.sb][W.dh + k]);
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(&R.cur[j], (off << 24) | (unsigned long long)n);
+    __threadfence();
+    __syncwarp();
+    return true;
+}
+
+__global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
+    __shared__ WarpSmem smem[RED_WARPS];
+    const int lane = threadIdx.x & 31;
+    WarpSmem &sm = smem[threadIdx.x >> 5];
+    RedStats st;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint64_t *bufA = R.scratch + wid * 2 * (int64_t)R.maxlen;
-    uint64_t *bufB = bufA + R.maxlen;
+    Work W;
+    W.g[0] = R.scratch + wid * 2 * (int64_t)R.maxlen;
+    W.g[1] = W.g[0] + R.maxlen;
+    W.cap = R.maxlen;
     const int64_t CAP = (int64_t)1 << 24;
     for (;;) {
         unsigned long long jj = 0;
         if (lane == 0) jj = atomicAdd(R.next, 1ull);
         jj = __shfl_sync(0xFFFFFFFFu, jj, 0);
-        if ((int64_t)jj >= R.ncols) return;
+        if ((int64_t)jj >= R.ncols) { flush_stats(R, st); return; }
         int64_t j = (int64_t)jj;
         uint64_t jkey = R.colkey[j];
         const Seg S = R.segs[R.colseg[j]];
-        // the coboundary of edge j
-        int n;
+        // the coboundary of edge j becomes the delta; base is empty
         {
             int a, c[3];
             decode_L(S, key_L(jkey), a, c);
             uint64_t cf[4];
             int k = edge_cofacets(R.I, S, a, c, cf);
             sort4(cf, k);
-            if (lane < k) bufA[lane] = cf[lane];
-            n = k;
+            W.sb = 0;
+            if (lane < k) sm.d[0][lane] = cf[lane];
+            W.dh = 0;
+            W.nd = k;
+            W.bown = 0;
+            W.nb = W.start = 0;
+            W.wbeg = -1;
             __syncwarp();
         }
         int64_t it = 0;
         for (;;) {
-            if (++it > CAP) { if (lane == 0) set_status(R.status, CR_ERR_TIMEOUT); return; }
-            if (n <= 0) { if (lane == 0) set_status(R.status, CR_ERR_INTERNAL); break; }
-            uint64_t p = bufA[0];
+            if (++it > CAP) { if (lane == 0) set_status(R.status, CR_ERR_TIMEOUT); flush_stats(R, st); return; }
+            st.it++;
+            if ((unsigned long long)it > st.maxit) st.maxit = (unsigned long long)it;
+            bool from_base = false;
+            TMARK(t0);
+            uint64_t p = pivot_of(W, sm, from_base);
+            TADD(st, 0, t0);
+            if (p == ~0ull) { if (lane == 0) set_status(R.status, CR_ERR_INTERNAL); break; }
             int64_t gidx = S.loff + key_L(p);
-            uint64_t ak = 0;
-            if (lane == 0) ak = apparent_edge(R.I, S, p);
-            ak = __shfl_sync(0xFFFFFFFFu, ak, 0);
+            uint64_t cf[4];
+            int k = 0;
+            TMARK(t1);
+            uint64_t ak = apparent_warp(R.I, S, p, sm, cf, k);
+            TADD(st, 1, t1);
             if (ak) {
-                int a, c[3];
-                decode_L(S, key_L(ak), a, c);
-                uint64_t cf[4];
-                int k = edge_cofacets(R.I, S, a, c, cf);
-                sort4(cf, k);
-                int m = warp_xor(bufA, n, cf, k, bufB, R.maxlen, false);
-                if (m < 0) { if (lane == 0) set_status(R.status, CR_ERR_WORKSPACE); return; }
-                uint64_t *t = bufA; bufA = bufB; bufB = t;
-                n = m;
+                st.app++;
+                TMARK(t2);
+                bool okadd = add_small(R, W, sm, from_base, k > 1 ? cf[1] : ~0ull, k > 2 ? cf[2] : ~0ull,
+                                       k > 3 ? cf[3] : ~0ull, k, st);
+                TADD(st, 2, t2);
+                if (!okadd) {
+                    if (lane == 0) fail_ws(R.status, SITE_POOL);
+                    flush_stats(R, st);
+                    return;
+                }
                 continue;
             }
-            int o = 0;
-            if (lane == 0) o = atomicAdd(&R.P[gidx], 0);
-            o = __shfl_sync(0xFFFFFFFFu, o, 0);
-            __threadfence();
+            TMARK(t3);
+            int o = __ldcg(&R.P[gidx]);
             if (o < 0) {
-                if (!publish(R, j, bufA, n)) { if (lane == 0) set_status(R.status, CR_ERR_WORKSPACE); return; }
+                TMARK(t6);
+                bool okpub = publish_work(R, j, W, sm, st);
+                TADD(st, 6, t6);
+                if (!okpub) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
                 int prev = 0;
                 if (lane == 0) prev = atomicCAS(&R.P[gidx], -1, (int)j);
                 prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
                 if (prev == -1) break;  // j settled
+                st.retry++;
                 continue;
             }
             if ((int64_t)o == j) break;
-            uint64_t okey = R.colkey[o];
-            if (okey > jkey) {
-                // o is an earlier column (a later edge): add it
-                unsigned long long off;
-                int len;
-                load_version(R, o, off, len);
-                if (len == 0) continue;
-                if (ld_cg(&R.arena[off]) != p) continue;  // stale snapshot: re-read the table
-                int m = warp_xor(bufA, n, R.arena + off, len, bufB, R.maxlen, true);
-                if (m < 0) { if (lane == 0) set_status(R.status, CR_ERR_WORKSPACE); return; }
-                uint64_t *t = bufA; bufA = bufB; bufB = t;
-                n = m;
-                continue;
+            // columns are numbered in cohomology order: a smaller index is an earlier column
+            bool takeover = (int64_t)o > j;  // o is a later column: j takes its pivot, then continues with o
+            if (takeover) {
+                if (!publish_work(R, j, W, sm, st)) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
+                int prev = 0;
+                if (lane == 0) prev = atomicCAS(&R.P[gidx], o, (int)j);
+                prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
+                if (prev != o) { st.retry++; continue; }
+                st.take++;
+                p = pivot_of(W, sm, from_base);  // publishing may have folded delta into base
             }
-            // o is a later column: take its pivot, then continue with o
-            if (!publish(R, j, bufA, n)) { if (lane == 0) set_status(R.status, CR_ERR_WORKSPACE); return; }
-            int prev = 0;
-            if (lane == 0) prev = atomicCAS(&R.P[gidx], o, (int)j);
-            prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
-            if (prev != o) continue;
-            unsigned long long off;
-            int len;
-            load_version(R, o, off, len);
-            int m = warp_xor(bufA, n, R.arena + off, len, bufB, R.maxlen, true);
-            if (m < 0) { if (lane == 0) set_status(R.status, CR_ERR_WORKSPACE); return; }
-            uint64_t *t = bufA; bufA = bufB; bufB = t;
-            n = m;
-            j = o;
-            jkey = okey;
+            unsigned long long ver = __ldcg(&R.cur[o]);
+            unsigned long long off = ver >> 24;
+            int len = (int)(ver & 0xFFFFFFull);
+            if (len == 0) continue;
+            bool ok2;
+            if (len - 1 <= DMAX) {
+                // stage the column; a stale snapshot (head != pivot) leaves the state untouched
+                for (int q2 = lane; q2 < len; q2 += 32) sm.c[q2] = ld_cg(R.arena + off + q2);
+                __syncwarp();
+                if (sm.c[0] != p) { st.retry++; continue; }
+                st.add++;
+                TADD(st, 3, t3);
+                TMARK(t4);
+                ok2 = add_staged(R, W, sm, from_base, len, st);
+                TADD(st, 4, t4);
+            } else {
+                if (ld_cg(&R.arena[off]) != p) { st.retry++; continue; }
+                st.add++;
+                TADD(st, 3, t3);
+                TMARK(t4);
+                ok2 = add_arena(R, W, sm, from_base, R.arena + off, len, st);
+                TADD(st, 4, t4);
+            }
+            if (!ok2) {
+                if (lane == 0) fail_ws(R.status, SITE_POOL);
+                flush_stats(R, st);
+                return;
+            }
+            if (takeover) j = o;
         }
     }
 }
@@ -471,10 +931,19 @@ __global__ void k_not_keys(uint64_t *k, int64_t n) {
 
 static inline unsigned nb1(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+static unsigned long long g_h1_stats[16];
+static int64_t g_h1_stats_cols = 0;
+int h1_stats(int64_t *out, int n) {
+    out[0] = g_h1_stats_cols;
+    for (int i = 0; i < 16 && i + 1 < n; i++) out[i + 1] = (int64_t)g_h1_stats[i];
+    return CR_OK;
+}
+
 int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, int nseg, int64_t vtot,
            H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status, int64_t *ncols_out, cudaStream_t st) {
-    Img3 I{img, dd, extra};
-    cudaMemsetAsync(B.cnt, 0, 3 * sizeof(unsigned long long), st);
+    Img3 I{img, dd, extra, B.appmask};
+    cudaMemsetAsync(B.appmask, 0, (size_t)((3 * vtot + 31) / 32) * sizeof(uint32_t), st);
+    cudaMemsetAsync(B.cnt, 0, 24 * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_H1_SCAN);
     CR_NOTE_LAUNCH();
     k_h1_scan<<<nb1(vtot), 256, 0, st>>>(I, segs, nseg, vtot, B.colkey, B.colseg, &B.cnt[0], B.max_cols, pb, flags,
@@ -485,7 +954,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
     int64_t ncols = (int64_t)hc;
     *ncols_out = ncols;
-    if (ncols > B.max_cols) return CR_ERR_WORKSPACE;
+    if (ncols > B.max_cols) { set_host_detail(SITE_COLUMNS); return CR_ERR_WORKSPACE; }
     if (ncols == 0) return CR_OK;
     if (ncols >= ((int64_t)1 << 31)) return CR_ERR_TOO_LARGE;
     // cohomology order: decreasing edge key (keys were stored complemented)
@@ -511,16 +980,22 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     R.arena_cap = B.arena_cap;
     R.scratch = B.scratch;
     R.maxlen = B.maxlen;
+    R.pool = B.pool;
+    R.pool_top = &B.cnt[3];
+    R.pool_cap = B.pool_cap;
     R.next = &B.cnt[2];
+    R.stats = &B.cnt[8];
     R.status = status;
     int64_t warps = B.nwarps < ncols ? B.nwarps : ncols;
-    unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    unsigned blocks = (unsigned)((warps + RED_WARPS - 1) / RED_WARPS);
     prof_begin(st, STAGE_H1_REDUCE);
     CR_NOTE_LAUNCH();
-    k_h1_reduce<<<blocks, 256, 0, st>>>(R);
+    k_h1_reduce<<<blocks, RED_WARPS * 32, 0, st>>>(R);
     prof_end(st, STAGE_H1_REDUCE, 12.0 * ncols);
     CR_NOTE_LAUNCH();
     k_h1_emit<<<nb1(ncols), 256, 0, st>>>(B.colkey, B.colseg, ncols, segs, B.P, B.cur, B.arena, pb, flags, status);
+    cudaMemcpyAsync(g_h1_stats, &B.cnt[8], 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    g_h1_stats_cols = ncols;
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 

@@ -68,9 +68,19 @@ __host__ __device__ __forceinline__ uint32_t cube_L(const Seg &s, int m, int x, 
 }
 
 // ---------------------------------------------------------------------------
-// status word (device int) -- first error wins
+// status block (device): int word 0 = error code, int word 8 = failure site;
+// the first error wins
 // ---------------------------------------------------------------------------
+enum Site {
+    SITE_NONE = 0, SITE_GROUPS = 1, SITE_EDGES = 2, SITE_COLUMNS = 3, SITE_ARENA = 4, SITE_POOL = 5,
+    SITE_UF_CARVE = 6, SITE_H1_CARVE = 7, SITE_OUT_CARVE = 8, SITE_FIXED = 9
+};
 __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
+__device__ __forceinline__ void fail_ws(int *status, int site) {
+    atomicCAS(status, 0, CR_ERR_WORKSPACE);
+    atomicCAS(status + 8, 0, site);
+}
+void set_host_detail(int site);
 
 // ---------------------------------------------------------------------------
 // workspace carving
@@ -148,11 +158,15 @@ struct H1Bufs {
     unsigned long long *cur;
     uint64_t *arena;
     int64_t arena_cap;
-    uint64_t *scratch;
+    uint64_t *scratch;        // 2 * maxlen per warp
     int64_t nwarps;
     int maxlen;
-    unsigned long long *cnt;  // [0] columns, [1] arena top, [2] work counter
+    uint32_t *appmask;        // apparent pivot faces (3 * vtot bits)
+    uint64_t *pool;           // grown column buffers for columns longer than maxlen
+    int64_t pool_cap;
+    unsigned long long *cnt;  // [0] columns, [1] arena top, [2] work counter, [3] pool top
 };
+int h1_stats(int64_t *out, int n);
 int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, int nseg, int64_t vtot,
            H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status, int64_t *ncols_out, cudaStream_t st);
 

@@ -152,7 +152,7 @@ __global__ void k_h0_roots(const float *__restrict__ img, const Seg *__restrict_
     bool isroot = gv < vtot && lab[gv] == (uint32_t)gv;
     int64_t g = warp_append(isroot, ngroups);
     if (!isroot) return;
-    if (g >= max_groups) { set_status(status, CR_ERR_WORKSPACE); lab[gv] = 0x80000000u; return; }
+    if (g >= max_groups) { fail_ws(status, SITE_GROUPS); lab[gv] = 0x80000000u; return; }
     int si = seg_of(segs, nseg, gv);
     int64_t lv = gv - segs[si].voff;
     gkey[g] = make_key(ord32(img[gv]), (uint32_t)lv);
@@ -228,7 +228,7 @@ __global__ void k_h0_cross(const float *__restrict__ img, const Seg *__restrict_
                 ea[i] = la;
                 eb[i] = lb;
             } else {
-                set_status(status, CR_ERR_WORKSPACE);
+                fail_ws(status, SITE_EDGES);
             }
         }
     }
@@ -355,7 +355,7 @@ __global__ void k_dual_roots(const float *__restrict__ img, const Seg *__restric
     bool isroot = gc < ctot && lab[gc] == (uint32_t)gc;
     int64_t g = warp_append(isroot, ngroups);
     if (!isroot) return;
-    if (g >= max_groups) { set_status(status, CR_ERR_WORKSPACE); lab[gc] = 0x80000000u; return; }
+    if (g >= max_groups) { fail_ws(status, SITE_GROUPS); lab[gc] = 0x80000000u; return; }
     int si = seg_of_node(segs, nseg, gc);
     const Seg S = segs[si];
     int64_t c = gc - S.coff;
@@ -450,7 +450,7 @@ __global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restric
                 ea[i] = la;
                 eb[i] = lb;
             } else {
-                set_status(status, CR_ERR_WORKSPACE);
+                fail_ws(status, SITE_EDGES);
             }
         }
     }
@@ -628,7 +628,8 @@ int run_h0(const float *img, const Seg *segs, int nseg, int64_t vtot, UF &u, con
     cudaMemcpyAsync(u.hcnt, u.cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
     int64_t ng = (int64_t)u.hcnt[0], ne = (int64_t)u.hcnt[1];
-    if (ng > u.max_groups || ne > u.max_edges) return CR_ERR_WORKSPACE;
+    if (ng > u.max_groups) { set_host_detail(SITE_GROUPS); return CR_ERR_WORKSPACE; }
+    if (ne > u.max_edges) { set_host_detail(SITE_EDGES); return CR_ERR_WORKSPACE; }
     int rc = rounds_loop(u, ng, ne, segs, 0, pb, flags, extra_mask, status, st);
     if (rc) return rc;
     CR_NOTE_LAUNCH();
@@ -664,7 +665,8 @@ int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t 
     cudaMemcpyAsync(u.hcnt, u.cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
     int64_t ng = (int64_t)u.hcnt[0], ne = (int64_t)u.hcnt[1];
-    if (ng > u.max_groups || ne > u.max_edges) return CR_ERR_WORKSPACE;
+    if (ng > u.max_groups) { set_host_detail(SITE_GROUPS); return CR_ERR_WORKSPACE; }
+    if (ne > u.max_edges) { set_host_detail(SITE_EDGES); return CR_ERR_WORKSPACE; }
     return rounds_loop(u, ng, ne, segs, 1, pb, flags, nullptr, status, st);
 }
 
