@@ -43,16 +43,16 @@ WORKLOADS = {
 }
 
 
-def make_input(name):
+def make_input(name, size=None):
     from paper_2005_12692_gb300 import synth
     if name == "uniform64":
         return synth.uniform64()
     if name == "grf1024":
-        return synth.grf1024()
+        return synth.grf1024(size or 1024)
     if name == "grf256cube_salt":
-        return synth.grf256cube_salt()
+        return synth.grf256cube_salt(size or 256)
     if name == "grf512cube":
-        return synth.grf512cube()
+        return synth.grf512cube(size or 512)
     if name == "batch4096":
         return synth.batch_images(4096)
     raise ValueError(name)
@@ -215,6 +215,9 @@ def main():
     ap.add_argument("--workload", default="grf1024", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop (profiling runs)")
+    ap.add_argument("--size", type=int, default=None,
+                    help="side length override of a single-image workload (same recipe; profiling on smaller cases)")
     args = ap.parse_args()
     W = WORKLOADS[args.workload]
 
@@ -227,7 +230,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        data = make_input(args.workload)
+        data = make_input(args.workload, args.size)
         import oracle  # noqa: F401
         cores = 1
         vals = []
@@ -260,7 +263,7 @@ def main():
     cr.build()
     L = cr.lib()
 
-    data = make_input(args.workload)
+    data = make_input(args.workload, args.size)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -331,7 +334,9 @@ def main():
 
     # -------- end to end through host buffers --------
     e2e_ms = []
-    if W["kind"] == "single":
+    if args.no_e2e:
+        h2d = d2h = 0
+    elif W["kind"] == "single":
         host = torch.from_numpy(data).pin_memory()
         h2d = host.numel() * 4
         d2h = 0
@@ -364,7 +369,7 @@ def main():
             if i >= args.warmup:
                 e2e_ms.append((time.perf_counter() - t0) * 1e3)
             d2h = gh.numel() * 4
-    e2e_value = units * world / (statistics.mean(e2e_ms) / 1e3)
+    e2e_value = units * world / (statistics.mean(e2e_ms) / 1e3) if e2e_ms else None
 
     peaks = load_peaks()
     roof = roofline_from(stages, peaks)
@@ -375,6 +380,7 @@ def main():
             "config": {"workload": args.workload,
                        "shape": list(data.shape) if W["kind"] == "single" else "4096 x U{28..256}^2",
                        "maxdim": W["maxdim"], "cells": num_cells(data.shape) if W["kind"] == "single" else None,
+                       "size_override": args.size,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between steps (256 MiB write)"},
             "clocks": clk, "gpu_launches": launches,

@@ -186,6 +186,53 @@ __global__ void k_out_offsets(const uint32_t *scanned, int n, int64_t np, int64_
 }
 static inline unsigned nbk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// One block sorts up to SMALL_SORT pairs of a single image in shared memory
+// (bitonic network on a packed key dim:2 | ord32(birth):32 | birth_cell:30)
+// and gathers them; tmp receives a copy of the unsorted pairs.
+constexpr int SMALL_SORT = 16384;
+__global__ void __launch_bounds__(1024) k_out_small_sort(cr_pair *pairs, int np, cr_pair *tmp) {
+    extern __shared__ unsigned char sbuf[];
+    int npow = 1;
+    while (npow < np) npow <<= 1;
+    uint64_t *key = (uint64_t *)sbuf;
+    uint32_t *idx = (uint32_t *)(key + npow);
+    for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+        if (i < np) {
+            cr_pair p = pairs[i];
+            tmp[i] = p;
+            key[i] = ((uint64_t)(p.dim & 3) << 62) | ((uint64_t)ord32(p.birth) << 30) | (uint64_t)(p.birth_cell & 0x3FFFFFFF);
+        } else {
+            key[i] = ~0ull;
+        }
+        idx[i] = (uint32_t)i;
+    }
+    __syncthreads();
+    for (int k = 2; k <= npow; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    bool up = (i & k) == 0;
+                    uint64_t a = key[i], b = key[l];
+                    if ((a > b) == up) {
+                        key[i] = b;
+                        key[l] = a;
+                        uint32_t t = idx[i];
+                        idx[i] = idx[l];
+                        idx[l] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        cr_pair p = tmp[idx[i]];
+        p.flags &= 0xFFu;
+        pairs[i] = p;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the pipeline
 // ---------------------------------------------------------------------------
@@ -362,7 +409,22 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         uint32_t *segc = R.take<uint32_t>(n + 1);
         uint32_t *part = R.take<uint32_t>(scan_temp_bytes(n + 1) / 4 + 1);
         if (!R.ok) { g_detail = SITE_OUT_CARVE; return CR_ERR_WORKSPACE; }
-        if (np > 0) {
+        bool small = n == 1 && np <= SMALL_SORT && 3 * P.vtot < ((int64_t)1 << 30);
+        if (np > 0 && small) {
+            static bool attr = false;
+            size_t smem = 0;
+            int npow = 1;
+            while (npow < np) npow <<= 1;
+            smem = (size_t)npow * 12;
+            if (!attr) {
+                cudaFuncSetAttribute(k_out_small_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_SORT * 12);
+                attr = true;
+            }
+            prof_begin(st, STAGE_OUT_SORT);
+            CR_NOTE_LAUNCH();
+            k_out_small_sort<<<1, 1024, smem, st>>>(pairs_out, (int)np, tmp);
+            prof_end(st, STAGE_OUT_SORT, 64.0 * np);
+        } else if (np > 0) {
             prof_begin(st, STAGE_OUT_SORT);
             if (pair_offsets) cudaMemsetAsync(segc, 0, (n + 1) * sizeof(uint32_t), st);
             CR_NOTE_LAUNCH();

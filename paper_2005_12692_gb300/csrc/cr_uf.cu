@@ -457,152 +457,217 @@ __global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restric
 }
 
 // ===========================================================================
-// Boruvka rounds with the elder rule
-// ===========================================================================
-__global__ void k_be_init(uint64_t *__restrict__ minE, int64_t ng) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < ng) minE[g] = ~0ull;
-}
-
-__global__ void k_be_min(const uint64_t *__restrict__ ek, const uint32_t *__restrict__ ea,
-                         const uint32_t *__restrict__ eb, int64_t ne, unsigned long long *__restrict__ minE) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne) return;
-    unsigned long long k = ek[i];
-    uint32_t a = ea[i], b = eb[i];
-    if (minE[a] > k) atomicMin(&minE[a], k);
-    if (minE[b] > k) atomicMin(&minE[b], k);
-}
-
-__global__ void k_be_tgt(const uint64_t *__restrict__ ek, const uint32_t *__restrict__ ea,
-                         const uint32_t *__restrict__ eb, int64_t ne, const uint64_t *__restrict__ minE,
-                         uint32_t *__restrict__ tgt) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne) return;
-    uint64_t k = ek[i];
-    uint32_t a = ea[i], b = eb[i];
-    if (minE[a] == k) tgt[a] = b;
-    if (minE[b] == k) tgt[b] = a;
-}
-
-// mode 0: primal (dim 0 pairs; mark dying edges in extra_mask);
-// mode 1: dual (pairs of dimension edim-1 between a facet and a top cube)
-__global__ void k_be_hook(int64_t ng, const uint64_t *__restrict__ minE, const uint32_t *__restrict__ tgt,
-                          const uint64_t *__restrict__ gkey, const uint32_t *__restrict__ gseg,
-                          uint32_t *__restrict__ hook, uint8_t *__restrict__ gdead, const Seg *__restrict__ segs,
-                          int mode, PairBuf pb, uint32_t flags, uint32_t *__restrict__ extra_mask) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
-    uint64_t m = minE[g];
-    if (m == ~0ull) { hook[g] = (uint32_t)g; return; }
-    uint32_t t = tgt[g];
-    if (gkey[t] < gkey[g]) {
-        hook[g] = t;
-        gdead[g] = 1;
-        uint32_t si = gseg[g];
-        if (mode == 0) {
-            uint64_t kb = gkey[g];
-            float b = key_value(kb), d = key_value(m);
-            if ((flags & CR_KEEP_ZERO) || b != d) emit_pair(pb, si, 0, b, d, key_L(kb), key_L(m), 0);
-            if (extra_mask) {
-                int64_t bit = segs[si].loff + key_L(m);
-                atomicOr(&extra_mask[bit >> 5], 1u << (bit & 31));
-            }
-        } else {
-            uint64_t kf = ~m, kc = ~gkey[g];
-            float b = key_value(kf), d = key_value(kc);
-            if ((flags & CR_KEEP_ZERO) || b != d)
-                emit_pair(pb, si, segs[si].edim - 1, b, d, key_L(kf), key_L(kc), 0);
-        }
-    } else {
-        hook[g] = (uint32_t)g;
-    }
-}
-
-__global__ void k_be_jump(uint32_t *__restrict__ hook, int64_t ng) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
-    uint32_t a = (uint32_t)g, b = hook[a];
-    int it = 0;
-    while (b != a && it++ < (1 << 24)) {
-        a = b;
-        b = hook[a];
-    }
-    hook[g] = a;
-}
-
-__global__ void k_be_relabel(const uint64_t *__restrict__ ek, const uint32_t *__restrict__ ea,
-                             const uint32_t *__restrict__ eb, int64_t ne, const uint32_t *__restrict__ hook,
-                             uint64_t *__restrict__ ok, uint32_t *__restrict__ oa, uint32_t *__restrict__ ob,
-                             unsigned long long *nout) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool keep = false;
-    uint32_t a = 0, b = 0;
-    uint64_t k = 0;
-    if (i < ne) {
-        a = hook[ea[i]];
-        b = hook[eb[i]];
-        k = ek[i];
-        keep = a != b;
-    }
-    int64_t j = warp_append(keep, nout);
-    if (keep) {
-        ok[j] = k;
-        oa[j] = a;
-        ob[j] = b;
-    }
-}
-
-// essential class of each image: the group that never died (primal only)
-__global__ void k_h0_essential(int64_t ng, const uint8_t *__restrict__ gdead, const uint64_t *__restrict__ gkey,
-                               const uint32_t *__restrict__ gseg, PairBuf pb) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ng || gdead[g]) return;
-    uint64_t k = gkey[g];
-    emit_pair(pb, gseg[g], 0, key_value(k), __int_as_float(0x7f800000), key_L(k), -1, CR_PAIR_ESSENTIAL);
-}
-
-// ===========================================================================
 // host drivers
 // ===========================================================================
 
 static inline unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-static int rounds_loop(UF &u, int64_t ng, int64_t ne, const Seg *segs, int mode, const PairBuf &pb,
-                       uint32_t flags, uint32_t *extra_mask, int *status, cudaStream_t st) {
+// ---------------------------------------------------------------------------
+// All Boruvka rounds in one cooperative kernel: the counts stay on the
+// device, phases are separated by a grid barrier with a bounded spin.
+// ---------------------------------------------------------------------------
+struct RoundArgs {
+    UF u;
+    const Seg *segs;
+    int mode;
+    PairBuf pb;
+    uint32_t flags;
+    uint32_t *extra_mask;
+    int *status;
+};
+
+// Barrier over the first `active` blocks of the grid; returns false when the
+// wait gave up (the status word then holds CR_ERR_TIMEOUT) or an error is set.
+__device__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen, unsigned int active, int *status) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        if (active > 1) {
+            unsigned int g = *gen;
+            __threadfence();
+            unsigned int arrived = atomicAdd(count, 1u);
+            if (arrived == active - 1) {
+                *count = 0;
+                __threadfence();
+                atomicAdd((unsigned int *)gen, 1u);
+            } else {
+                long long spins = 0;
+                while (*gen == g) {
+                    if (++spins > (1ll << 28)) {  // far beyond any phase of a round
+                        set_status(status, CR_ERR_TIMEOUT);
+                        s_ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)status) s_ok = 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+constexpr int UF_THREADS = 1024;
+
+// One round = four phases separated by grid barriers:
+//   A  (edges)  minE[g] <- min key of the edges at g   (minE was reset in C)
+//   B  (edges)  the edge attaining minE[g] decides g's hook by the elder rule
+//               and emits the death; only that edge writes g's entries
+//   C  (groups) chase hooks to the round's roots; reset minE for the next round
+//   D  (edges)  relabel endpoints to roots, drop edges inside a group, compact
+__global__ void __launch_bounds__(UF_THREADS) k_uf_rounds(RoundArgs A) {
+    UF &u = A.u;
+    unsigned int *bar_count = (unsigned int *)&u.cnt[4];
+    volatile unsigned int *bar_gen = (volatile unsigned int *)&u.cnt[5];
+    if (*(volatile int *)A.status) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned int active = gridDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    int64_t ng = (int64_t)*(volatile unsigned long long *)&u.cnt[0];
+    if (ng > u.max_groups) ng = u.max_groups;
+    unsigned long long *necnt[2] = {&u.cnt[1], &u.cnt[2]};
+    for (int64_t g = tid; g < ng; g += nthr) {
+        u.gdead[g] = 0;
+        u.hook[g] = (uint32_t)g;
+        u.minE[g] = ~0ull;
+    }
+    if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
     int cur = 0;
-    int rounds = 0;
-    cudaMemsetAsync(u.gdead, 0, (size_t)ng, st);
-    while (ne > 0) {
-        if (++rounds > 100000) return CR_ERR_TIMEOUT;
-        prof_begin(st, STAGE_UF_ROUND);
-        CR_NOTE_LAUNCH();
-        k_be_init<<<nb(ng), 256, 0, st>>>(u.minE, ng);
-        CR_NOTE_LAUNCH();
-        k_be_min<<<nb(ne), 256, 0, st>>>(u.ek[cur], u.ea[cur], u.eb[cur], ne, (unsigned long long *)u.minE);
-        CR_NOTE_LAUNCH();
-        k_be_tgt<<<nb(ne), 256, 0, st>>>(u.ek[cur], u.ea[cur], u.eb[cur], ne, u.minE, u.tgt);
-        CR_NOTE_LAUNCH();
-        k_be_hook<<<nb(ng), 256, 0, st>>>(ng, u.minE, u.tgt, u.gkey, u.gseg, u.hook, u.gdead, segs, mode, pb, flags,
-                                          extra_mask);
-        CR_NOTE_LAUNCH();
-        k_be_jump<<<nb(ng), 256, 0, st>>>(u.hook, ng);
-        cudaMemsetAsync(&u.cnt[2], 0, sizeof(unsigned long long), st);
-        CR_NOTE_LAUNCH();
-        k_be_relabel<<<nb(ne), 256, 0, st>>>(u.ek[cur], u.ea[cur], u.eb[cur], ne, u.hook, u.ek[cur ^ 1],
-                                             u.ea[cur ^ 1], u.eb[cur ^ 1], &u.cnt[2]);
-        prof_end(st, STAGE_UF_ROUND, 3.0 * 16.0 * ne + 40.0 * ng);
-        cudaMemcpyAsync(&u.hcnt[2], &u.cnt[2], sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-        if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
-        ne = (int64_t)u.hcnt[2];
+    for (int round = 0; round < (1 << 20); round++) {
+        int64_t ne = (int64_t)*(volatile unsigned long long *)necnt[cur];
+        if (ne > u.max_edges) ne = u.max_edges;
+        if (ne == 0) break;
+        if (tid == 0) *necnt[cur ^ 1] = 0;
+        const uint64_t *ek = u.ek[cur];
+        const uint32_t *ea = u.ea[cur], *eb = u.eb[cur];
+        // A
+        for (int64_t i = tid; i < ne; i += nthr) {
+            unsigned long long k = ek[i];
+            uint32_t a = ea[i], b = eb[i];
+            if (u.minE[a] > k) atomicMin((unsigned long long *)&u.minE[a], k);
+            if (u.minE[b] > k) atomicMin((unsigned long long *)&u.minE[b], k);
+        }
+        if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
+        // B
+        for (int64_t i = tid; i < ne; i += nthr) {
+            uint64_t k = ek[i];
+            uint32_t ends[2] = {ea[i], eb[i]};
+            for (int s2 = 0; s2 < 2; s2++) {
+                uint32_t g = ends[s2], t = ends[s2 ^ 1];
+                if (u.minE[g] != k || !(u.gkey[t] < u.gkey[g])) continue;
+                u.hook[g] = t;
+                u.gdead[g] = 1;
+                uint32_t si = u.gseg[g];
+                if (A.mode == 0) {
+                    uint64_t kb = u.gkey[g];
+                    float bv = key_value(kb), dv = key_value(k);
+                    if ((A.flags & CR_KEEP_ZERO) || bv != dv) emit_pair(A.pb, si, 0, bv, dv, key_L(kb), key_L(k), 0);
+                    if (A.extra_mask) {
+                        int64_t bit = A.segs[si].loff + key_L(k);
+                        atomicOr(&A.extra_mask[bit >> 5], 1u << (bit & 31));
+                    }
+                } else {
+                    uint64_t kf = ~k, kc = ~u.gkey[g];
+                    float bv = key_value(kf), dv = key_value(kc);
+                    if ((A.flags & CR_KEEP_ZERO) || bv != dv)
+                        emit_pair(A.pb, si, A.segs[si].edim - 1, bv, dv, key_L(kf), key_L(kc), 0);
+                }
+            }
+        }
+        if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
+        // C
+        for (int64_t g = tid; g < ng; g += nthr) {
+            uint32_t b = u.hook[g];
+            if (b != (uint32_t)g) {
+                int it = 0;
+                while (it++ < (1 << 24)) {
+                    uint32_t c = u.hook[b];
+                    if (c == b) break;
+                    b = c;
+                }
+                u.hook[g] = b;
+            }
+            u.minE[g] = ~0ull;
+        }
+        if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
+        // D
+        {
+            uint64_t *ok = u.ek[cur ^ 1];
+            uint32_t *oa = u.ea[cur ^ 1], *ob = u.eb[cur ^ 1];
+            const int64_t wbase = tid - lane;
+            for (int64_t base = wbase; base < ne; base += nthr) {
+                int64_t i = base + lane;
+                bool keep = false;
+                uint32_t a = 0, b = 0;
+                uint64_t k = 0;
+                if (i < ne) {
+                    a = u.hook[ea[i]];
+                    b = u.hook[eb[i]];
+                    k = ek[i];
+                    keep = a != b;
+                }
+                int64_t j = warp_append(keep, necnt[cur ^ 1]);
+                if (keep) {
+                    ok[j] = k;
+                    oa[j] = a;
+                    ob[j] = b;
+                }
+            }
+        }
+        if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
         cur ^= 1;
     }
-    return CR_OK;
+}
+
+// the essential class of each image: the group that never died (primal only)
+__global__ void k_h0_essential_dev(const unsigned long long *ngp, int64_t max_groups, const uint8_t *__restrict__ gdead,
+                                   const uint64_t *__restrict__ gkey, const uint32_t *__restrict__ gseg, PairBuf pb) {
+    int64_t ng = (int64_t)*ngp;
+    if (ng > max_groups) ng = max_groups;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        if (gdead[g]) continue;
+        uint64_t k = gkey[g];
+        emit_pair(pb, gseg[g], 0, key_value(k), __int_as_float(0x7f800000), key_L(k), -1, CR_PAIR_ESSENTIAL);
+    }
+}
+
+static int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+static int rounds_coop(UF &u, int64_t work_estimate, const Seg *segs, int mode, const PairBuf &pb, uint32_t flags,
+                       uint32_t *extra_mask, int *status, cudaStream_t st) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uf_rounds, UF_THREADS, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    int64_t maxb = (int64_t)(per_sm < 1 ? 1 : 1) * sm_count();  // one block per SM keeps barriers short
+    int64_t want = work_estimate / (8 * UF_THREADS) + 1;
+    int blocks = (int)(want < maxb ? want : maxb);
+    if (blocks < 1) blocks = 1;
+    RoundArgs A{u, segs, mode, pb, flags, extra_mask, status};
+    void *args[] = {&A};
+    prof_begin(st, STAGE_UF_ROUND);
+    CR_NOTE_LAUNCH();
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_uf_rounds, dim3(blocks), dim3(UF_THREADS), args, 0, st);
+    prof_end(st, STAGE_UF_ROUND, 0.0);
+    return e == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
 int run_h0(const float *img, const Seg *segs, int nseg, int64_t vtot, UF &u, const PairBuf &pb, uint32_t flags,
            uint32_t *extra_mask, int *status, cudaStream_t st) {
-    cudaMemsetAsync(u.cnt, 0, 3 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(u.cnt, 0, 8 * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_H0_STENCIL);
     CR_NOTE_LAUNCH();
     k_h0_stencil<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, u.dd, status, pb, flags);
@@ -625,21 +690,16 @@ int run_h0(const float *img, const Seg *segs, int nseg, int64_t vtot, UF &u, con
     k_h0_cross<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, u.dd, u.ek[0], u.ea[0], u.eb[0], &u.cnt[1],
                                          u.max_edges, &u.cnt[0], status);
     prof_end(st, STAGE_H0_CROSS, 9.0 * vtot);
-    cudaMemcpyAsync(u.hcnt, u.cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
-    int64_t ng = (int64_t)u.hcnt[0], ne = (int64_t)u.hcnt[1];
-    if (ng > u.max_groups) { set_host_detail(SITE_GROUPS); return CR_ERR_WORKSPACE; }
-    if (ne > u.max_edges) { set_host_detail(SITE_EDGES); return CR_ERR_WORKSPACE; }
-    int rc = rounds_loop(u, ng, ne, segs, 0, pb, flags, extra_mask, status, st);
+    int rc = rounds_coop(u, vtot, segs, 0, pb, flags, extra_mask, status, st);
     if (rc) return rc;
     CR_NOTE_LAUNCH();
-    k_h0_essential<<<nb(ng), 256, 0, st>>>(ng, u.gdead, u.gkey, u.gseg, pb);
+    k_h0_essential_dev<<<2 * sm_count(), 256, 0, st>>>(&u.cnt[0], u.max_groups, u.gdead, u.gkey, u.gseg, pb);
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
 int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, UF &u, const PairBuf &pb,
              uint32_t flags, int *status, cudaStream_t st) {
-    cudaMemsetAsync(u.cnt, 0, 3 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(u.cnt, 0, 8 * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_DUAL_STENCIL);
     CR_NOTE_LAUNCH();
     k_dual_stencil<<<nb(ctot), 256, 0, st>>>(img, segs, nseg, ctot, u.lab, u.dd, pb, flags);
@@ -662,12 +722,7 @@ int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t 
     k_dual_cross<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, u.dd, u.ek[0], u.ea[0], u.eb[0], &u.cnt[1],
                                            u.max_edges, &u.cnt[0], status);
     prof_end(st, STAGE_DUAL_CROSS, 4.0 * vtot + 5.0 * ctot);
-    cudaMemcpyAsync(u.hcnt, u.cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
-    int64_t ng = (int64_t)u.hcnt[0], ne = (int64_t)u.hcnt[1];
-    if (ng > u.max_groups) { set_host_detail(SITE_GROUPS); return CR_ERR_WORKSPACE; }
-    if (ne > u.max_edges) { set_host_detail(SITE_EDGES); return CR_ERR_WORKSPACE; }
-    return rounds_loop(u, ng, ne, segs, 1, pb, flags, nullptr, status, st);
+    return rounds_coop(u, vtot, segs, 1, pb, flags, nullptr, status, st);
 }
 
 }  // namespace cr
