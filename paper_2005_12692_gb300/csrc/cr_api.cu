@@ -22,7 +22,7 @@ void set_host_detail(int site) { g_detail = site; }
 // ---------------------------------------------------------------------------
 struct HostPlan {
     std::vector<Seg> segs;
-    int64_t vtot = 0, ctot = 0, cells = 0;
+    int64_t vtot = 0, ctot = 0, cells = 0, ntiles = 0;
     int64_t max_face_per_image = 0;
     bool any_h0 = false, any_dual = false, any_mid = false;
     int nseg_bits = 0;
@@ -74,6 +74,12 @@ static int plan_images(const int64_t *const *shapes_rows, int n, int ndim, int m
         if (want_dual) ncell = S.edim == 3 ? (nx - 1) * (ny - 1) * (nz - 1) : (nx - 1) * (ny - 1);
         S.coff = coff;
         S.ncell = ncell;
+        S.tiles_x = (int32_t)((nx + TILE_X - 1) / TILE_X);
+        S.tiles_y = (int32_t)((ny + TILE_Y - 1) / TILE_Y);
+        S.tiles_z = (int32_t)((nz + TILE_Z - 1) / TILE_Z);
+        S.pad = 0;
+        S.toff = P.ntiles;
+        P.ntiles += (int64_t)S.tiles_x * S.tiles_y * S.tiles_z;
         P.any_h0 |= want_h0 || want_mid;
         P.any_dual |= ncell > 0;
         P.any_mid |= want_mid;
@@ -132,7 +138,7 @@ static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
         red_geometry(P, nw, ml);
         int64_t cols = worst ? 3 * P.vtot : (3 * P.vtot) / 8 + 4096;
         int64_t arena = worst ? 12 * P.vtot : 2 * P.vtot + (1 << 20);
-        int64_t pool = worst ? 8 * P.vtot : P.vtot + (1 << 20);
+        int64_t pool = worst ? 8 * P.vtot : 2 * P.vtot + (1 << 22);
         h1 = al((size_t)cols * 32) + al(radix_temp_bytes(cols)) + al((size_t)(3 * P.vtot) * 4) +
              al((size_t)((3 * P.vtot + 31) / 32) * 4) +
              al((size_t)arena * 8) + al((size_t)pool * 8) + al((size_t)nw * 2 * ml * 8) + (1 << 20);
@@ -303,7 +309,8 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         }
         u.max_edges = max_edges;
         if (!R.ok) return CR_ERR_WORKSPACE;
-        rc = run_h0(imgs, segs, n, P.vtot, u, pb, flags, P.any_mid ? extra : nullptr, status, st);
+        rc = run_h0(imgs, segs, P.segs.data(), n, P.vtot, P.ntiles, u, pb, flags, P.any_mid ? extra : nullptr,
+                    status, st);
         if (rc) return rc;
     }
 

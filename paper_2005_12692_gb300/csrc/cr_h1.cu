@@ -367,6 +367,7 @@ struct WarpSmem {
     int q[DMAX];
     int pc[DMAX + 1];
     uint64_t win[32];    // base[wbeg .. wbeg+32): cached head of the base
+    uint64_t mwin[32];   // the same for the middle level
     uint32_t nv[64];     // ord32 values of the 4x4x4 vertices around a face (0 = outside)
     uint8_t ndd[64];     // their primal hook codes
     uint32_t xm[4];      // later-round H0 death bits of the face's four edges
@@ -460,6 +461,36 @@ __device__ uint64_t apparent_warp(const Img3 &I, const Seg &S, uint64_t fk, Warp
     return best;
 }
 
+// Per-lane version for the lookahead: the apparent column of face fk by
+// direct loads; false if fk is not an apparent pivot.
+__device__ bool apparent_lane(const Img3 &I, const Seg &S, uint64_t fk, uint64_t &c1, uint64_t &c2, uint64_t &c3,
+                              int &k) {
+    int64_t bit = S.loff + key_L(fk);
+    if (!((__ldcg(&I.appmask[bit >> 5]) >> (bit & 31)) & 1u)) return false;
+    int fm, c[3];
+    decode_L(S, key_L(fk), fm, c);
+    int ea, ec[3];
+    face_max_facet(I, S, fm, c, ea, ec);
+    uint64_t cf[4];
+    int n = edge_cofacets(I, S, ea, ec, cf);
+    sort4(cf, n);
+    c1 = n > 1 ? cf[1] : ~0ull;
+    c2 = n > 2 ? cf[2] : ~0ull;
+    c3 = n > 3 ? cf[3] : ~0ull;
+    k = n;
+    return true;
+}
+
+// Lookahead cache: one entry per lane, filled for the next entries of the
+// working column in one parallel step, so that most pivots need no
+// dependent global lookup.  kind 1 = apparent pivot (column tail c1..c3),
+// kind 2 = owned by column `own` with published version `ver` (a snapshot,
+// re-validated when the column is staged).
+struct Look {
+    uint64_t key, c1, c2, c3, ver;
+    int kind, k, own;
+};
+
 // ---------------------------------------------------------------------------
 // Working column of one warp.  Entries below the current pivot are always
 // cancelled (an added column shares the pivot, all its other entries are
@@ -469,6 +500,13 @@ __device__ uint64_t apparent_warp(const Img3 &I, const Seg &S, uint64_t fk, Warp
 // whose symmetric difference is the column.  A small addition is a
 // shared-memory merge into delta; base is rebuilt only when delta fills.
 // ---------------------------------------------------------------------------
+// The column is base xor mid xor delta.  The middle level (global, at most
+// MIDMAX entries) is used once the base is long: delta flushes then touch
+// only the middle level, and the base is rebuilt when the middle fills.
+constexpr int MIDMAX = 8192;
+constexpr int MID_ON = 8192;
+constexpr int MIDCAP = 2 * MIDMAX + DMAX;
+
 struct Work {
     uint64_t *g[2];  // this warp's global buffers (base lives in g[bown])
     int cap;
@@ -476,6 +514,9 @@ struct Work {
     int nb, start;
     int sb, dh, nd;
     int wbeg;        // start of the cached window of the base (-1: none)
+    uint64_t *mg[2]; // middle level buffers (null until first needed)
+    int mown, nm, mstart, mwbeg;
+    bool mid_on;
 };
 
 // diagnostic counters (cnt[8..15]): iterations, apparent additions, column
@@ -484,10 +525,13 @@ struct Work {
 struct RedStats {
     unsigned long long it = 0, app = 0, add = 0, merged = 0, take = 0, retry = 0, flush = 0, maxit = 0;
     unsigned long long t[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // cycles per phase (diagnostic builds)
+    bool lng = false;
 };
 #ifdef CR_H1_TIMING
+// only iterations of long column runs (beyond 16384) are timed: the critical path
+__device__ bool g_long_iter_dummy;
 #define TMARK(v) long long v = clock64()
-#define TADD(st, i, v) (st).t[i] += (unsigned long long)(clock64() - (v))
+#define TADD(st, i, v) ((st).lng ? (void)((st).t[i] += (unsigned long long)(clock64() - (v))) : (void)0)
 #else
 #define TMARK(v)
 #define TADD(st, i, v)
@@ -615,28 +659,79 @@ __device__ int insert_merge(const uint64_t *A, int na, const uint64_t *D, int nD
 }
 
 // fold delta into base (base <- base[start..nb) xor delta[dh..nd))
-__device__ bool flush_delta(const RedParams &R, Work &W, WarpSmem &sm, RedStats &st) {
-    int nd = W.nd - W.dh;
-    if (nd == 0) return true;
+// base <- base[start..nb) xor mid[mstart..nm); the middle level becomes empty
+__device__ bool merge_mid(const RedParams &R, Work &W, RedStats &st) {
+    int nmid = W.nm - W.mstart;
+    if (nmid == 0) return true;
     int na = W.nb - W.start;
     const uint64_t *A = W.g[W.bown] + W.start;
-    if ((int64_t)na + nd > W.cap && !grow_to(R, W, (int64_t)na + nd)) return false;
+    if ((int64_t)na + nmid > W.cap && !grow_to(R, W, (int64_t)na + nmid)) return false;
     int x = W.bown ^ 1;
-    TMARK(tf);
-    int n = insert_merge<true>(A, na, &sm.d[W.sb][W.dh], nd, W.g[x], sm);
-    TADD(st, 5, tf);
+    int n = warp_xor<true, true>(A, na, W.mg[W.mown] + W.mstart, nmid, W.g[x], W.cap);
     __threadfence_block();
+    if (n < 0) return false;
     W.bown = x;
     W.nb = n;
     W.start = 0;
-    W.dh = W.nd = 0;
     W.wbeg = -1;
-    st.flush++;
-    st.merged += (unsigned long long)(na + nd);
+    W.nm = W.mstart = 0;
+    W.mwbeg = -1;
+    st.merged += (unsigned long long)(na + nmid);
     return true;
 }
 
-// the pivot (earliest face) of the working column, cancelling equal heads; ~0 if empty
+// fold delta into the middle level (long columns) or into the base
+__device__ bool flush_delta(const RedParams &R, Work &W, WarpSmem &sm, RedStats &st) {
+    int nd = W.nd - W.dh;
+    if (nd == 0) return true;
+    if (!W.mid_on && W.nb - W.start > MID_ON) {
+        if (!W.mg[0]) {
+            const int lane = threadIdx.x & 31;
+            unsigned long long off = 0;
+            if (lane == 0) off = atomicAdd(R.pool_top, (unsigned long long)(2 * MIDCAP));
+            off = __shfl_sync(0xFFFFFFFFu, off, 0);
+            if ((int64_t)(off + 2 * MIDCAP) > R.pool_cap) return false;
+            W.mg[0] = R.pool + off;
+            W.mg[1] = R.pool + off + MIDCAP;
+        }
+        W.mid_on = true;
+        W.mown = 0;
+        W.nm = W.mstart = 0;
+        W.mwbeg = -1;
+    }
+    TMARK(tf);
+    if (W.mid_on) {
+        int nmid = W.nm - W.mstart;
+        int x = W.mown ^ 1;
+        int n = insert_merge<true>(W.mg[W.mown] + W.mstart, nmid, &sm.d[W.sb][W.dh], nd, W.mg[x], sm);
+        __threadfence_block();
+        W.mown = x;
+        W.nm = n;
+        W.mstart = 0;
+        W.mwbeg = -1;
+        W.dh = W.nd = 0;
+        st.merged += (unsigned long long)(nmid + nd);
+        if (W.nm > MIDMAX && !merge_mid(R, W, st)) return false;
+    } else {
+        int na = W.nb - W.start;
+        const uint64_t *A = W.g[W.bown] + W.start;
+        if ((int64_t)na + nd > W.cap && !grow_to(R, W, (int64_t)na + nd)) return false;
+        int x = W.bown ^ 1;
+        int n = insert_merge<true>(A, na, &sm.d[W.sb][W.dh], nd, W.g[x], sm);
+        __threadfence_block();
+        W.bown = x;
+        W.nb = n;
+        W.start = 0;
+        W.dh = W.nd = 0;
+        W.wbeg = -1;
+        st.merged += (unsigned long long)(na + nd);
+    }
+    TADD(st, 5, tf);
+    st.flush++;
+    return true;
+}
+
+// heads of the levels, through 32-entry windows in shared memory
 __device__ __forceinline__ uint64_t base_head(Work &W, WarpSmem &sm) {
     if (W.start >= W.nb) return ~0ull;
     if (W.wbeg < 0 || W.start >= W.wbeg + 32) {
@@ -649,25 +744,53 @@ __device__ __forceinline__ uint64_t base_head(Work &W, WarpSmem &sm) {
     }
     return sm.win[W.start - W.wbeg];
 }
+__device__ __forceinline__ uint64_t mid_head(Work &W, WarpSmem &sm) {
+    if (!W.mid_on || W.mstart >= W.nm) return ~0ull;
+    if (W.mwbeg < 0 || W.mstart >= W.mwbeg + 32) {
+        const int lane = threadIdx.x & 31;
+        int i = W.mstart + lane;
+        __syncwarp();
+        sm.mwin[lane] = i < W.nm ? ld_cg(W.mg[W.mown] + i) : ~0ull;
+        __syncwarp();
+        W.mwbeg = W.mstart;
+    }
+    return sm.mwin[W.mstart - W.mwbeg];
+}
 
-__device__ uint64_t pivot_of(Work &W, WarpSmem &sm, bool &from_base) {
+// the pivot (earliest face) of base xor mid xor delta; src = 1 base, 2 mid, 0 delta; ~0 if empty
+__device__ uint64_t pivot_of(Work &W, WarpSmem &sm, int &src) {
     for (;;) {
         uint64_t hb = base_head(W, sm);
+        uint64_t hm = mid_head(W, sm);
         uint64_t hd = W.dh < W.nd ? sm.d[W.sb][W.dh] : ~0ull;
-        if (hb == hd) {
-            if (hb == ~0ull) return ~0ull;
-            W.start++;
-            W.dh++;
+        uint64_t m = hb < hm ? hb : hm;
+        m = m < hd ? m : hd;
+        if (m == ~0ull) return ~0ull;
+        int cnt = (hb == m) + (hm == m) + (hd == m);
+        if (cnt == 2) {  // two copies cancel
+            if (hb == m) W.start++;
+            if (hm == m) W.mstart++;
+            if (hd == m) W.dh++;
             continue;
         }
-        from_base = hb < hd;
-        return from_base ? hb : hd;
+        if (cnt == 3) {  // three copies: two cancel, the delta copy remains
+            W.start++;
+            W.mstart++;
+        }
+        src = (hd == m) ? 0 : ((hb == m) ? 1 : 2);
+        return m;
     }
 }
 
+__device__ __forceinline__ void remove_pivot(Work &W, int src) {
+    if (src == 1) W.start++;
+    else if (src == 2) W.mstart++;
+    else W.dh++;
+}
+
 // add the column staged in sm.c[0..m) whose first entry is the current pivot
-__device__ bool add_staged(const RedParams &R, Work &W, WarpSmem &sm, bool from_base, int m, RedStats &st) {
-    if (from_base) W.start++; else W.dh++;
+__device__ bool add_staged(const RedParams &R, Work &W, WarpSmem &sm, int src, int m, RedStats &st) {
+    remove_pivot(W, src);
     int mc = m - 1;
     if (W.nd - W.dh + mc > DMAX) {
         if (!flush_delta(R, W, sm, st)) return false;
@@ -679,13 +802,49 @@ __device__ bool add_staged(const RedParams &R, Work &W, WarpSmem &sm, bool from_
     return true;
 }
 
+__device__ void look_refill(const RedParams &R, const Seg &S, Work &W, WarpSmem &sm, Look &L) {
+    const int lane = threadIdx.x & 31;
+    uint64_t cand = ~0ull;
+    if (lane < 10) {
+        int i = W.start + lane;
+        if (i < W.nb) cand = ld_cg(W.g[W.bown] + i);
+    } else if (lane < 20) {
+        int i = W.mstart + lane - 10;
+        if (W.mid_on && i < W.nm) cand = ld_cg(W.mg[W.mown] + i);
+    } else {
+        int i = W.dh + lane - 20;
+        if (i < W.nd) cand = sm.d[W.sb][i];
+    }
+    L.key = ~0ull;
+    L.kind = 0;
+    if (cand == ~0ull) return;
+    uint64_t c1, c2, c3;
+    int k;
+    if (apparent_lane(R.I, S, cand, c1, c2, c3, k)) {
+        L.key = cand;
+        L.kind = 1;
+        L.c1 = c1;
+        L.c2 = c2;
+        L.c3 = c3;
+        L.k = k;
+        return;
+    }
+    int o = __ldcg(&R.P[S.loff + key_L(cand)]);
+    if (o >= 0) {
+        L.key = cand;
+        L.kind = 2;
+        L.own = o;
+        L.ver = __ldcg(&R.cur[o]);
+    }
+}
+
 // add a short column x0 < x1 < x2 < x3 (k <= 4 entries, x0 = current pivot;
 // unused entries are ~0): one pass over delta, no scratch arrays.  Lane e
 // locates entry e+1 in delta; the results are broadcast by shuffles.
-__device__ bool add_small(const RedParams &R, Work &W, WarpSmem &sm, bool from_base, uint64_t x1, uint64_t x2,
+__device__ bool add_small(const RedParams &R, Work &W, WarpSmem &sm, int src, uint64_t x1, uint64_t x2,
                           uint64_t x3, int k, RedStats &st) {
     const int lane = threadIdx.x & 31;
-    if (from_base) W.start++; else W.dh++;
+    remove_pivot(W, src);
     const int m = k - 1;
     if (W.nd - W.dh + m > DMAX) {
         if (!flush_delta(R, W, sm, st)) return false;
@@ -729,17 +888,33 @@ __device__ bool add_small(const RedParams &R, Work &W, WarpSmem &sm, bool from_b
 }
 
 // add a published column (arena, length len, first entry = current pivot)
-__device__ bool add_arena(const RedParams &R, Work &W, WarpSmem &sm, bool from_base, const uint64_t *C, int len,
+__device__ bool add_arena(const RedParams &R, Work &W, WarpSmem &sm, int src, const uint64_t *C, int len,
                           RedStats &st) {
     const int lane = threadIdx.x & 31;
     if (len - 1 <= DMAX) {
         for (int k = lane; k < len; k += 32) sm.c[k] = ld_cg(C + k);
         __syncwarp();
-        return add_staged(R, W, sm, from_base, len, st);
+        return add_staged(R, W, sm, src, len, st);
     }
     // a long column: fold delta into base, then merge base with the column's tail
-    if (from_base) W.start++; else W.dh++;
+    remove_pivot(W, src);
     if (!flush_delta(R, W, sm, st)) return false;
+    if (W.mid_on && len - 1 <= MIDMAX) {
+        // long column, long working column: fold the column into the middle level
+        int nmid = W.nm - W.mstart;
+        int x = W.mown ^ 1;
+        int n = warp_xor<true, true>(W.mg[W.mown] + W.mstart, nmid, C + 1, len - 1, W.mg[x], MIDCAP);
+        __threadfence_block();
+        if (n < 0) return false;
+        W.mown = x;
+        W.nm = n;
+        W.mstart = 0;
+        W.mwbeg = -1;
+        st.merged += (unsigned long long)(nmid + len);
+        if (W.nm > MIDMAX && !merge_mid(R, W, st)) return false;
+        return true;
+    }
+    if (W.mid_on && !merge_mid(R, W, st)) return false;
     int na = W.nb - W.start;
     const uint64_t *A = W.g[W.bown] + W.start;
     if ((int64_t)na + len - 1 > W.cap && !grow_to(R, W, (int64_t)na + len - 1)) return false;
@@ -758,8 +933,13 @@ __device__ bool add_arena(const RedParams &R, Work &W, WarpSmem &sm, bool from_b
 // publish the working column as column j's current version
 __device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &sm, RedStats &st) {
     const int lane = threadIdx.x & 31;
-    if (W.nb - W.start > 0 && W.nd - W.dh > 0)
+    if (W.mid_on && W.nm - W.mstart > 0) {
         if (!flush_delta(R, W, sm, st)) return false;
+        if (!merge_mid(R, W, st)) return false;
+    } else if (W.nb - W.start > 0 && W.nd - W.dh > 0) {
+        if (!flush_delta(R, W, sm, st)) return false;
+    }
+    if (W.mid_on && W.nm - W.mstart > 0 && !merge_mid(R, W, st)) return false;
     int nbase = W.nb - W.start, nd = W.nd - W.dh;
     int n = nbase + nd;
     unsigned long long off = 0;
@@ -787,9 +967,12 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
     RedStats st;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     Work W;
+    Look look;
     W.g[0] = R.scratch + wid * 2 * (int64_t)R.maxlen;
     W.g[1] = W.g[0] + R.maxlen;
     W.cap = R.maxlen;
+    W.mg[0] = W.mg[1] = nullptr;
+    W.mid_on = false;
     const int64_t CAP = (int64_t)1 << 24;
     for (;;) {
         unsigned long long jj = 0;
@@ -813,39 +996,85 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
             W.bown = 0;
             W.nb = W.start = 0;
             W.wbeg = -1;
+            W.mid_on = false;
+            W.nm = W.mstart = 0;
+            W.mwbeg = -1;
             __syncwarp();
         }
+        look.key = ~0ull;
+        look.kind = 0;
+        bool refilled = false;
         int64_t it = 0;
         for (;;) {
             if (++it > CAP) { if (lane == 0) set_status(R.status, CR_ERR_TIMEOUT); flush_stats(R, st); return; }
             st.it++;
             if ((unsigned long long)it > st.maxit) st.maxit = (unsigned long long)it;
-            bool from_base = false;
+            st.lng = it > 16384;
+#ifdef CR_H1_TIMING
+            if (st.lng) st.t[7]++;
+#endif
+            int src = 0;
             TMARK(t0);
-            uint64_t p = pivot_of(W, sm, from_base);
+            uint64_t p = pivot_of(W, sm, src);
             TADD(st, 0, t0);
             if (p == ~0ull) { if (lane == 0) set_status(R.status, CR_ERR_INTERNAL); break; }
             int64_t gidx = S.loff + key_L(p);
-            uint64_t cf[4];
-            int k = 0;
             TMARK(t1);
-            uint64_t ak = apparent_warp(R.I, S, p, sm, cf, k);
-            TADD(st, 1, t1);
-            if (ak) {
-                st.app++;
-                TMARK(t2);
-                bool okadd = add_small(R, W, sm, from_base, k > 1 ? cf[1] : ~0ull, k > 2 ? cf[2] : ~0ull,
-                                       k > 3 ? cf[3] : ~0ull, k, st);
-                TADD(st, 2, t2);
-                if (!okadd) {
-                    if (lane == 0) fail_ws(R.status, SITE_POOL);
-                    flush_stats(R, st);
-                    return;
-                }
-                continue;
+            unsigned hit = __ballot_sync(0xFFFFFFFFu, look.key == p);
+            if (!hit && !refilled) {
+                look_refill(R, S, W, sm, look);
+                refilled = true;
+                hit = __ballot_sync(0xFFFFFFFFu, look.key == p);
             }
+            int hkind = 0, hown = -1;
+            unsigned long long hver = 0;
+            if (hit) {
+                int hl = __ffs(hit) - 1;  // cache lane holding the pivot
+                hkind = __shfl_sync(0xFFFFFFFFu, look.kind, hl);
+                if (hkind == 1) {
+                    uint64_t c1 = __shfl_sync(0xFFFFFFFFu, look.c1, hl);
+                    uint64_t c2 = __shfl_sync(0xFFFFFFFFu, look.c2, hl);
+                    uint64_t c3 = __shfl_sync(0xFFFFFFFFu, look.c3, hl);
+                    int kk = __shfl_sync(0xFFFFFFFFu, look.k, hl);
+                    TADD(st, 1, t1);
+                    st.app++;
+                    TMARK(t2);
+                    bool okadd = add_small(R, W, sm, src, c1, c2, c3, kk, st);
+                    TADD(st, 2, t2);
+                    if (!okadd) {
+                        if (lane == 0) fail_ws(R.status, SITE_POOL);
+                        flush_stats(R, st);
+                        return;
+                    }
+                    refilled = false;
+                    continue;
+                }
+                hown = __shfl_sync(0xFFFFFFFFu, look.own, hl);
+                hver = __shfl_sync(0xFFFFFFFFu, look.ver, hl);
+                if (lane == hl) look.key = ~0ull;  // used once; a stale snapshot is re-read directly
+            } else {
+                uint64_t cf[4];
+                int k = 0;
+                uint64_t ak = apparent_warp(R.I, S, p, sm, cf, k);
+                if (ak) {
+                    TADD(st, 1, t1);
+                    st.app++;
+                    TMARK(t2);
+                    bool okadd = add_small(R, W, sm, src, k > 1 ? cf[1] : ~0ull, k > 2 ? cf[2] : ~0ull,
+                                           k > 3 ? cf[3] : ~0ull, k, st);
+                    TADD(st, 2, t2);
+                    if (!okadd) {
+                        if (lane == 0) fail_ws(R.status, SITE_POOL);
+                        flush_stats(R, st);
+                        return;
+                    }
+                    refilled = false;
+                    continue;
+                }
+            }
+            TADD(st, 1, t1);
             TMARK(t3);
-            int o = __ldcg(&R.P[gidx]);
+            int o = hkind == 2 ? hown : __ldcg(&R.P[gidx]);
             if (o < 0) {
                 TMARK(t6);
                 bool okpub = publish_work(R, j, W, sm, st);
@@ -868,9 +1097,10 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
                 prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
                 if (prev != o) { st.retry++; continue; }
                 st.take++;
-                p = pivot_of(W, sm, from_base);  // publishing may have folded delta into base
+                p = pivot_of(W, sm, src);  // publishing may have folded delta into base
             }
-            unsigned long long ver = __ldcg(&R.cur[o]);
+            unsigned long long ver = (hkind == 2 && !takeover) ? hver : __ldcg(&R.cur[o]);
+            refilled = false;
             unsigned long long off = ver >> 24;
             int len = (int)(ver & 0xFFFFFFull);
             if (len == 0) continue;
@@ -883,14 +1113,14 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
                 st.add++;
                 TADD(st, 3, t3);
                 TMARK(t4);
-                ok2 = add_staged(R, W, sm, from_base, len, st);
+                ok2 = add_staged(R, W, sm, src, len, st);
                 TADD(st, 4, t4);
             } else {
                 if (ld_cg(&R.arena[off]) != p) { st.retry++; continue; }
                 st.add++;
                 TADD(st, 3, t3);
                 TMARK(t4);
-                ok2 = add_arena(R, W, sm, from_base, R.arena + off, len, st);
+                ok2 = add_arena(R, W, sm, src, R.arena + off, len, st);
                 TADD(st, 4, t4);
             }
             if (!ok2) {

@@ -29,7 +29,12 @@ struct Seg {
     int64_t ncell; // number of top cubes of this image
     int32_t nx, ny, nz;
     int32_t edim;  // effective dimension (leading unit extents dropped), 0..3
+    int64_t toff;  // first tile of this image in the tiled launches
+    int32_t tiles_x, tiles_y, tiles_z, pad;
 };
+
+// tiles of the 2.5D stencil kernels: TILE_X x TILE_Y voxels marching TILE_Z planes
+constexpr int TILE_X = 32, TILE_Y = 8, TILE_Z = 16;
 
 // ---------------------------------------------------------------------------
 // keys
@@ -141,8 +146,8 @@ struct UF {
     unsigned long long *cnt;   // device counters [0] groups, [1] edges, [2] edges after a round
     unsigned long long *hcnt;  // host mirror
 };
-int run_h0(const float *img, const Seg *segs, int nseg, int64_t vtot, UF &u, const PairBuf &pb, uint32_t flags,
-           uint32_t *extra_mask, int *status, cudaStream_t st);
+int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ntiles, UF &u,
+           const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status, cudaStream_t st);
 int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, UF &u, const PairBuf &pb,
              uint32_t flags, int *status, cudaStream_t st);
 

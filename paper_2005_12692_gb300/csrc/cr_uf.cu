@@ -23,6 +23,8 @@
 // pointer jumping yields basins, and only edges between different basins are
 // written out for the later rounds.
 #include "cr_internal.cuh"
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 namespace cr {
 
@@ -107,6 +109,281 @@ __global__ void k_h0_stencil(const float *__restrict__ img, const Seg *__restric
         parent[gv] = (uint32_t)gv;
         dd[gv] = 0;
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same stencil, tiled: a block owns TILE_X x TILE_Y voxels of one image
+// and marches TILE_Z planes in z.  Each xy-plane is staged with a one-voxel
+// halo in shared memory; the z neighbours come from registers.  All index
+// arithmetic is 32-bit within the image.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int seg_of_tile(const Seg *segs, int n, int64_t t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].toff <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tiled(const float *__restrict__ img,
+                                                                    const Seg *__restrict__ segs, int nseg,
+                                                                    uint32_t *__restrict__ parent,
+                                                                    uint8_t *__restrict__ dd, int *status, PairBuf pb,
+                                                                    uint32_t flags) {
+    __shared__ uint32_t pl[TILE_Y + 2][TILE_X + 2];
+    __shared__ int s_si;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_si = seg_of_tile(segs, nseg, blockIdx.x);
+    __syncthreads();
+    const int si = s_si;
+    const Seg S = segs[si];
+    uint32_t t = (uint32_t)(blockIdx.x - S.toff);
+    const uint32_t tix = t % (uint32_t)S.tiles_x;
+    t /= (uint32_t)S.tiles_x;
+    const uint32_t tiy = t % (uint32_t)S.tiles_y;
+    const uint32_t tiz = t / (uint32_t)S.tiles_y;
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
+    const int x = (int)tix * TILE_X + threadIdx.x, y = (int)tiy * TILE_Y + threadIdx.y;
+    const int z0 = (int)tiz * TILE_Z, z1 = min(z0 + TILE_Z, nz);
+    const bool inxy = x < nx && y < ny;
+    const float *im = img + S.voff;
+    const int tid = threadIdx.y * TILE_X + threadIdx.x;
+    // z neighbours of this thread's column
+    uint32_t below = 0, cur = 0, above = 0;
+    if (inxy) {
+        uint32_t l = (uint32_t)y * nx + x;
+        if (z0 > 0) below = ord32(im[(uint32_t)(z0 - 1) * plane + l]);
+        cur = ord32(im[(uint32_t)z0 * plane + l]);
+    }
+    bool nan_seen = false;
+    for (int z = z0; z < z1; z++) {
+        const uint32_t zoff = (uint32_t)z * plane;
+        // stage the plane with its halo
+        for (int i = tid; i < (TILE_Y + 2) * (TILE_X + 2); i += TILE_X * TILE_Y) {
+            int hy = i / (TILE_X + 2), hx = i % (TILE_X + 2);
+            int gx = (int)tix * TILE_X + hx - 1, gy = (int)tiy * TILE_Y + hy - 1;
+            uint32_t o = 0;
+            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+                float f = im[zoff + (uint32_t)gy * nx + gx];
+                nan_seen |= isnan(f);
+                o = ord32(f);
+            }
+            pl[hy][hx] = o;
+        }
+        if (inxy && z + 1 < nz) above = ord32(im[zoff + plane + (uint32_t)y * nx + x]);
+        __syncthreads();
+        if (inxy) {
+            const uint32_t lv = zoff + (uint32_t)y * nx + x;
+            const uint32_t ov = cur;
+            const uint64_t kv = make_key(ov, lv);
+            uint64_t best = ~0ull;
+            int bestdir = 0;
+            uint32_t bestou = 0, bestlu = 0;
+            // neighbours: -x, +x, -y, +y, -z, +z
+#pragma unroll
+            for (int d = 0; d < 6; d++) {
+                int ax = d >> 1;
+                bool pos = d & 1;
+                bool ok;
+                uint32_t ou, lu, la;
+                if (ax == 0) {
+                    ok = pos ? x + 1 < nx : x > 0;
+                    ou = pl[threadIdx.y + 1][threadIdx.x + (pos ? 2 : 0)];
+                    lu = pos ? lv + 1 : lv - 1;
+                    la = pos ? lv : lv - 1;
+                } else if (ax == 1) {
+                    ok = pos ? y + 1 < ny : y > 0;
+                    ou = pl[threadIdx.y + (pos ? 2 : 0)][threadIdx.x + 1];
+                    lu = pos ? lv + nx : lv - nx;
+                    la = (pos ? lv : lv - nx) + plane * (uint32_t)nz;
+                } else {
+                    ok = pos ? z + 1 < nz : z > 0;
+                    ou = pos ? above : below;
+                    lu = pos ? lv + plane : lv - plane;
+                    la = (pos ? lv : lv - plane) + 2u * plane * (uint32_t)nz;
+                }
+                if (!ok) continue;
+                uint64_t ek = make_key(ov > ou ? ov : ou, la);
+                if (ek < best) {
+                    best = ek;
+                    bestdir = d + 1;
+                    bestou = ou;
+                    bestlu = lu;
+                }
+            }
+            const int64_t gv = S.voff + lv;
+            if (bestdir && make_key(bestou, bestlu) < kv) {
+                parent[gv] = (uint32_t)(S.voff + bestlu);
+                dd[gv] = (uint8_t)bestdir;
+                if (flags & CR_KEEP_ZERO) emit_pair(pb, (uint32_t)si, 0, unord32(ov), key_value(best), lv, key_L(best), 0);
+            } else {
+                parent[gv] = (uint32_t)gv;
+                dd[gv] = 0;
+            }
+        }
+        below = cur;
+        cur = above;
+        __syncthreads();
+    }
+    if (nan_seen) set_status(status, CR_ERR_NAN);
+}
+
+// ---------------------------------------------------------------------------
+// The same stencil fed by the tensor-memory accelerator: one
+// cp.async.bulk.tensor copy brings the block's whole 32x8x16 tile with a
+// halo (a 40x10x18 box, x starting 4 voxels early so the copy starts on a
+// 16-byte boundary; outside the image the box is zero-filled and never used)
+// into shared memory, completing on an mbarrier.  Single images whose rows
+// are a multiple of 16 bytes.
+// ---------------------------------------------------------------------------
+constexpr int TMA_BX = TILE_X + 8, TMA_BY = TILE_Y + 2, TMA_BZ = TILE_Z + 2;
+constexpr int TMA_BYTES = TMA_BX * TMA_BY * TMA_BZ * 4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// wait on phase 0 of an mbarrier, at most `limit` polls; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, long long limit) {
+    uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tma(const __grid_constant__ CUtensorMap tmap,
+                                                                  const Seg *__restrict__ segs,
+                                                                  uint32_t *__restrict__ parent,
+                                                                  uint8_t *__restrict__ dd, int *status, PairBuf pb,
+                                                                  uint32_t flags) {
+    __shared__ __align__(128) float box[TMA_BZ][TMA_BY][TMA_BX];
+    __shared__ __align__(8) uint64_t bar;
+    const Seg S = segs[0];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    uint32_t t = blockIdx.x;
+    const int tix = (int)(t % (uint32_t)S.tiles_x);
+    t /= (uint32_t)S.tiles_x;
+    const int tiy = (int)(t % (uint32_t)S.tiles_y);
+    const int tiz = (int)(t / (uint32_t)S.tiles_y);
+    const int x0 = tix * TILE_X, y0 = tiy * TILE_Y, z0 = tiz * TILE_Z;
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    if (leader) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (leader) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(TMA_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+            ::"r"(smem_u32(&box[0][0][0])), "l"(&tmap), "r"(x0 - 4), "r"(y0 - 1), "r"(z0 - 1), "r"(smem_u32(&bar))
+            : "memory");
+    }
+    if (!mbar_wait(&bar, 1ll << 24)) {
+        set_status(status, CR_ERR_TIMEOUT);
+        mbar_wait(&bar, 1ll << 24);  // give the copy in flight a chance to land before the block exits
+        return;
+    }
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
+    const int bx = threadIdx.x + 4, by = threadIdx.y + 1;
+    bool nan_seen = false;
+    const int zend = min(TILE_Z, nz - z0);
+    for (int zz = 0; zz < zend; zz++) {
+        const int z = z0 + zz, bz = zz + 1;
+        const float fv = box[bz][by][bx];
+        nan_seen |= isnan(fv);
+        const uint32_t ov = ord32(fv);
+        const uint32_t lv = (uint32_t)z * plane + (uint32_t)y * nx + x;
+        const uint64_t kv = make_key(ov, lv);
+        uint64_t best = ~0ull;
+        int bestdir = 0;
+        uint32_t bestou = 0, bestlu = 0;
+#pragma unroll
+        for (int d = 0; d < 6; d++) {
+            const int ax = d >> 1;
+            const bool pos = d & 1;
+            bool ok;
+            float fu;
+            uint32_t lu, la;
+            if (ax == 0) {
+                ok = pos ? x + 1 < nx : x > 0;
+                fu = box[bz][by][bx + (pos ? 1 : -1)];
+                lu = pos ? lv + 1 : lv - 1;
+                la = pos ? lv : lv - 1;
+            } else if (ax == 1) {
+                ok = pos ? y + 1 < ny : y > 0;
+                fu = box[bz][by + (pos ? 1 : -1)][bx];
+                lu = pos ? lv + nx : lv - nx;
+                la = (pos ? lv : lv - nx) + plane * (uint32_t)nz;
+            } else {
+                ok = pos ? z + 1 < nz : z > 0;
+                fu = box[bz + (pos ? 1 : -1)][by][bx];
+                lu = pos ? lv + plane : lv - plane;
+                la = (pos ? lv : lv - plane) + 2u * plane * (uint32_t)nz;
+            }
+            if (!ok) continue;
+            const uint32_t ou = ord32(fu);
+            const uint64_t ek = make_key(ov > ou ? ov : ou, la);
+            if (ek < best) {
+                best = ek;
+                bestdir = d + 1;
+                bestou = ou;
+                bestlu = lu;
+            }
+        }
+        if (bestdir && make_key(bestou, bestlu) < kv) {
+            parent[lv] = bestlu;
+            dd[lv] = (uint8_t)bestdir;
+            if (flags & CR_KEEP_ZERO) emit_pair(pb, 0u, 0, unord32(ov), key_value(best), lv, key_L(best), 0);
+        } else {
+            parent[lv] = lv;
+            dd[lv] = 0;
+        }
+    }
+    if (nan_seen) set_status(status, CR_ERR_NAN);
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// a tensor map over one image as an (nx, ny, nz) float32 tensor; false if TMA cannot serve it
+static bool make_image_map(CUtensorMap *m, const float *img, const Seg &S) {
+    if (((uintptr_t)img & 15) || (S.nx % 4) != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)S.nx, (cuuint64_t)S.ny, (cuuint64_t)S.nz};
+    cuuint64_t strides[2] = {(cuuint64_t)S.nx * 4, (cuuint64_t)S.nx * S.ny * 4};
+    cuuint32_t box[3] = {(cuuint32_t)TMA_BX, (cuuint32_t)TMA_BY, (cuuint32_t)TMA_BZ};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)img, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 // ===========================================================================
@@ -665,12 +942,19 @@ static int rounds_coop(UF &u, int64_t work_estimate, const Seg *segs, int mode, 
     return e == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
-int run_h0(const float *img, const Seg *segs, int nseg, int64_t vtot, UF &u, const PairBuf &pb, uint32_t flags,
-           uint32_t *extra_mask, int *status, cudaStream_t st) {
+int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ntiles, UF &u,
+           const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status, cudaStream_t st) {
     cudaMemsetAsync(u.cnt, 0, 8 * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_H0_STENCIL);
     CR_NOTE_LAUNCH();
-    k_h0_stencil<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, u.dd, status, pb, flags);
+    CUtensorMap tmap;
+    if (nseg == 1 && make_image_map(&tmap, img, hsegs[0])) {
+        k_h0_stencil_tma<<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd, status, pb,
+                                                                            flags);
+    } else {
+        k_h0_stencil_tiled<<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(img, segs, nseg, u.lab, u.dd, status,
+                                                                              pb, flags);
+    }
     prof_end(st, STAGE_H0_STENCIL, 9.0 * vtot);
     prof_begin(st, STAGE_JUMP);
     CR_NOTE_LAUNCH();
