@@ -140,7 +140,8 @@ def read_profile(cr):
     return out
 
 
-SINGLE_KERNEL_STAGES = ("h0_stencil", "jump", "h0_cross", "dual_stencil", "dual_cross", "h1_scan", "h1_reduce")
+# stages that are one kernel launch per call (the roofline is quoted per kernel)
+SINGLE_KERNEL_STAGES = ("h0_stencil", "h0_cross", "dual_stencil", "dual_cross", "h1_scan", "h1_reduce", "uf_round")
 
 
 def roofline_from(stages, peaks, sustained=True):
@@ -371,6 +372,31 @@ def main():
             d2h = gh.numel() * 4
     e2e_value = units * world / (statistics.mean(e2e_ms) / 1e3) if e2e_ms else None
 
+    # the plain per-image path on the same GPU (a subset, scaled to images/s)
+    plain = None
+    if W["kind"] == "batch" and not args.no_e2e:
+        sub = 512
+        imgs_dev = [torch.from_numpy(a).to(dev) for a in data[:sub]]
+
+        def plain_step():
+            for im in imgs_dev:
+                p = cr.cr_persistence(im, maxdim=1)
+                sel = (p.dim == 1) & torch.isfinite(p.death)
+                life = torch.where(sel, p.death - p.birth, torch.zeros_like(p.birth))
+                cr.cr_backward(im, p, -2 * life, 2 * life)
+
+        plain_step()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plain_step()
+        b.record(stream)
+        b.synchronize()
+        pms = a.elapsed_time(b)
+        plain = {"images_per_s": sub / (pms / 1e3), "sample": "first %d images, same loss" % sub,
+                 "batched_over_plain": value / (sub / (pms / 1e3))}
+
     peaks = load_peaks()
     roof = roofline_from(stages, peaks)
 
@@ -387,6 +413,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": metric.split()[0], "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
+            "plain_path": plain,
             "stages": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
                        for k, v in stages.items()}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -353,7 +353,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         if (B.pool_cap < 64) { set_host_detail(SITE_H1_CARVE); return CR_ERR_WORKSPACE; }
         B.pool = R.take<uint64_t>(B.pool_cap);
         int64_t ncols = 0;
-        rc = run_h1(imgs, dd, extra, segs, n, P.vtot, B, pb, flags, status, &ncols, st);
+        rc = run_h1(imgs, dd, extra, segs, n, P.vtot, P.ntiles, B, pb, flags, status, &ncols, st);
         if (rc) return rc;
     }
 
@@ -388,18 +388,27 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         }
         u.max_edges = max_edges;
         if (!R.ok) return CR_ERR_WORKSPACE;
-        rc = run_dual(imgs, segs, n, P.vtot, P.ctot, u, pb, flags, status, st);
+        rc = run_dual(imgs, segs, n, P.vtot, P.ctot, P.ntiles, u, pb, flags, status, st);
         if (rc) return rc;
     }
 
     // ---- count, status ----
     int hstatus[16] = {0};
+    unsigned long long ufc[64];
+    cudaMemcpyAsync(ufc, cnt, 64 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hc, pair_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hstatus, status, 16 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
     if (hstatus[0]) {
         g_detail = hstatus[8];
         return hstatus[0];
+    }
+    // algorithmic bytes of the union-find rounds: per round and edge 88 B
+    // (edge reads in four phases, min-edge updates, relabel writes), per
+    // group 12 B (hook chase and min-edge reset); counters of both runs
+    for (int base : {8, 48}) {
+        double e = (double)ufc[base + 3], r = (double)ufc[base + 6], g = (double)ufc[base + 0];
+        prof_add_bytes(STAGE_UF_ROUND, 88.0 * e + 12.0 * g * r);
     }
     int64_t np = (int64_t)hc[0];
     *n_pairs = np;

@@ -146,63 +146,54 @@ __device__ __forceinline__ int seg_of_v(const Seg *segs, int n, int64_t gv) {
     return lo;
 }
 
-__global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, int64_t vtot, uint64_t *__restrict__ colkey,
+__global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, uint64_t *__restrict__ colkey,
                           uint32_t *__restrict__ colseg, unsigned long long *ncol, int64_t max_cols, PairBuf pb,
                           uint32_t flags, int *status) {
-    int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool in = gv < vtot;
-    Seg S;
-    int si = 0;
-    int c[3] = {0, 0, 0};
-    if (in) {
-        si = seg_of_v(segs, nseg, gv);
-        S = segs[si];
-        if (S.edim != 3) in = false;
-        int64_t lv = gv - S.voff;
-        c[0] = (int)(lv % S.nx);
-        c[1] = (int)((lv / S.nx) % S.ny);
-        c[2] = (int)(lv / ((int64_t)S.nx * S.ny));
-    }
-    for (int a = 0; a < 3; a++) {
-        bool keep = false;
-        uint64_t sk = 0;
-        if (in && c[a] + 1 < ext_of(S, a) && !h0_negative(I, S, a, c)) {
-            sk = edge_key(I, S, a, c);
-            uint64_t cf[4];
-            int n = edge_cofacets(I, S, a, c, cf);
-            if (n == 0) {
-                set_status(status, CR_ERR_INTERNAL);
-            } else {
-                uint64_t t = cf[0];
-                for (int i = 1; i < n; i++) t = cf[i] < t ? cf[i] : t;
-                int fm, fc[3];
-                decode_L(S, key_L(t), fm, fc);
-                int ea, ec[3];
-                uint64_t top = face_max_facet(I, S, fm, fc, ea, ec);
-                if (top == sk) {
-                    int64_t bit = S.loff + key_L(t);
-                    atomicOr(&I.appmask[bit >> 5], 1u << (bit & 31));
-                    if (flags & CR_KEEP_ZERO)
-                        emit_pair(pb, (uint32_t)si, 1, key_value(sk), key_value(t), key_L(sk), key_L(t), 0);
+    const int si = block_seg(segs, nseg);
+    const Seg S = segs[si];
+    int tx, ty, z0, z1;
+    tile_column(S, tx, ty, z0, z1);
+    const bool inxy = S.edim == 3 && tx < S.nx && ty < S.ny;
+    for (int zz = z0; zz < z1; zz++) {
+        const bool in = inxy;
+        int c[3] = {tx, ty, zz};
+        uint64_t keeps[3];
+        int cnt = 0;
+        for (int a = 0; a < 3; a++) {
+            bool keep = false;
+            uint64_t sk = 0;
+            if (in && c[a] + 1 < ext_of(S, a) && !h0_negative(I, S, a, c)) {
+                sk = edge_key(I, S, a, c);
+                uint64_t cf[4];
+                int n = edge_cofacets(I, S, a, c, cf);
+                if (n == 0) {
+                    set_status(status, CR_ERR_INTERNAL);
                 } else {
-                    keep = true;
+                    uint64_t t = cf[0];
+                    for (int i = 1; i < n; i++) t = cf[i] < t ? cf[i] : t;
+                    int fm, fc[3];
+                    decode_L(S, key_L(t), fm, fc);
+                    int ea, ec[3];
+                    uint64_t top = face_max_facet(I, S, fm, fc, ea, ec);
+                    if (top == sk) {
+                        int64_t bit = S.loff + key_L(t);
+                        atomicOr(&I.appmask[bit >> 5], 1u << (bit & 31));
+                        if (flags & CR_KEEP_ZERO)
+                            emit_pair(pb, (uint32_t)si, 1, key_value(sk), key_value(t), key_L(sk), key_L(t), 0);
+                    } else {
+                        keep = true;
+                    }
                 }
             }
+            if (keep) keeps[cnt++] = sk;
         }
-        unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
-        if (mask) {
-            int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(ncol, (unsigned long long)__popc(mask));
-            base = __shfl_sync(0xFFFFFFFFu, base, leader);
-            if (keep) {
-                int64_t i = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
-                if (i < max_cols) {
-                    colkey[i] = ~sk;  // sorted ascending below = cohomology order
-                    colseg[i] = (uint32_t)si;
-                } else {
-                    fail_ws(status, SITE_COLUMNS);
-                }
+        int64_t i0 = block_append(cnt, ncol);
+        for (int k = 0; k < cnt; k++) {
+            if (i0 + k < max_cols) {
+                colkey[i0 + k] = ~keeps[k];  // sorted ascending below = cohomology order
+                colseg[i0 + k] = (uint32_t)si;
+            } else {
+                fail_ws(status, SITE_COLUMNS);
             }
         }
     }
@@ -1170,14 +1161,15 @@ int h1_stats(int64_t *out, int n) {
 }
 
 int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, int nseg, int64_t vtot,
-           H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status, int64_t *ncols_out, cudaStream_t st) {
+           int64_t ntiles, H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status, int64_t *ncols_out,
+           cudaStream_t st) {
     Img3 I{img, dd, extra, B.appmask};
     cudaMemsetAsync(B.appmask, 0, (size_t)((3 * vtot + 31) / 32) * sizeof(uint32_t), st);
     cudaMemsetAsync(B.cnt, 0, 24 * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_H1_SCAN);
     CR_NOTE_LAUNCH();
-    k_h1_scan<<<nb1(vtot), 256, 0, st>>>(I, segs, nseg, vtot, B.colkey, B.colseg, &B.cnt[0], B.max_cols, pb, flags,
-                                         status);
+    k_h1_scan<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(I, segs, nseg, B.colkey, B.colseg, &B.cnt[0],
+                                                            B.max_cols, pb, flags, status);
     prof_end(st, STAGE_H1_SCAN, 5.0 * vtot);
     unsigned long long hc = 0;
     cudaMemcpyAsync(&hc, &B.cnt[0], sizeof(hc), cudaMemcpyDeviceToHost, st);

@@ -36,6 +36,68 @@ struct Seg {
 // tiles of the 2.5D stencil kernels: TILE_X x TILE_Y voxels marching TILE_Z planes
 constexpr int TILE_X = 32, TILE_Y = 8, TILE_Z = 16;
 
+// image of a tile (binary search over the segments' first tiles)
+__device__ __forceinline__ int seg_of_tile(const Seg *segs, int n, int64_t t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].toff <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Block-aggregated append: every thread of the block calls it with the number
+// of items it will write; one atomic per block reserves the space.  Returns
+// this thread's first slot.
+__device__ __forceinline__ int64_t block_append(int cnt, unsigned long long *counter) {
+    __shared__ int s_w[32];
+    __shared__ unsigned long long s_base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int v = lane < nw ? s_w[lane] : 0;
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane < nw) s_w[lane] = inc - v;
+        if (lane == 31) s_base = inc > 0 ? atomicAdd(counter, (unsigned long long)inc) : 0ull;
+    }
+    __syncthreads();
+    int64_t base = (int64_t)s_base + s_w[w] + (incl - cnt);
+    __syncthreads();
+    return base;
+}
+
+// Tile-grid launches (grid = tiles, block = TILE_X*TILE_Y threads): the
+// block's image, looked up once, and this thread's column of the tile.
+__device__ __forceinline__ int block_seg(const Seg *segs, int nseg) {
+    __shared__ int s_si;
+    if (threadIdx.x == 0) s_si = seg_of_tile(segs, nseg, blockIdx.x);
+    __syncthreads();
+    return s_si;
+}
+__device__ __forceinline__ void tile_column(const Seg &S, int &x, int &y, int &z0, int &z1) {
+    uint32_t t = (uint32_t)(blockIdx.x - S.toff);
+    uint32_t tix = t % (uint32_t)S.tiles_x;
+    t /= (uint32_t)S.tiles_x;
+    uint32_t tiy = t % (uint32_t)S.tiles_y;
+    uint32_t tiz = t / (uint32_t)S.tiles_y;
+    x = (int)tix * TILE_X + (int)(threadIdx.x & (TILE_X - 1));
+    y = (int)tiy * TILE_Y + (int)(threadIdx.x / TILE_X);
+    z0 = (int)tiz * TILE_Z;
+    z1 = min(z0 + TILE_Z, S.nz);
+}
+
 // ---------------------------------------------------------------------------
 // keys
 // ---------------------------------------------------------------------------
@@ -148,8 +210,8 @@ struct UF {
 };
 int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ntiles, UF &u,
            const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status, cudaStream_t st);
-int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, UF &u, const PairBuf &pb,
-             uint32_t flags, int *status, cudaStream_t st);
+int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, int64_t ntiles, UF &u,
+             const PairBuf &pb, uint32_t flags, int *status, cudaStream_t st);
 
 // middle-dimension buffers (cr_h1.cu)
 struct H1Bufs {
@@ -173,7 +235,8 @@ struct H1Bufs {
 };
 int h1_stats(int64_t *out, int n);
 int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, int nseg, int64_t vtot,
-           H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status, int64_t *ncols_out, cudaStream_t st);
+           int64_t ntiles, H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status, int64_t *ncols_out,
+           cudaStream_t st);
 
 // radix sort of (u64 key, u32 value) by bits [lo, hi) of the key, stable, LSD.
 // tmp buffers must hold n entries each.  Returns cudaError.
@@ -195,6 +258,7 @@ extern std::atomic<long long> g_launch_count;
 void prof_begin(cudaStream_t st, int stage);
 void prof_end(cudaStream_t st, int stage, double bytes);
 void prof_flush();
+void prof_add_bytes(int stage, double bytes);
 #define CR_NOTE_LAUNCH() (::cr::g_launch_count.fetch_add(1, std::memory_order_relaxed))
 
 }  // namespace cr

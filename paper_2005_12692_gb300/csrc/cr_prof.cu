@@ -65,6 +65,13 @@ void prof_end(cudaStream_t st, int stage, double bytes) {
     }
 }
 
+// bytes known only after the stream reached this point (device counters)
+void prof_add_bytes(int stage, double bytes) {
+    if (!g_on) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_bytes[stage] += bytes;
+}
+
 void prof_flush() {
     if (!g_on) return;
     std::lock_guard<std::mutex> lk(g_mu);

@@ -117,14 +117,6 @@ __global__ void k_h0_stencil(const float *__restrict__ img, const Seg *__restric
 // halo in shared memory; the z neighbours come from registers.  All index
 // arithmetic is 32-bit within the image.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int seg_of_tile(const Seg *segs, int n, int64_t t) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].toff <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
 
 __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tiled(const float *__restrict__ img,
                                                                     const Seg *__restrict__ segs, int nseg,
@@ -392,6 +384,15 @@ static bool make_image_map(CUtensorMap *m, const float *img, const Seg &S) {
 // root and write only its own entry, so no later write can replace a root by
 // a non-root ancestor.
 // ===========================================================================
+// one in-place pointer-doubling step per node (every write stores an ancestor)
+__global__ void k_double(uint32_t *__restrict__ p, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t a = p[i];
+    uint32_t b = p[a];
+    if (b != a) p[i] = b;
+}
+
 __global__ void k_halve(uint32_t *__restrict__ p, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -454,56 +455,56 @@ __global__ void k_unmark(uint32_t *__restrict__ lab, int64_t n) {
 
 // edges between different basins; an edge is a stencil (round-0) hook iff
 // one of its endpoints points at the other through it
-__global__ void k_h0_cross(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t vtot,
+__global__ void k_h0_cross(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg,
                            const uint32_t *__restrict__ lab, const uint8_t *__restrict__ dd,
                            uint64_t *__restrict__ ek, uint32_t *__restrict__ ea, uint32_t *__restrict__ eb,
                            unsigned long long *ne, int64_t max_edges, const unsigned long long *ngroups,
                            int *status) {
     const uint32_t ng = (uint32_t)*ngroups;
-    int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool in = gv < vtot;
-    Seg S;
-    int64_t lv = 0;
-    int x = 0, y = 0, z = 0;
-    uint32_t ov = 0, la = 0;
-    if (in) {
-        S = segs[seg_of(segs, nseg, gv)];
-        lv = gv - S.voff;
-        x = (int)(lv % S.nx);
-        y = (int)((lv / S.nx) % S.ny);
-        z = (int)(lv / ((int64_t)S.nx * S.ny));
-        ov = ord32(img[gv]);
-        la = lab[gv];
-    }
-    for (int ax = 0; ax < 3; ax++) {
-        bool emit = false;
-        uint64_t key = 0;
-        uint32_t lb = 0;
-        if (in) {
+    const int si = block_seg(segs, nseg);
+    const Seg S = segs[si];
+    int x, y, z0, z1;
+    tile_column(S, x, y, z0, z1);
+    const bool inxy = x < S.nx && y < S.ny;
+    const uint32_t nx = (uint32_t)S.nx, plane = (uint32_t)S.nx * (uint32_t)S.ny;
+    for (int z = z0; z < z1; z++) {
+        const uint32_t lv = (uint32_t)z * plane + (uint32_t)y * nx + (uint32_t)x;
+        const int64_t gv = S.voff + lv;
+        uint32_t ov = 0, la = 0;
+        uint8_t dv = 0;
+        if (inxy) {
+            ov = ord32(img[gv]);
+            la = lab[gv];
+            dv = dd[gv];
+        }
+        uint64_t keys[3];
+        uint32_t lbs[3];
+        int cnt = 0;
+        for (int ax = 0; ax < 3; ax++) {
+            if (!inxy) break;
             int ext = ax == 0 ? S.nx : (ax == 1 ? S.ny : S.nz);
             int c = ax == 0 ? x : (ax == 1 ? y : z);
-            if (c + 1 < ext) {
-                int64_t du = ax == 0 ? 1 : (ax == 1 ? (int64_t)S.nx : (int64_t)S.nx * S.ny);
-                int64_t u = gv + du;
-                bool stencil = dd[gv] == (uint8_t)(2 * ax + 2) || dd[u] == (uint8_t)(2 * ax + 1);
-                lb = lab[u];
-                if (!stencil && lb != la) {
-                    uint32_t ou = ord32(img[u]);
-                    key = make_key(ov > ou ? ov : ou, cube_L(S, ax, x, y, z));
-                    emit = true;
-                }
+            if (c + 1 >= ext) continue;
+            uint32_t du = ax == 0 ? 1u : (ax == 1 ? nx : plane);
+            int64_t u = gv + du;
+            bool stencil = dv == (uint8_t)(2 * ax + 2) || dd[u] == (uint8_t)(2 * ax + 1);
+            uint32_t lb = lab[u];
+            if (stencil || lb == la) continue;
+            if (la >= ng || lb >= ng) {
+                set_status(status, CR_ERR_INTERNAL);
+                continue;
             }
+            uint32_t ou = ord32(img[u]);
+            keys[cnt] = make_key(ov > ou ? ov : ou, lv + (uint32_t)ax * plane * (uint32_t)S.nz);
+            lbs[cnt] = lb;
+            cnt++;
         }
-        if (emit && (la >= ng || lb >= ng)) {
-            set_status(status, CR_ERR_INTERNAL);
-            emit = false;
-        }
-        int64_t i = warp_append(emit, ne);
-        if (emit) {
-            if (i < max_edges) {
-                ek[i] = key;
-                ea[i] = la;
-                eb[i] = lb;
+        int64_t i = block_append(cnt, ne);
+        for (int k = 0; k < cnt; k++) {
+            if (i + k < max_edges) {
+                ek[i + k] = keys[k];
+                ea[i + k] = la;
+                eb[i + k] = lbs[k];
             } else {
                 fail_ws(status, SITE_EDGES);
             }
@@ -581,46 +582,48 @@ __device__ __forceinline__ bool cell_in(const Seg &S, int x, int y, int z) {
     return z == 0;
 }
 
-__global__ void k_dual_stencil(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t ctot,
+__global__ void k_dual_stencil(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg,
                                uint32_t *__restrict__ parent, uint8_t *__restrict__ dd, PairBuf pb, uint32_t flags) {
-    int64_t gc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gc >= ctot) return;
-    int si = seg_of_node(segs, nseg, gc);
+    const int si = block_seg(segs, nseg);
     const Seg S = segs[si];
-    int64_t c = gc - S.coff;
-    if (c >= S.ncell) {  // the outer node
-        parent[gc] = (uint32_t)gc;
-        dd[gc] = 0;
-        return;
+    if (blockIdx.x == S.toff && threadIdx.x == 0) {  // the outer node
+        parent[S.coff + S.ncell] = (uint32_t)(S.coff + S.ncell);
+        dd[S.coff + S.ncell] = 0;
     }
-    CellPos p = cell_pos(S, c);
-    uint64_t kc = top_key(img, S, p.x, p.y, p.z);
-    int nf = S.edim == 3 ? 6 : 4;
-    uint64_t best = 0;
-    int bf = -1, bx = 0, by = 0, bz = 0;
-    for (int f = 0; f < nf; f++) {
-        int ox, oy, oz;
-        uint64_t fk = facet_key(img, S, p.x, p.y, p.z, f, ox, oy, oz);
-        if (bf < 0 || fk > best) { best = fk; bf = f; bx = ox; by = oy; bz = oz; }
-    }
-    bool hook;
-    int64_t other;
-    if (!cell_in(S, bx, by, bz)) {
-        hook = true;  // the outer node is the oldest
-        other = S.coff + S.ncell;
-    } else {
-        uint64_t ko = top_key(img, S, bx, by, bz);
-        hook = ko > kc;  // larger key = older in the reversed order
-        other = S.coff + cell_index(S, bx, by, bz);
-    }
-    if (hook) {
-        parent[gc] = (uint32_t)other;
-        dd[gc] = (uint8_t)(bf + 1);
-        if (flags & CR_KEEP_ZERO)
-            emit_pair(pb, (uint32_t)si, S.edim - 1, key_value(best), key_value(kc), key_L(best), key_L(kc), 0);
-    } else {
-        parent[gc] = (uint32_t)gc;
-        dd[gc] = 0;
+    if (S.ncell == 0) return;
+    int x, y, z0, z1;
+    tile_column(S, x, y, z0, z1);
+    for (int z = z0; z < z1; z++) {
+        if (!cell_in(S, x, y, z)) continue;
+        const int64_t gc = S.coff + cell_index(S, x, y, z);
+        uint64_t kc = top_key(img, S, x, y, z);
+        int nf = S.edim == 3 ? 6 : 4;
+        uint64_t best = 0;
+        int bf = -1, bx = 0, by = 0, bz = 0;
+        for (int f = 0; f < nf; f++) {
+            int ox, oy, oz;
+            uint64_t fk = facet_key(img, S, x, y, z, f, ox, oy, oz);
+            if (bf < 0 || fk > best) { best = fk; bf = f; bx = ox; by = oy; bz = oz; }
+        }
+        bool hook;
+        int64_t other;
+        if (!cell_in(S, bx, by, bz)) {
+            hook = true;  // the outer node is the oldest
+            other = S.coff + S.ncell;
+        } else {
+            uint64_t ko = top_key(img, S, bx, by, bz);
+            hook = ko > kc;  // larger key = older in the reversed order
+            other = S.coff + cell_index(S, bx, by, bz);
+        }
+        if (hook) {
+            parent[gc] = (uint32_t)other;
+            dd[gc] = (uint8_t)(bf + 1);
+            if (flags & CR_KEEP_ZERO)
+                emit_pair(pb, (uint32_t)si, S.edim - 1, key_value(best), key_value(kc), key_L(best), key_L(kc), 0);
+        } else {
+            parent[gc] = (uint32_t)gc;
+            dd[gc] = 0;
+        }
     }
 }
 
@@ -648,84 +651,89 @@ __global__ void k_dual_roots(const float *__restrict__ img, const Seg *__restric
 }
 
 // dual edges = facets of the top cubes, iterated over the L-space of type m
-__global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t vtot,
+__global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg,
                              const uint32_t *__restrict__ lab, const uint8_t *__restrict__ dd,
                              uint64_t *__restrict__ ek, uint32_t *__restrict__ ea, uint32_t *__restrict__ eb,
                              unsigned long long *ne, int64_t max_edges, const unsigned long long *ngroups,
                              int *status) {
     const uint32_t ng = (uint32_t)*ngroups;
-    int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool in = gv < vtot;
-    Seg S;
-    int x = 0, y = 0, z = 0;
-    if (in) {
-        S = segs[seg_of(segs, nseg, gv)];
-        if (S.ncell == 0) in = false;
-        int64_t lv = gv - S.voff;
-        x = (int)(lv % S.nx);
-        y = (int)((lv / S.nx) % S.ny);
-        z = (int)(lv / ((int64_t)S.nx * S.ny));
-    }
-    for (int m = 0; m < 3; m++) {
-        bool emit = false;
-        uint64_t key = 0;
-        uint32_t la = 0, lb = 0;
-        if (in && (S.edim == 3 || m < 2)) {
-            // the two sides (a = "minus" side cube, b = "plus" side cube) and the facet code on each side
-            int ax, ay, az, bx = x, by = y, bz = z, fa, fb;
-            bool exists;
-            uint64_t fk = 0;
-            if (S.edim == 2) {
-                if (m == 0) {  // x-edge at (x,y)
-                    exists = x + 1 < S.nx;
-                    ax = x; ay = y - 1; az = 0; fa = 1; fb = 0;
-                    if (exists) fk = make_key(vmax_ord(img, S, x, y, 0, 1, 0, 0), cube_L(S, 0, x, y, 0));
-                } else {  // y-edge at (x,y)
-                    exists = y + 1 < S.ny;
-                    ax = x - 1; ay = y; az = 0; fa = 3; fb = 2;
-                    if (exists) fk = make_key(vmax_ord(img, S, x, y, 0, 0, 1, 0), cube_L(S, 1, x, y, 0));
+    const int si = block_seg(segs, nseg);
+    const Seg S = segs[si];
+    int x, y, z0, z1;
+    tile_column(S, x, y, z0, z1);
+    const bool inxy = S.ncell > 0 && x < S.nx && y < S.ny;
+    for (int z = z0; z < z1; z++) {
+        const bool in = inxy;
+        uint64_t keys[3];
+        uint32_t las[3], lbs[3];
+        int cnt = 0;
+        for (int m = 0; m < 3; m++) {
+            bool emit = false;
+            uint64_t key = 0;
+            uint32_t la = 0, lb = 0;
+            if (in && (S.edim == 3 || m < 2)) {
+                // the two sides (a = "minus" side cube, b = "plus" side cube) and the facet code on each side
+                int ax, ay, az, bx = x, by = y, bz = z, fa, fb;
+                bool exists;
+                uint64_t fk = 0;
+                if (S.edim == 2) {
+                    if (m == 0) {  // x-edge at (x,y)
+                        exists = x + 1 < S.nx;
+                        ax = x; ay = y - 1; az = 0; fa = 1; fb = 0;
+                        if (exists) fk = make_key(vmax_ord(img, S, x, y, 0, 1, 0, 0), cube_L(S, 0, x, y, 0));
+                    } else {  // y-edge at (x,y)
+                        exists = y + 1 < S.ny;
+                        ax = x - 1; ay = y; az = 0; fa = 3; fb = 2;
+                        if (exists) fk = make_key(vmax_ord(img, S, x, y, 0, 0, 1, 0), cube_L(S, 1, x, y, 0));
+                    }
+                } else {
+                    if (m == 0) {  // face {x,y}
+                        exists = x + 1 < S.nx && y + 1 < S.ny;
+                        ax = x; ay = y; az = z - 1; fa = 1; fb = 0;
+                        if (exists) fk = make_key(vmax_ord(img, S, x, y, z, 1, 1, 0), cube_L(S, 0, x, y, z));
+                    } else if (m == 1) {  // face {x,z}
+                        exists = x + 1 < S.nx && z + 1 < S.nz;
+                        ax = x; ay = y - 1; az = z; fa = 3; fb = 2;
+                        if (exists) fk = make_key(vmax_ord(img, S, x, y, z, 1, 0, 1), cube_L(S, 1, x, y, z));
+                    } else {  // face {y,z}
+                        exists = y + 1 < S.ny && z + 1 < S.nz;
+                        ax = x - 1; ay = y; az = z; fa = 5; fb = 4;
+                        if (exists) fk = make_key(vmax_ord(img, S, x, y, z, 0, 1, 1), cube_L(S, 2, x, y, z));
+                    }
                 }
-            } else {
-                if (m == 0) {  // face {x,y}
-                    exists = x + 1 < S.nx && y + 1 < S.ny;
-                    ax = x; ay = y; az = z - 1; fa = 1; fb = 0;
-                    if (exists) fk = make_key(vmax_ord(img, S, x, y, z, 1, 1, 0), cube_L(S, 0, x, y, z));
-                } else if (m == 1) {  // face {x,z}
-                    exists = x + 1 < S.nx && z + 1 < S.nz;
-                    ax = x; ay = y - 1; az = z; fa = 3; fb = 2;
-                    if (exists) fk = make_key(vmax_ord(img, S, x, y, z, 1, 0, 1), cube_L(S, 1, x, y, z));
-                } else {  // face {y,z}
-                    exists = y + 1 < S.ny && z + 1 < S.nz;
-                    ax = x - 1; ay = y; az = z; fa = 5; fb = 4;
-                    if (exists) fk = make_key(vmax_ord(img, S, x, y, z, 0, 1, 1), cube_L(S, 2, x, y, z));
-                }
-            }
-            if (exists) {
-                int64_t outer = S.coff + S.ncell;
-                bool ina = cell_in(S, ax, ay, az), inb = cell_in(S, bx, by, bz);
-                int64_t na = ina ? S.coff + cell_index(S, ax, ay, az) : outer;
-                int64_t nb = inb ? S.coff + cell_index(S, bx, by, bz) : outer;
-                bool stencil = (ina && dd[na] == (uint8_t)(fa + 1)) || (inb && dd[nb] == (uint8_t)(fb + 1));
-                if (!stencil) {
-                    la = lab[na];
-                    lb = lab[nb];
-                    if (la != lb) {
-                        emit = true;
-                        key = ~fk;
+                if (exists) {
+                    int64_t outer = S.coff + S.ncell;
+                    bool ina = cell_in(S, ax, ay, az), inb = cell_in(S, bx, by, bz);
+                    int64_t na = ina ? S.coff + cell_index(S, ax, ay, az) : outer;
+                    int64_t nb = inb ? S.coff + cell_index(S, bx, by, bz) : outer;
+                    bool stencil = (ina && dd[na] == (uint8_t)(fa + 1)) || (inb && dd[nb] == (uint8_t)(fb + 1));
+                    if (!stencil) {
+                        la = lab[na];
+                        lb = lab[nb];
+                        if (la != lb) {
+                            emit = true;
+                            key = ~fk;
+                        }
                     }
                 }
             }
+            if (emit && (la >= ng || lb >= ng)) {
+                set_status(status, CR_ERR_INTERNAL);
+                emit = false;
+            }
+            if (emit) {
+                keys[cnt] = key;
+                las[cnt] = la;
+                lbs[cnt] = lb;
+                cnt++;
+            }
         }
-        if (emit && (la >= ng || lb >= ng)) {
-            set_status(status, CR_ERR_INTERNAL);
-            emit = false;
-        }
-        int64_t i = warp_append(emit, ne);
-        if (emit) {
-            if (i < max_edges) {
-                ek[i] = key;
-                ea[i] = la;
-                eb[i] = lb;
+        int64_t i = block_append(cnt, ne);
+        for (int k = 0; k < cnt; k++) {
+            if (i + k < max_edges) {
+                ek[i + k] = keys[k];
+                ea[i + k] = las[k];
+                eb[i + k] = lbs[k];
             } else {
                 fail_ws(status, SITE_EDGES);
             }
@@ -817,7 +825,11 @@ __global__ void __launch_bounds__(UF_THREADS) k_uf_rounds(RoundArgs A) {
         int64_t ne = (int64_t)*(volatile unsigned long long *)necnt[cur];
         if (ne > u.max_edges) ne = u.max_edges;
         if (ne == 0) break;
-        if (tid == 0) *necnt[cur ^ 1] = 0;
+        if (tid == 0) {
+            *necnt[cur ^ 1] = 0;
+            u.cnt[3] += (unsigned long long)ne;  // edges visited, for the algorithmic byte count
+            u.cnt[6] += 1ull;                    // rounds
+        }
         const uint64_t *ek = u.ek[cur];
         const uint32_t *ea = u.ea[cur], *eb = u.eb[cur];
         // A
@@ -874,9 +886,8 @@ __global__ void __launch_bounds__(UF_THREADS) k_uf_rounds(RoundArgs A) {
         {
             uint64_t *ok = u.ek[cur ^ 1];
             uint32_t *oa = u.ea[cur ^ 1], *ob = u.eb[cur ^ 1];
-            const int64_t wbase = tid - lane;
-            for (int64_t base = wbase; base < ne; base += nthr) {
-                int64_t i = base + lane;
+            for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ne; base += nthr) {
+                int64_t i = base + threadIdx.x;
                 bool keep = false;
                 uint32_t a = 0, b = 0;
                 uint64_t k = 0;
@@ -886,12 +897,13 @@ __global__ void __launch_bounds__(UF_THREADS) k_uf_rounds(RoundArgs A) {
                     k = ek[i];
                     keep = a != b;
                 }
-                int64_t j = warp_append(keep, necnt[cur ^ 1]);
+                int64_t j = block_append(keep ? 1 : 0, necnt[cur ^ 1]);
                 if (keep) {
                     ok[j] = k;
                     oa[j] = a;
                     ob[j] = b;
                 }
+
             }
         }
         if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
@@ -958,7 +970,10 @@ int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
     prof_end(st, STAGE_H0_STENCIL, 9.0 * vtot);
     prof_begin(st, STAGE_JUMP);
     CR_NOTE_LAUNCH();
-    k_halve<<<nb(vtot), 256, 0, st>>>(u.lab, vtot);
+    for (int pass = 0; pass < 5; pass++) {
+        if (pass) CR_NOTE_LAUNCH();
+        k_double<<<nb(vtot), 256, 0, st>>>(u.lab, vtot);
+    }
     CR_NOTE_LAUNCH();
     k_find_root<<<nb(vtot), 256, 0, st>>>(u.lab, vtot, status);
     prof_end(st, STAGE_JUMP, 8.0 * vtot);
@@ -971,8 +986,8 @@ int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
     k_unmark<<<nb(vtot), 256, 0, st>>>(u.lab, vtot);
     prof_begin(st, STAGE_H0_CROSS);
     CR_NOTE_LAUNCH();
-    k_h0_cross<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, u.dd, u.ek[0], u.ea[0], u.eb[0], &u.cnt[1],
-                                         u.max_edges, &u.cnt[0], status);
+    k_h0_cross<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, u.ek[0], u.ea[0],
+                                                             u.eb[0], &u.cnt[1], u.max_edges, &u.cnt[0], status);
     prof_end(st, STAGE_H0_CROSS, 9.0 * vtot);
     int rc = rounds_coop(u, vtot, segs, 0, pb, flags, extra_mask, status, st);
     if (rc) return rc;
@@ -981,16 +996,19 @@ int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
-int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, UF &u, const PairBuf &pb,
-             uint32_t flags, int *status, cudaStream_t st) {
+int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, int64_t ntiles, UF &u,
+             const PairBuf &pb, uint32_t flags, int *status, cudaStream_t st) {
     cudaMemsetAsync(u.cnt, 0, 8 * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_DUAL_STENCIL);
     CR_NOTE_LAUNCH();
-    k_dual_stencil<<<nb(ctot), 256, 0, st>>>(img, segs, nseg, ctot, u.lab, u.dd, pb, flags);
+    k_dual_stencil<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, pb, flags);
     prof_end(st, STAGE_DUAL_STENCIL, 4.0 * vtot + 5.0 * ctot);
     prof_begin(st, STAGE_JUMP);
     CR_NOTE_LAUNCH();
-    k_halve<<<nb(ctot), 256, 0, st>>>(u.lab, ctot);
+    for (int pass = 0; pass < 5; pass++) {
+        if (pass) CR_NOTE_LAUNCH();
+        k_double<<<nb(ctot), 256, 0, st>>>(u.lab, ctot);
+    }
     CR_NOTE_LAUNCH();
     k_find_root<<<nb(ctot), 256, 0, st>>>(u.lab, ctot, status);
     prof_end(st, STAGE_JUMP, 8.0 * ctot);
@@ -1003,8 +1021,8 @@ int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t 
     k_unmark<<<nb(ctot), 256, 0, st>>>(u.lab, ctot);
     prof_begin(st, STAGE_DUAL_CROSS);
     CR_NOTE_LAUNCH();
-    k_dual_cross<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, u.dd, u.ek[0], u.ea[0], u.eb[0], &u.cnt[1],
-                                           u.max_edges, &u.cnt[0], status);
+    k_dual_cross<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, u.ek[0], u.ea[0],
+                                                               u.eb[0], &u.cnt[1], u.max_edges, &u.cnt[0], status);
     prof_end(st, STAGE_DUAL_CROSS, 4.0 * vtot + 5.0 * ctot);
     return rounds_coop(u, vtot, segs, 1, pb, flags, nullptr, status, st);
 }
