@@ -353,7 +353,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         if (B.pool_cap < 64) { set_host_detail(SITE_H1_CARVE); return CR_ERR_WORKSPACE; }
         B.pool = R.take<uint64_t>(B.pool_cap);
         int64_t ncols = 0;
-        rc = run_h1(imgs, dd, extra, segs, n, P.vtot, P.ntiles, B, pb, flags, status, &ncols, st);
+        rc = run_h1(imgs, dd, extra, segs, P.segs.data(), n, P.vtot, P.ntiles, B, pb, flags, status, &ncols, st);
         if (rc) return rc;
     }
 

@@ -200,6 +200,134 @@ __global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, uint64
 }
 
 // ---------------------------------------------------------------------------
+// The scan fed by TMA (single volumes whose rows are 16-byte multiples): the
+// block's 32x8x16 tile plus halo is one cp.async.bulk.tensor box in shared
+// memory; every edge, face and key is computed from it with 32-bit values.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_constant__ CUtensorMap tmap, Img3 I,
+                                                               const Seg *__restrict__ segs,
+                                                               uint64_t *__restrict__ colkey,
+                                                               uint32_t *__restrict__ colseg,
+                                                               unsigned long long *ncol, int64_t max_cols,
+                                                               PairBuf pb, uint32_t flags, int *status) {
+    __shared__ __align__(128) float box[TMA_BZ][TMA_BY][TMA_BX];
+    __shared__ __align__(8) uint64_t bar;
+    const Seg S = segs[0];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    uint32_t t = blockIdx.x;
+    const int tix = (int)(t % (uint32_t)S.tiles_x);
+    t /= (uint32_t)S.tiles_x;
+    const int tiy = (int)(t % (uint32_t)S.tiles_y);
+    const int tiz = (int)(t / (uint32_t)S.tiles_y);
+    const int x0 = tix * TILE_X, y0 = tiy * TILE_Y, z0 = tiz * TILE_Z;
+    if (threadIdx.x == 0) tma_load_box(&tmap, &box[0][0][0], &bar, x0, y0, z0);
+    __syncthreads();
+    if (!mbar_wait(&bar, 1ll << 24)) {
+        set_status(status, CR_ERR_TIMEOUT);
+        mbar_wait(&bar, 1ll << 24);
+        return;
+    }
+    const int tx = threadIdx.x & (TILE_X - 1), ty = threadIdx.x / TILE_X;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inxy = x < nx && y < ny;
+    const uint32_t plane = (uint32_t)nx * (uint32_t)ny, P = plane * (uint32_t)nz;
+    const int ext[3] = {nx, ny, nz};
+    const int bx = tx + 4, by = ty + 1;
+    const int zend = min(TILE_Z, nz - z0);
+    for (int zz = 0; zz < zend; zz++) {
+        const int z = z0 + zz, bz = zz + 1;
+        const int co[3] = {x, y, z};
+        const uint32_t lv = (uint32_t)z * plane + (uint32_t)y * nx + x;
+        const int64_t gv = S.voff + lv;
+        // ord value of the vertex at offset (dx, dy, dz) from this voxel
+        auto V = [&](int dx, int dy, int dz) -> uint32_t { return ord32(box[bz + dz][by + dy][bx + dx]); };
+        const uint32_t stride[3] = {1u, (uint32_t)nx, plane};
+        uint64_t keep0 = 0, keep1 = 0, keep2 = 0;
+        bool kf0 = false, kf1 = false, kf2 = false;
+        const uint8_t dv = inxy ? I.dd[gv] : 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            bool keep = false;
+            uint64_t sk = 0;
+            do {
+                if (!inxy || co[a] + 1 >= ext[a]) break;
+                // killed in dimension 0?
+                if (dv == (uint8_t)(2 * a + 2) || I.dd[gv + stride[a]] == (uint8_t)(2 * a + 1)) break;
+                const uint32_t sL = lv + (uint32_t)a * P;
+                if ((I.extra[(S.loff + sL) >> 5] >> ((S.loff + sL) & 31)) & 1u) break;
+                const int ax0 = a == 0, ay0 = a == 1, az0 = a == 2;
+                const uint32_t v0 = V(0, 0, 0), v1 = V(ax0, ay0, az0);
+                sk = make_key(v0 > v1 ? v0 : v1, sL);
+                // earliest cofacet: faces spanning {a, b}, anchored here or one step back in b
+                uint64_t tk = ~0ull;
+                int tb = 0, toff = 0;
+#pragma unroll
+                for (int b = 0; b < 3; b++) {
+                    if (b == a) continue;
+                    const int bx0 = b == 0, by0 = b == 1, bz0 = b == 2;
+                    const uint32_t ftype = (uint32_t)(a + b - 1);
+#pragma unroll
+                    for (int back = 0; back < 2; back++) {
+                        if (back == 0 ? co[b] + 1 >= ext[b] : co[b] < 1) continue;
+                        const int o = back ? -1 : 0;
+                        const int wx = o * bx0, wy = o * by0, wz = o * bz0;
+                        uint32_t m = V(wx, wy, wz), q;
+                        q = V(wx + ax0, wy + ay0, wz + az0);
+                        m = q > m ? q : m;
+                        q = V(wx + bx0, wy + by0, wz + bz0);
+                        m = q > m ? q : m;
+                        q = V(wx + ax0 + bx0, wy + ay0 + by0, wz + az0 + bz0);
+                        m = q > m ? q : m;
+                        const uint64_t fk = make_key(m, ftype * P + (back ? lv - stride[b] : lv));
+                        if (fk < tk) { tk = fk; tb = b; toff = o; }
+                    }
+                }
+                if (tk == ~0ull) { set_status(status, CR_ERR_INTERNAL); break; }
+                // is this edge the latest facet of that face?  Its edges: along a at w
+                // and w+e_b, along b at w and w+e_a (w = the face's anchor)
+                const int bx0 = tb == 0, by0 = tb == 1, bz0 = tb == 2;
+                const int wx = toff * bx0, wy = toff * by0, wz = toff * bz0;
+                const uint32_t wL = toff ? lv - stride[tb] : lv;
+                const uint32_t sb = tb == 0 ? 1u : (tb == 1 ? (uint32_t)nx : plane);
+                const uint32_t sa = stride[a];
+                uint32_t u0, u1;
+                uint64_t best;
+                u0 = V(wx, wy, wz); u1 = V(wx + ax0, wy + ay0, wz + az0);                       // along a at w
+                best = make_key(u0 > u1 ? u0 : u1, wL + (uint32_t)a * P);
+                u0 = V(wx + bx0, wy + by0, wz + bz0); u1 = V(wx + bx0 + ax0, wy + by0 + ay0, wz + bz0 + az0);  // along a at w+e_b
+                uint64_t e2 = make_key(u0 > u1 ? u0 : u1, wL + sb + (uint32_t)a * P);
+                best = e2 > best ? e2 : best;
+                u0 = V(wx, wy, wz); u1 = V(wx + bx0, wy + by0, wz + bz0);                       // along b at w
+                e2 = make_key(u0 > u1 ? u0 : u1, wL + (uint32_t)tb * P);
+                best = e2 > best ? e2 : best;
+                u0 = V(wx + ax0, wy + ay0, wz + az0); u1 = V(wx + ax0 + bx0, wy + ay0 + by0, wz + az0 + bz0);  // along b at w+e_a
+                e2 = make_key(u0 > u1 ? u0 : u1, wL + sa + (uint32_t)tb * P);
+                best = e2 > best ? e2 : best;
+                if (best == sk) {
+                    const int64_t bit = S.loff + key_L(tk);
+                    atomicOr(&I.appmask[bit >> 5], 1u << (bit & 31));
+                    if (flags & CR_KEEP_ZERO) emit_pair(pb, 0u, 1, key_value(sk), key_value(tk), sL, key_L(tk), 0);
+                } else {
+                    keep = true;
+                }
+            } while (0);
+            if (a == 0) { keep0 = sk; kf0 = keep; }
+            if (a == 1) { keep1 = sk; kf1 = keep; }
+            if (a == 2) { keep2 = sk; kf2 = keep; }
+        }
+        const int cnt = (int)kf0 + (int)kf1 + (int)kf2;
+        int64_t i0 = block_append(cnt, ncol);
+        if (i0 + cnt > max_cols) {
+            if (cnt) fail_ws(status, SITE_COLUMNS);
+        } else {
+            if (kf0) { colkey[i0] = ~keep0; colseg[i0++] = 0u; }
+            if (kf1) { colkey[i0] = ~keep1; colseg[i0++] = 0u; }
+            if (kf2) { colkey[i0] = ~keep2; colseg[i0++] = 0u; }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // 2. lock-free reduction
 // ---------------------------------------------------------------------------
 struct RedParams {
@@ -1160,16 +1288,22 @@ int h1_stats(int64_t *out, int n) {
     return CR_OK;
 }
 
-int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, int nseg, int64_t vtot,
-           int64_t ntiles, H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status, int64_t *ncols_out,
-           cudaStream_t st) {
+int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, const Seg *hseg, int nseg,
+           int64_t vtot, int64_t ntiles, H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status,
+           int64_t *ncols_out, cudaStream_t st) {
     Img3 I{img, dd, extra, B.appmask};
     cudaMemsetAsync(B.appmask, 0, (size_t)((3 * vtot + 31) / 32) * sizeof(uint32_t), st);
     cudaMemsetAsync(B.cnt, 0, 24 * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_H1_SCAN);
     CR_NOTE_LAUNCH();
-    k_h1_scan<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(I, segs, nseg, B.colkey, B.colseg, &B.cnt[0],
-                                                            B.max_cols, pb, flags, status);
+    CUtensorMap tmap;
+    if (nseg == 1 && hseg && hseg->edim == 3 && make_image_map(&tmap, img, *hseg)) {
+        k_h1_scan_tma<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(tmap, I, segs, B.colkey, B.colseg, &B.cnt[0],
+                                                                    B.max_cols, pb, flags, status);
+    } else {
+        k_h1_scan<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(I, segs, nseg, B.colkey, B.colseg, &B.cnt[0],
+                                                                B.max_cols, pb, flags, status);
+    }
     prof_end(st, STAGE_H1_SCAN, 5.0 * vtot);
     unsigned long long hc = 0;
     cudaMemcpyAsync(&hc, &B.cnt[0], sizeof(hc), cudaMemcpyDeviceToHost, st);

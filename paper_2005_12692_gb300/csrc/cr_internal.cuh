@@ -14,6 +14,7 @@
 #include <cstddef>
 #include <cstring>
 #include <atomic>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include "../../include/cr.h"
 
@@ -76,6 +77,85 @@ __device__ __forceinline__ int64_t block_append(int cnt, unsigned long long *cou
     int64_t base = (int64_t)s_base + s_w[w] + (incl - cnt);
     __syncthreads();
     return base;
+}
+
+constexpr int TMA_BX = TILE_X + 8, TMA_BY = TILE_Y + 2, TMA_BZ = TILE_Z + 2;
+constexpr int TMA_BYTES = TMA_BX * TMA_BY * TMA_BZ * 4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// wait on phase 0 of an mbarrier, at most `limit` polls; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, long long limit) {
+    uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+
+// wait on the given phase parity of an mbarrier, at most `limit` polls
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity, long long limit) {
+    uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void mbar_init1(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// arm the barrier for one box and issue the copy (one thread)
+__device__ __forceinline__ void tma_issue_box(const void *tmap, float *dst, uint64_t *bar, int x0, int y0, int z0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(TMA_BYTES)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(tmap), "r"(x0 - 4), "r"(y0 - 1), "r"(z0 - 1), "r"(smem_u32(bar))
+        : "memory");
+}
+// origin of tile t of a single image
+__device__ __forceinline__ void tile_origin(const Seg &S, uint32_t t, int &x0, int &y0, int &z0) {
+    const uint32_t tix = t % (uint32_t)S.tiles_x;
+    t /= (uint32_t)S.tiles_x;
+    const uint32_t tiy = t % (uint32_t)S.tiles_y;
+    const uint32_t tiz = t / (uint32_t)S.tiles_y;
+    x0 = (int)tix * TILE_X;
+    y0 = (int)tiy * TILE_Y;
+    z0 = (int)tiz * TILE_Z;
+}
+constexpr long long TMA_WAIT = 1ll << 24;
+
+// TMA copy of the box around a tile: x starts 4 voxels early (16-byte
+// boundary), y and z one voxel early; issued by one thread, completion on bar
+__device__ __forceinline__ void tma_load_box(const void *tmap, float *dst, uint64_t *bar, int x0, int y0, int z0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(TMA_BYTES)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(tmap), "r"(x0 - 4), "r"(y0 - 1), "r"(z0 - 1), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // Tile-grid launches (grid = tiles, block = TILE_X*TILE_Y threads): the
@@ -234,9 +314,11 @@ struct H1Bufs {
     unsigned long long *cnt;  // [0] columns, [1] arena top, [2] work counter, [3] pool top
 };
 int h1_stats(int64_t *out, int n);
-int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, int nseg, int64_t vtot,
-           int64_t ntiles, H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status, int64_t *ncols_out,
-           cudaStream_t st);
+// tensor map over one image as an (nx, ny, nz) float32 tensor with the tile box; false if TMA cannot serve it
+bool make_image_map(CUtensorMap *m, const float *img, const Seg &S);
+int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, const Seg *hseg, int nseg,
+           int64_t vtot, int64_t ntiles, H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status,
+           int64_t *ncols_out, cudaStream_t st);
 
 // radix sort of (u64 key, u32 value) by bits [lo, hi) of the key, stable, LSD.
 // tmp buffers must hold n entries each.  Returns cudaError.

@@ -229,30 +229,6 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tiled(const float
 // into shared memory, completing on an mbarrier.  Single images whose rows
 // are a multiple of 16 bytes.
 // ---------------------------------------------------------------------------
-constexpr int TMA_BX = TILE_X + 8, TMA_BY = TILE_Y + 2, TMA_BZ = TILE_Z + 2;
-constexpr int TMA_BYTES = TMA_BX * TMA_BY * TMA_BZ * 4;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// wait on phase 0 of an mbarrier, at most `limit` polls; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, long long limit) {
-    uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < limit; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
 __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tma(const __grid_constant__ CUtensorMap tmap,
                                                                   const Seg *__restrict__ segs,
                                                                   uint32_t *__restrict__ parent,
@@ -293,53 +269,39 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tma(const __grid_
     const int bx = threadIdx.x + 4, by = threadIdx.y + 1;
     bool nan_seen = false;
     const int zend = min(TILE_Z, nz - z0);
+    const uint32_t P = plane * (uint32_t)nz;  // size of one type's L-range
     for (int zz = 0; zz < zend; zz++) {
         const int z = z0 + zz, bz = zz + 1;
         const float fv = box[bz][by][bx];
         nan_seen |= isnan(fv);
         const uint32_t ov = ord32(fv);
         const uint32_t lv = (uint32_t)z * plane + (uint32_t)y * nx + x;
-        const uint64_t kv = make_key(ov, lv);
-        uint64_t best = ~0ull;
-        int bestdir = 0;
-        uint32_t bestou = 0, bestlu = 0;
-#pragma unroll
-        for (int d = 0; d < 6; d++) {
-            const int ax = d >> 1;
-            const bool pos = d & 1;
-            bool ok;
-            float fu;
-            uint32_t lu, la;
-            if (ax == 0) {
-                ok = pos ? x + 1 < nx : x > 0;
-                fu = box[bz][by][bx + (pos ? 1 : -1)];
-                lu = pos ? lv + 1 : lv - 1;
-                la = pos ? lv : lv - 1;
-            } else if (ax == 1) {
-                ok = pos ? y + 1 < ny : y > 0;
-                fu = box[bz][by + (pos ? 1 : -1)][bx];
-                lu = pos ? lv + nx : lv - nx;
-                la = (pos ? lv : lv - nx) + plane * (uint32_t)nz;
-            } else {
-                ok = pos ? z + 1 < nz : z > 0;
-                fu = box[bz + (pos ? 1 : -1)][by][bx];
-                lu = pos ? lv + plane : lv - plane;
-                la = (pos ? lv : lv - plane) + 2u * plane * (uint32_t)nz;
-            }
-            if (!ok) continue;
-            const uint32_t ou = ord32(fu);
-            const uint64_t ek = make_key(ov > ou ? ov : ou, la);
-            if (ek < best) {
-                best = ek;
-                bestdir = d + 1;
-                bestou = ou;
-                bestlu = lu;
-            }
+        // edges in descending L: +z, -z, +y, -y, +x, -x; a strictly smaller
+        // value wins, so among equal values the larger L (the earlier edge) stays
+        uint32_t bval = 0xFFFFFFFFu, bou = 0, blu = 0, bL = 0;
+        int bdir = 0;
+#define CR_EDGE(OK, UF, LU, LA, DIR)                           \
+        if (OK) {                                              \
+            const uint32_t ou_ = ord32(UF);                    \
+            const uint32_t ev_ = ov > ou_ ? ov : ou_;          \
+            if (bdir == 0 || ev_ < bval) {                     \
+                bval = ev_; bou = ou_; blu = (LU); bL = (LA); bdir = (DIR); \
+            }                                                  \
         }
-        if (bestdir && make_key(bestou, bestlu) < kv) {
-            parent[lv] = bestlu;
-            dd[lv] = (uint8_t)bestdir;
-            if (flags & CR_KEEP_ZERO) emit_pair(pb, 0u, 0, unord32(ov), key_value(best), lv, key_L(best), 0);
+        CR_EDGE(z + 1 < nz, box[bz + 1][by][bx], lv + plane, lv + 2u * P, 6)
+        CR_EDGE(z > 0, box[bz - 1][by][bx], lv - plane, lv - plane + 2u * P, 5)
+        CR_EDGE(y + 1 < ny, box[bz][by + 1][bx], lv + nx, lv + P, 4)
+        CR_EDGE(y > 0, box[bz][by - 1][bx], lv - nx, lv - nx + P, 3)
+        CR_EDGE(x + 1 < nx, box[bz][by][bx + 1], lv + 1, lv, 2)
+        CR_EDGE(x > 0, box[bz][by][bx - 1], lv - 1, lv - 1, 1)
+#undef CR_EDGE
+        // the neighbour is older iff (value, -L) is smaller
+        const bool older = bdir && (bou < ov || (bou == ov && blu > lv));
+        if (older) {
+            parent[lv] = blu;
+            dd[lv] = (uint8_t)bdir;
+            if (flags & CR_KEEP_ZERO)
+                emit_pair(pb, 0u, 0, unord32(ov), unord32(bval), lv, bL, 0);
         } else {
             parent[lv] = lv;
             dd[lv] = 0;
@@ -364,7 +326,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // a tensor map over one image as an (nx, ny, nz) float32 tensor; false if TMA cannot serve it
-static bool make_image_map(CUtensorMap *m, const float *img, const Seg &S) {
+bool make_image_map(CUtensorMap *m, const float *img, const Seg &S) {
     if (((uintptr_t)img & 15) || (S.nx % 4) != 0) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
