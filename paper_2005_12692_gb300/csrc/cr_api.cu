@@ -128,7 +128,7 @@ static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
     int64_t nodes = P.vtot > P.ctot ? P.vtot : P.ctot;
     size_t uf, h1 = 0, out;
     if (worst) {
-        uf = al((size_t)nodes * 33) + al((size_t)(3 * P.vtot) * 32) + (1 << 20);
+        uf = al((size_t)nodes * 45) + al((size_t)(3 * P.vtot) * 32) + (1 << 20);
     } else {
         uf = al((size_t)nodes * 16) + al((size_t)P.vtot * 48) + (8 << 20);
     }
@@ -192,51 +192,69 @@ __global__ void k_out_offsets(const uint32_t *scanned, int n, int64_t np, int64_
 }
 static inline unsigned nbk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-// One block sorts up to SMALL_SORT pairs of a single image in shared memory
-// (bitonic network on a packed key dim:2 | ord32(birth):32 | birth_cell:30)
-// and gathers them; tmp receives a copy of the unsorted pairs.
+// Up to SMALL_SORT pairs of a single image are ordered by rank: the packed
+// key dim:2 | ord32(birth):32 | birth_cell:30 is unique (a cell gives birth
+// to at most one class of its dimension), so the destination of pair i is the
+// number of smaller keys.  Blocks own RK_T*RK_R pairs and one slice of the
+// keys to compare against, so a few thousand pairs still spread over the GPU.
 constexpr int SMALL_SORT = 16384;
-__global__ void __launch_bounds__(1024) k_out_small_sort(cr_pair *pairs, int np, cr_pair *tmp) {
-    extern __shared__ unsigned char sbuf[];
-    int npow = 1;
-    while (npow < np) npow <<= 1;
-    uint64_t *key = (uint64_t *)sbuf;
-    uint32_t *idx = (uint32_t *)(key + npow);
-    for (int i = threadIdx.x; i < npow; i += blockDim.x) {
-        if (i < np) {
-            cr_pair p = pairs[i];
-            tmp[i] = p;
-            key[i] = ((uint64_t)(p.dim & 3) << 62) | ((uint64_t)ord32(p.birth) << 30) | (uint64_t)(p.birth_cell & 0x3FFFFFFF);
-        } else {
-            key[i] = ~0ull;
-        }
-        idx[i] = (uint32_t)i;
+constexpr int RK_T = 128, RK_R = 4, RK_TILE = 1024;
+
+__device__ __forceinline__ uint64_t pair_sort_key(const cr_pair *p) {
+    return ((uint64_t)(p->dim & 3) << 62) | ((uint64_t)ord32(p->birth) << 30) | (uint64_t)(p->birth_cell & 0x3FFFFFFF);
+}
+
+// rank[i] += #{j in this block's slice : key_j < key_i}; slice 0 also copies
+// the pairs to tmp
+__global__ void __launch_bounds__(RK_T) k_out_rank(const cr_pair *__restrict__ pairs, int np, int chunk,
+                                                   uint32_t *__restrict__ rank, cr_pair *__restrict__ tmp) {
+    __shared__ uint64_t tile[RK_TILE];
+    uint64_t mine[RK_R];
+    uint32_t cnt[RK_R];
+    const int base = blockIdx.x * RK_T * RK_R;
+#pragma unroll
+    for (int r = 0; r < RK_R; r++) {
+        const int i = base + r * RK_T + threadIdx.x;
+        mine[r] = i < np ? pair_sort_key(pairs + i) : 0ull;
+        cnt[r] = 0;
+        if (blockIdx.y == 0 && i < np) tmp[i] = pairs[i];
     }
-    __syncthreads();
-    for (int k = 2; k <= npow; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < npow; i += blockDim.x) {
-                int l = i ^ j;
-                if (l > i) {
-                    bool up = (i & k) == 0;
-                    uint64_t a = key[i], b = key[l];
-                    if ((a > b) == up) {
-                        key[i] = b;
-                        key[l] = a;
-                        uint32_t t = idx[i];
-                        idx[i] = idx[l];
-                        idx[l] = t;
-                    }
-                }
+    const int j0 = blockIdx.y * chunk, j1 = min(np, j0 + chunk);
+    for (int t0 = j0; t0 < j1; t0 += RK_TILE) {
+        const int n = min(RK_TILE, j1 - t0);
+        for (int q = threadIdx.x; q < n; q += RK_T) tile[q] = pair_sort_key(pairs + t0 + q);
+        __syncthreads();
+        int q = 0;
+        for (; q + 4 <= n; q += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint64_t kj = tile[q + u];
+#pragma unroll
+                for (int r = 0; r < RK_R; r++) cnt[r] += kj < mine[r] ? 1u : 0u;
             }
-            __syncthreads();
         }
+        for (; q < n; q++) {
+            const uint64_t kj = tile[q];
+#pragma unroll
+            for (int r = 0; r < RK_R; r++) cnt[r] += kj < mine[r] ? 1u : 0u;
+        }
+        __syncthreads();
     }
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        cr_pair p = tmp[idx[i]];
-        p.flags &= 0xFFu;
-        pairs[i] = p;
+#pragma unroll
+    for (int r = 0; r < RK_R; r++) {
+        const int i = base + r * RK_T + threadIdx.x;
+        if (i < np && cnt[r]) atomicAdd(&rank[i], cnt[r]);
     }
+}
+
+__global__ void k_out_place(const cr_pair *__restrict__ tmp, int np, const uint32_t *__restrict__ rank,
+                            cr_pair *__restrict__ pairs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    cr_pair p = tmp[i];
+    p.flags &= 0xFFu;
+    const uint32_t d = rank[i];
+    if (d < (uint32_t)np) pairs[d] = p;
 }
 
 // ---------------------------------------------------------------------------
@@ -287,14 +305,15 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         // groups: the number of roots is not known yet; give the union-find a
         // share of the region proportional to the node count and the rest to edges
         int64_t max_groups = P.vtot;
-        size_t gbytes = (size_t)max_groups * 33 + 6 * 256;
-        if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 33) - 64;
+        size_t gbytes = (size_t)max_groups * 45 + 8 * 256;
+        if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 45) - 64;
         if (max_groups < 1) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
         u.gkey = R.take<uint64_t>(max_groups);
         u.minE = R.take<uint64_t>(max_groups);
         u.groot = R.take<uint32_t>(max_groups);
         u.gseg = R.take<uint32_t>(max_groups);
-        u.tgt = R.take<uint32_t>(max_groups);
+        u.minE2 = R.take<uint64_t>(max_groups);
+        u.dkey = R.take<uint64_t>(max_groups);
         u.hook = R.take<uint32_t>(max_groups);
         u.gdead = R.take<uint8_t>(max_groups);
         u.max_groups = max_groups;
@@ -366,14 +385,15 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         u.cnt = &cnt[48];
         u.hcnt = hc;
         int64_t max_groups = P.ctot;
-        size_t gbytes = (size_t)max_groups * 33 + 6 * 256;
-        if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 33) - 64;
+        size_t gbytes = (size_t)max_groups * 45 + 8 * 256;
+        if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 45) - 64;
         if (max_groups < 1) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
         u.gkey = R.take<uint64_t>(max_groups);
         u.minE = R.take<uint64_t>(max_groups);
         u.groot = R.take<uint32_t>(max_groups);
         u.gseg = R.take<uint32_t>(max_groups);
-        u.tgt = R.take<uint32_t>(max_groups);
+        u.minE2 = R.take<uint64_t>(max_groups);
+        u.dkey = R.take<uint64_t>(max_groups);
         u.hook = R.take<uint32_t>(max_groups);
         u.gdead = R.take<uint8_t>(max_groups);
         u.max_groups = max_groups;
@@ -403,12 +423,13 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         g_detail = hstatus[8];
         return hstatus[0];
     }
-    // algorithmic bytes of the union-find rounds: per round and edge 88 B
-    // (edge reads in four phases, min-edge updates, relabel writes), per
-    // group 12 B (hook chase and min-edge reset); counters of both runs
+    // algorithmic bytes of the union-find rounds, per round and live edge
+    // 104 B (phase B: the edge, both ends' min edge and age key; phase D: the
+    // edge, both ends' root, the kept edge and both min-edge updates), per
+    // group and round 12 B (min-edge reset, hook read); counters of both runs
     for (int base : {8, 48}) {
         double e = (double)ufc[base + 3], r = (double)ufc[base + 6], g = (double)ufc[base + 0];
-        prof_add_bytes(STAGE_UF_ROUND, 88.0 * e + 12.0 * g * r);
+        prof_add_bytes(STAGE_UF_ROUND, 104.0 * e + 12.0 * g * r);
     }
     int64_t np = (int64_t)hc[0];
     *n_pairs = np;
@@ -427,18 +448,19 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         if (!R.ok) { g_detail = SITE_OUT_CARVE; return CR_ERR_WORKSPACE; }
         bool small = n == 1 && np <= SMALL_SORT && 3 * P.vtot < ((int64_t)1 << 30);
         if (np > 0 && small) {
-            static bool attr = false;
-            size_t smem = 0;
-            int npow = 1;
-            while (npow < np) npow <<= 1;
-            smem = (size_t)npow * 12;
-            if (!attr) {
-                cudaFuncSetAttribute(k_out_small_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_SORT * 12);
-                attr = true;
-            }
+            // blocks over pairs x slices of the keys: about two blocks per SM
+            const int nbx = (int)((np + RK_T * RK_R - 1) / (RK_T * RK_R));
+            int slices = (2 * num_sms() + nbx - 1) / nbx;
+            if (slices < 1) slices = 1;
+            if (slices > 64) slices = 64;
+            int chunk = (int)((np + slices - 1) / slices);
+            slices = (int)((np + chunk - 1) / chunk);
             prof_begin(st, STAGE_OUT_SORT);
+            cudaMemsetAsync(v0, 0, (size_t)np * sizeof(uint32_t), st);
             CR_NOTE_LAUNCH();
-            k_out_small_sort<<<1, 1024, smem, st>>>(pairs_out, (int)np, tmp);
+            k_out_rank<<<dim3((unsigned)nbx, (unsigned)slices), RK_T, 0, st>>>(pairs_out, (int)np, chunk, v0, tmp);
+            CR_NOTE_LAUNCH();
+            k_out_place<<<nbk(np), 256, 0, st>>>(tmp, (int)np, v0, pairs_out);
             prof_end(st, STAGE_OUT_SORT, 64.0 * np);
         } else if (np > 0) {
             prof_begin(st, STAGE_OUT_SORT);

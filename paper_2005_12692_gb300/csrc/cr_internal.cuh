@@ -280,8 +280,9 @@ struct UF {
     uint64_t *gkey;  // group -> age key of its root (smaller = older)
     uint32_t *groot, *gseg;
     uint8_t *gdead;
-    uint64_t *minE;
-    uint32_t *tgt, *hook;
+    uint64_t *minE, *minE2;  // min edge key at each group, for this round and the next
+    uint64_t *dkey;          // key of the edge a group died at
+    uint32_t *hook;
     uint64_t *ek[2];
     uint32_t *ea[2], *eb[2];
     int64_t max_edges, max_groups;

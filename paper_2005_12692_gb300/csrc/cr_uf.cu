@@ -723,34 +723,32 @@ struct RoundArgs {
     int *status;
 };
 
-// Barrier over the first `active` blocks of the grid; returns false when the
-// wait gave up (the status word then holds CR_ERR_TIMEOUT) or an error is set.
-__device__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen, unsigned int active, int *status) {
-    __syncthreads();
+// Grid barrier on a monotonic arrival counter: thread 0 of every block adds 1
+// with release semantics and polls with acquire loads until all blocks of
+// barrier number n have arrived (counter >= n * blocks).  Returns false when
+// another block reported an error or the wait gave up (CR_ERR_TIMEOUT).
+constexpr long long BARRIER_POLLS = 1ll << 24;
+__device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int &target, int *status) {
     __shared__ int s_ok;
+    target += gridDim.x;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        s_ok = 1;
-        if (active > 1) {
-            unsigned int g = *gen;
-            __threadfence();
-            unsigned int arrived = atomicAdd(count, 1u);
-            if (arrived == active - 1) {
-                *count = 0;
-                __threadfence();
-                atomicAdd((unsigned int *)gen, 1u);
-            } else {
-                long long spins = 0;
-                while (*gen == g) {
-                    if (++spins > (1ll << 28)) {  // far beyond any phase of a round
-                        set_status(status, CR_ERR_TIMEOUT);
-                        s_ok = 0;
-                        break;
-                    }
+        int ok = 1;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        for (long long polls = 1;; polls++) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if ((polls & 63) == 0) {
+                if (*(volatile int *)status) { ok = 0; break; }
+                if (polls > BARRIER_POLLS) {
+                    set_status(status, CR_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
             }
         }
-        __threadfence();
-        if (*(volatile int *)status) s_ok = 0;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -758,130 +756,236 @@ __device__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen, un
 
 constexpr int UF_THREADS = 1024;
 
-// One round = four phases separated by grid barriers:
-//   A  (edges)  minE[g] <- min key of the edges at g   (minE was reset in C)
-//   B  (edges)  the edge attaining minE[g] decides g's hook by the elder rule
-//               and emits the death; only that edge writes g's entries
-//   C  (groups) chase hooks to the round's roots; reset minE for the next round
-//   D  (edges)  relabel endpoints to roots, drop edges inside a group, compact
-__global__ void __launch_bounds__(UF_THREADS) k_uf_rounds(RoundArgs A) {
+#ifdef CR_UF_TIMING
+// diagnostics build: block 0 records the global timer at every phase end
+__device__ unsigned long long g_uf_trace[2][1024];
+__device__ int g_uf_trace_n[2];
+#define UF_MARK(v)                                                              \
+    do {                                                                        \
+        if (blockIdx.x == 0 && threadIdx.x == 0) {                              \
+            int m_ = g_uf_trace_n[A.mode];                                      \
+            if (m_ < 1024) {                                                    \
+                unsigned long long t_;                                          \
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));          \
+                g_uf_trace[A.mode][m_] = (t_ << 20) | ((unsigned long long)(v) & 0xFFFFF); \
+                g_uf_trace_n[A.mode] = m_ + 1;                                  \
+            }                                                                   \
+        }                                                                       \
+    } while (0)
+#else
+#define UF_MARK(v) \
+    do {           \
+    } while (0)
+#endif
+
+// Borůvka rounds under the elder rule, three phases per round:
+//   B  (edges)  the edge attaining minE[g] decides g's hook: g dies into the
+//               other end if that end is older (death key kept in dkey[g]).
+//               Groups clear the other min-edge buffer for the next round.
+//   C  (groups) pointer jumping to the round's roots; every thread writes only
+//               its own group's hook, always with an ancestor
+//   D  (edges)  endpoints move to their roots and are offered to the next
+//               round's min edge of both ends; edges inside a group drop out
+// While there are more edges than threads, D compacts the survivors into the
+// other edge buffer.  Once they fit, the list stays in place: an edge whose
+// ends meet is marked by a == b and skipped, which saves the compaction's
+// atomic and its count read on every round's critical path.
+// The first round's min edges come from a prologue phase; the deaths are
+// written out after the rounds by k_uf_emit.
+__global__ void __launch_bounds__(UF_THREADS, 1) k_uf_rounds(RoundArgs A) {
     UF &u = A.u;
-    unsigned int *bar_count = (unsigned int *)&u.cnt[4];
-    volatile unsigned int *bar_gen = (volatile unsigned int *)&u.cnt[5];
+    unsigned int *bar = (unsigned int *)&u.cnt[4];
+    unsigned long long *live_total = &u.cnt[7];
+    unsigned int target = 0;
     if (*(volatile int *)A.status) return;
-    const int lane = threadIdx.x & 31;
-    const unsigned int active = gridDim.x;
+#ifdef CR_UF_TIMING
+    if (blockIdx.x == 0 && threadIdx.x == 0) g_uf_trace_n[A.mode] = 0;
+#endif
+    UF_MARK(0);
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     int64_t ng = (int64_t)*(volatile unsigned long long *)&u.cnt[0];
     if (ng > u.max_groups) ng = u.max_groups;
-    unsigned long long *necnt[2] = {&u.cnt[1], &u.cnt[2]};
     for (int64_t g = tid; g < ng; g += nthr) {
         u.gdead[g] = 0;
         u.hook[g] = (uint32_t)g;
         u.minE[g] = ~0ull;
     }
-    if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
+    if (!grid_barrier(bar, target, A.status)) return;
+    UF_MARK(1);
+    int64_t ne = (int64_t)__ldcg(&u.cnt[1]);
+    if (ne > u.max_edges) ne = u.max_edges;
+    for (int64_t i = tid; i < ne; i += nthr) {
+        const unsigned long long k = u.ek[0][i];
+        const uint32_t a = u.ea[0][i], b = u.eb[0][i];
+        if (__ldcg(u.minE + a) > k) atomicMin((unsigned long long *)&u.minE[a], k);
+        if (__ldcg(u.minE + b) > k) atomicMin((unsigned long long *)&u.minE[b], k);
+    }
+    if (!grid_barrier(bar, target, A.status)) return;
+    UF_MARK(2);
     int cur = 0;
+    bool inplace = false;
+    unsigned long long live_seen = 0;
+    int64_t live = ne;
     for (int round = 0; round < (1 << 20); round++) {
-        int64_t ne = (int64_t)*(volatile unsigned long long *)necnt[cur];
-        if (ne > u.max_edges) ne = u.max_edges;
-        if (ne == 0) break;
+        unsigned long long *nnext = cur ? &u.cnt[1] : &u.cnt[2];
+        if (round > 0) {
+            if (inplace) {
+                const unsigned long long v = __ldcg(live_total);
+                live = (int64_t)(v - live_seen);
+                live_seen = v;
+            } else {
+                ne = (int64_t)__ldcg(cur ? &u.cnt[2] : &u.cnt[1]);
+                if (ne > u.max_edges) ne = u.max_edges;
+                live = ne;
+            }
+        }
+        if (live == 0) break;
+        const bool compact = !inplace && ne > nthr;
         if (tid == 0) {
-            *necnt[cur ^ 1] = 0;
-            u.cnt[3] += (unsigned long long)ne;  // edges visited, for the algorithmic byte count
-            u.cnt[6] += 1ull;                    // rounds
+            if (compact) *nnext = 0;
+            u.cnt[3] += (unsigned long long)live;  // edges visited, for the algorithmic byte count
+            u.cnt[6] += 1ull;                      // rounds
         }
-        const uint64_t *ek = u.ek[cur];
-        const uint32_t *ea = u.ea[cur], *eb = u.eb[cur];
-        // A
-        for (int64_t i = tid; i < ne; i += nthr) {
-            unsigned long long k = ek[i];
-            uint32_t a = ea[i], b = eb[i];
-            if (u.minE[a] > k) atomicMin((unsigned long long *)&u.minE[a], k);
-            if (u.minE[b] > k) atomicMin((unsigned long long *)&u.minE[b], k);
-        }
-        if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
+        uint64_t *ek = cur ? u.ek[1] : u.ek[0];
+        uint32_t *ea = cur ? u.ea[1] : u.ea[0], *eb = cur ? u.eb[1] : u.eb[0];
+        // the min-edge buffers alternate every round, the edge buffers only
+        // when the list is compacted
+        const uint64_t *mcur = (round & 1) ? u.minE2 : u.minE;
+        uint64_t *mnext = (round & 1) ? u.minE : u.minE2;
         // B
         for (int64_t i = tid; i < ne; i += nthr) {
-            uint64_t k = ek[i];
-            uint32_t ends[2] = {ea[i], eb[i]};
-            for (int s2 = 0; s2 < 2; s2++) {
-                uint32_t g = ends[s2], t = ends[s2 ^ 1];
-                if (u.minE[g] != k || !(u.gkey[t] < u.gkey[g])) continue;
-                u.hook[g] = t;
-                u.gdead[g] = 1;
-                uint32_t si = u.gseg[g];
-                if (A.mode == 0) {
-                    uint64_t kb = u.gkey[g];
-                    float bv = key_value(kb), dv = key_value(k);
-                    if ((A.flags & CR_KEEP_ZERO) || bv != dv) emit_pair(A.pb, si, 0, bv, dv, key_L(kb), key_L(k), 0);
-                    if (A.extra_mask) {
-                        int64_t bit = A.segs[si].loff + key_L(k);
-                        atomicOr(&A.extra_mask[bit >> 5], 1u << (bit & 31));
-                    }
-                } else {
-                    uint64_t kf = ~k, kc = ~u.gkey[g];
-                    float bv = key_value(kf), dv = key_value(kc);
-                    if ((A.flags & CR_KEEP_ZERO) || bv != dv)
-                        emit_pair(A.pb, si, A.segs[si].edim - 1, bv, dv, key_L(kf), key_L(kc), 0);
-                }
-            }
+            const uint64_t k = ek[i];
+            const uint32_t e0 = ea[i], e1 = eb[i];
+            if (e0 == e1) continue;  // dropped edge (in-place list)
+            const uint64_t m0 = __ldcg(mcur + e0), m1 = __ldcg(mcur + e1);
+            const uint64_t k0 = u.gkey[e0], k1 = u.gkey[e1];
+            // only the younger end can die, and only on its own min edge
+            const bool young0 = k1 < k0;
+            const uint32_t g = young0 ? e0 : e1, t = young0 ? e1 : e0;
+            if ((young0 ? m0 : m1) != k) continue;
+            u.hook[g] = t;
+            u.gdead[g] = 1;
+            u.dkey[g] = k;
         }
-        if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
+        for (int64_t g = tid; g < ng; g += nthr) mnext[g] = ~0ull;
+        if (!grid_barrier(bar, target, A.status)) return;
+        UF_MARK(live);
         // C
         for (int64_t g = tid; g < ng; g += nthr) {
-            uint32_t b = u.hook[g];
-            if (b != (uint32_t)g) {
-                int it = 0;
-                while (it++ < (1 << 24)) {
-                    uint32_t c = u.hook[b];
-                    if (c == b) break;
-                    b = c;
-                }
-                u.hook[g] = b;
+            uint32_t p = __ldcg(u.hook + g);
+            if (p == (uint32_t)g) continue;
+            for (int it = 0; it < (1 << 24); it++) {
+                const uint32_t pp = __ldcg(u.hook + p);
+                if (pp == p) break;
+                p = pp;
+                u.hook[g] = p;
             }
-            u.minE[g] = ~0ull;
         }
-        if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
+        if (!grid_barrier(bar, target, A.status)) return;
+        UF_MARK(live);
         // D
-        {
-            uint64_t *ok = u.ek[cur ^ 1];
-            uint32_t *oa = u.ea[cur ^ 1], *ob = u.eb[cur ^ 1];
+        if (compact) {
+            uint64_t *ok = cur ? u.ek[0] : u.ek[1];
+            uint32_t *oa = cur ? u.ea[0] : u.ea[1], *ob = cur ? u.eb[0] : u.eb[1];
             for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ne; base += nthr) {
-                int64_t i = base + threadIdx.x;
+                const int64_t i = base + threadIdx.x;
                 bool keep = false;
                 uint32_t a = 0, b = 0;
-                uint64_t k = 0;
+                uint64_t k = 0, ma = 0, mb = 0;
                 if (i < ne) {
-                    a = u.hook[ea[i]];
-                    b = u.hook[eb[i]];
+                    a = __ldcg(u.hook + ea[i]);
+                    b = __ldcg(u.hook + eb[i]);
                     k = ek[i];
                     keep = a != b;
+                    if (keep) {
+                        ma = __ldcg(mnext + a);
+                        mb = __ldcg(mnext + b);
+                    }
                 }
-                int64_t j = block_append(keep ? 1 : 0, necnt[cur ^ 1]);
+                const int64_t j = block_append(keep ? 1 : 0, nnext);
                 if (keep) {
                     ok[j] = k;
                     oa[j] = a;
                     ob[j] = b;
+                    if (ma > k) atomicMin((unsigned long long *)&mnext[a], k);
+                    if (mb > k) atomicMin((unsigned long long *)&mnext[b], k);
                 }
-
             }
+            cur ^= 1;
+        } else {
+            inplace = true;
+            int nlive = 0;
+            for (int64_t i = tid; i < ne; i += nthr) {
+                const uint32_t e0 = ea[i], e1 = eb[i];
+                const uint64_t k = ek[i];
+                if (e0 == e1) continue;
+                const uint32_t a = __ldcg(u.hook + e0), b = __ldcg(u.hook + e1);
+                if (a == b) {
+                    ea[i] = a;
+                    eb[i] = a;
+                    continue;
+                }
+                const uint64_t ma = __ldcg(mnext + a), mb = __ldcg(mnext + b);
+                if (a != e0) ea[i] = a;
+                if (b != e1) eb[i] = b;
+                if (ma > k) atomicMin((unsigned long long *)&mnext[a], k);
+                if (mb > k) atomicMin((unsigned long long *)&mnext[b], k);
+                nlive++;
+            }
+            nlive = __reduce_add_sync(0xFFFFFFFFu, nlive);
+            if ((threadIdx.x & 31) == 0 && nlive) atomicAdd(live_total, (unsigned long long)nlive);
         }
-        if (!grid_barrier(bar_count, bar_gen, active, A.status)) return;
-        cur ^= 1;
+        if (!grid_barrier(bar, target, A.status)) return;
+        UF_MARK(live);
     }
 }
 
-// the essential class of each image: the group that never died (primal only)
-__global__ void k_h0_essential_dev(const unsigned long long *ngp, int64_t max_groups, const uint8_t *__restrict__ gdead,
-                                   const uint64_t *__restrict__ gkey, const uint32_t *__restrict__ gseg, PairBuf pb) {
+// After the rounds: every group that died gives one pair (primal: born at the
+// group's root, dying at its death edge, which is also marked as killed in
+// dimension 0 for the middle dimension; dual: the reversed pair one dimension
+// up).  The one surviving primal group of each image is its essential class.
+__global__ void k_uf_emit(const unsigned long long *ngp, UF u, int mode, const Seg *__restrict__ segs, PairBuf pb,
+                          uint32_t flags, uint32_t *extra_mask) {
     int64_t ng = (int64_t)*ngp;
-    if (ng > max_groups) ng = max_groups;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
-        if (gdead[g]) continue;
-        uint64_t k = gkey[g];
-        emit_pair(pb, gseg[g], 0, key_value(k), __int_as_float(0x7f800000), key_L(k), -1, CR_PAIR_ESSENTIAL);
+    if (ng > u.max_groups) ng = u.max_groups;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ng; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = base + threadIdx.x;
+        int emit = 0;
+        cr_pair p;
+        if (g < ng) {
+            const uint64_t kb = u.gkey[g];
+            const uint32_t si = u.gseg[g];
+            if (!u.gdead[g]) {
+                if (mode == 0) {
+                    p = cr_pair{0, key_value(kb), __int_as_float(0x7f800000), CR_PAIR_ESSENTIAL | (si << 8),
+                                (int64_t)key_L(kb), -1};
+                    emit = 1;
+                }
+            } else {
+                const uint64_t k = u.dkey[g];
+                if (mode == 0) {
+                    const float bv = key_value(kb), dv = key_value(k);
+                    if (extra_mask) {
+                        const int64_t bit = segs[si].loff + key_L(k);
+                        atomicOr(&extra_mask[bit >> 5], 1u << (bit & 31));
+                    }
+                    if ((flags & CR_KEEP_ZERO) || bv != dv) {
+                        p = cr_pair{0, bv, dv, si << 8, (int64_t)key_L(kb), (int64_t)key_L(k)};
+                        emit = 1;
+                    }
+                } else {
+                    const uint64_t kf = ~k, kc = ~kb;
+                    const float bv = key_value(kf), dv = key_value(kc);
+                    if ((flags & CR_KEEP_ZERO) || bv != dv) {
+                        p = cr_pair{segs[si].edim - 1, bv, dv, si << 8, (int64_t)key_L(kf), (int64_t)key_L(kc)};
+                        emit = 1;
+                    }
+                }
+            }
+        }
+        const int64_t j = block_append(emit, pb.count);
+        if (emit && j < pb.capacity) pb.pairs[j] = p;
     }
 }
 
@@ -954,7 +1058,7 @@ int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
     int rc = rounds_coop(u, vtot, segs, 0, pb, flags, extra_mask, status, st);
     if (rc) return rc;
     CR_NOTE_LAUNCH();
-    k_h0_essential_dev<<<2 * sm_count(), 256, 0, st>>>(&u.cnt[0], u.max_groups, u.gdead, u.gkey, u.gseg, pb);
+    k_uf_emit<<<2 * sm_count(), 256, 0, st>>>(&u.cnt[0], u, 0, segs, pb, flags, extra_mask);
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
@@ -986,7 +1090,21 @@ int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t 
     k_dual_cross<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, u.ek[0], u.ea[0],
                                                                u.eb[0], &u.cnt[1], u.max_edges, &u.cnt[0], status);
     prof_end(st, STAGE_DUAL_CROSS, 4.0 * vtot + 5.0 * ctot);
-    return rounds_coop(u, vtot, segs, 1, pb, flags, nullptr, status, st);
+    int rc = rounds_coop(u, vtot, segs, 1, pb, flags, nullptr, status, st);
+    if (rc) return rc;
+    CR_NOTE_LAUNCH();
+    k_uf_emit<<<2 * sm_count(), 256, 0, st>>>(&u.cnt[0], u, 1, segs, pb, flags, nullptr);
+    return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
 }  // namespace cr
+
+#ifdef CR_UF_TIMING
+extern "C" int cr_debug_uf_trace(int mode, unsigned long long *out, int cap) {
+    int n = 0;
+    cudaMemcpyFromSymbol(&n, cr::g_uf_trace_n, sizeof(int), mode * sizeof(int));
+    if (n > cap) n = cap;
+    cudaMemcpyFromSymbol(out, cr::g_uf_trace, n * sizeof(unsigned long long), mode * 1024 * sizeof(unsigned long long));
+    return n;
+}
+#endif
