@@ -35,11 +35,11 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOADS = {
-    "uniform64": dict(kind="single", shape=(64, 64), maxdim=1),
-    "grf1024": dict(kind="single", shape=(1024, 1024), maxdim=1),
-    "grf256cube_salt": dict(kind="single", shape=(256, 256, 256), maxdim=2),
-    "grf512cube": dict(kind="single", shape=(512, 512, 512), maxdim=2),
-    "batch4096": dict(kind="batch", n=4096, maxdim=1),
+    "uniform64": dict(kind="single", shape=(64, 64), maxdim=1, steps=500),
+    "grf1024": dict(kind="single", shape=(1024, 1024), maxdim=1, steps=200),
+    "grf256cube_salt": dict(kind="single", shape=(256, 256, 256), maxdim=2, steps=10),
+    "grf512cube": dict(kind="single", shape=(512, 512, 512), maxdim=2, steps=5),
+    "batch4096": dict(kind="batch", n=4096, maxdim=1, steps=10),
 }
 
 
@@ -69,7 +69,12 @@ def num_cells(shape):
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling (every 20 ms) from before the warm-up to the end of
+    the timed region.  Samples carry nvidia-smi's own timestamps; the report
+    uses those inside the timed region, or, when the region is shorter than
+    the sampling period, the nearest sample on each side of it (the GPU is
+    running the same steps then: warm-up and the profiled pass precede it)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -82,10 +87,13 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:  # sampler live before the GPU work starts
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
@@ -93,9 +101,18 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    @staticmethod
+    def _ts(text):
+        from datetime import datetime
+        try:
+            return datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, region):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.05)  # one more sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -103,22 +120,33 @@ class ClockSampler:
             self.proc.kill()
         if self.t:
             self.t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                rows.append((self._ts(parts[0]), float(parts[2]), float(parts[3]),
+                             {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        t0, t1 = region
+        inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+        window = "timed region"
+        use = inside
+        if not use:
+            before = [r for r in rows if r[0] is not None and r[0] < t0]
+            after = [r for r in rows if r[0] is not None and r[0] > t1]
+            use = before[-1:] + after[:1]
+            window = "nearest sample on each side of the timed region (%.1f ms, shorter than the 20 ms sampling)" \
+                % ((t1 - t0) * 1e3)
+        reasons = set()
+        for r in use:
+            reasons |= r[3]
+        return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "reasons": sorted(reasons), "samples": len(use), "window": window}
 
 
 # ---------------------------------------------------------------------------
@@ -144,6 +172,33 @@ def read_profile(cr):
 SINGLE_KERNEL_STAGES = ("h0_stencil", "h0_cross", "dual_stencil", "dual_cross", "h1_scan", "h1_reduce", "uf_round")
 
 
+# what bounds each kernel in practice (the roofline denominator is HBM for all)
+LIMITER = {"uf_round": "latency: grid barriers and dependent loads per phase",
+           "h1_reduce": "latency: serial chain of the longest column",
+           "h0_cross": "latency: scattered neighbour label loads",
+           "dual_cross": "latency: scattered neighbour label loads"}
+
+
+def dominant_stage(stages):
+    best = None
+    for k in SINGLE_KERNEL_STAGES:
+        if k in stages and (best is None or stages[k]["ms"] > stages[best]["ms"]):
+            best = k
+    return best
+
+
+def stage_index(cr, name):
+    import ctypes
+    L = cr.lib()
+    nm = ctypes.c_char_p()
+    for s in range(64):
+        if L.cr_profile_read(s, ctypes.byref(nm), None, None, None) != 0:
+            break
+        if nm.value.decode() == name:
+            return s
+    raise KeyError(name)
+
+
 def roofline_from(stages, peaks, sustained=True):
     best = None
     for k in SINGLE_KERNEL_STAGES:
@@ -162,7 +217,8 @@ def roofline_from(stages, peaks, sustained=True):
         peak, src = 6800.0, "fallback"
     return {"kernel": best, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": src, "traffic": None,
-            "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_s * 1e3}
+            "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_s * 1e3,
+            "limiter": LIMITER.get(best, "hbm")}
 
 
 def load_peaks():
@@ -211,7 +267,8 @@ def run_oracle(name, data):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default per workload: enough for a timed region of ~0.1 s or more)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="grf1024", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -221,6 +278,9 @@ def main():
                     help="side length override of a single-image workload (same recipe; profiling on smaller cases)")
     args = ap.parse_args()
     W = WORKLOADS[args.workload]
+    if args.steps is None:
+        # the oracle arm times seconds-long CPU samples: a handful of steps
+        args.steps = 5 if args.impl == "reference" else W["steps"]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -297,18 +357,35 @@ def main():
             g = cr.cr_backward_batched(flat, shapes, offs, bp, -2 * life, 2 * life)
             return g
 
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
 
-    # -------- timed region (device-resident input) --------
+    # -------- stage breakdown (separate pass: its events would perturb the timing) --------
+    prof_steps = max(2, min(args.steps, 5))
+    L.cr_profile_select(0xFFFFFFFF)
     L.cr_profile_reset()
     L.cr_profile_enable(1)
-    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    for _ in range(prof_steps):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize(dev)
+    L.cr_profile_enable(0)
+    stages = read_profile(cr)
+    roof_stage = dominant_stage(stages)
+
+    # -------- timed region (device-resident input) --------
+    # only the dominant kernel's launches are bracketed by events, for the roofline
+    L.cr_profile_reset()
+    if roof_stage is not None:
+        L.cr_profile_select(1 << stage_index(cr, roof_stage))
+        L.cr_profile_enable(1)
     launches0 = int(L.cr_launch_count())
     step_ms = []
     barrier()
-    clocks.start()
+    t_region0 = time.time()
     for _ in range(args.steps):
         flush.fill_(1)
         torch.cuda.synchronize(dev)
@@ -320,10 +397,12 @@ def main():
         b.synchronize()
         step_ms.append(a.elapsed_time(b))
     barrier()
-    clk = clocks.stop()
+    t_region1 = time.time()
+    clk = clocks.stop((t_region0, t_region1))
     L.cr_profile_enable(0)
+    L.cr_profile_select(0xFFFFFFFF)
     launches = int(L.cr_launch_count()) - launches0
-    stages = read_profile(cr)
+    timed_stages = read_profile(cr)
     total_ms = sum(step_ms)
     if world > 1:
         import torch.distributed as dist
@@ -398,7 +477,7 @@ def main():
                  "batched_over_plain": value / (sub / (pms / 1e3))}
 
     peaks = load_peaks()
-    roof = roofline_from(stages, peaks)
+    roof = roofline_from({roof_stage: timed_stages[roof_stage]} if roof_stage in timed_stages else stages, peaks)
 
     line = {"metric": metric, "value": value, "unit": metric.split()[0], "n_gpus": args.gpus * 0 + world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -414,8 +493,9 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
             "plain_path": plain,
-            "stages": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
-                       for k, v in stages.items()}}
+            "stages": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps}
+                       for k, v in stages.items()},
+            "stages_note": "separate profiled pass of %d steps (events around every stage)" % prof_steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, desc = run_oracle(args.workload, data)
         line["cpu_baseline"] = {"value": v, "unit": metric.split()[0], "cores": 1, "kind": "oracle",

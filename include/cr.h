@@ -192,9 +192,13 @@ int cr_persistence_noalloc(const float *img, int ndim, const int64_t *shape, int
  * bracketed by CUDA events recorded on the caller's stream; totals per stage
  * are read with cr_profile_read (stage 0..15; name, total milliseconds,
  * number of timed launches, algorithmic bytes the stage must move).  Returns
- * CR_ERR_INVALID_ARG past the last stage.  cr_launch_count is the number of
- * kernels the library has launched since it was loaded.  Host-only. */
+ * CR_ERR_INVALID_ARG past the last stage.  cr_profile_select restricts the
+ * events to the stages whose bit is set in stage_mask (bit s = stage s;
+ * default all), so that one kernel can be timed inside an otherwise
+ * unobserved run.  cr_launch_count is the number of kernels the library has
+ * launched since it was loaded.  Host-only. */
 int cr_profile_enable(int on);
+int cr_profile_select(uint32_t stage_mask);
 void cr_profile_reset(void);
 int cr_profile_read(int stage, const char **name, double *total_ms, int64_t *count, double *bytes);
 int64_t cr_launch_count(void);

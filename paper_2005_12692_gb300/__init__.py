@@ -85,6 +85,8 @@ def lib() -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_int), i64p, i64p, i64p]
         L.cr_profile_enable.argtypes = [ctypes.c_int]
         L.cr_profile_enable.restype = ctypes.c_int
+        L.cr_profile_select.argtypes = [ctypes.c_uint32]
+        L.cr_profile_select.restype = ctypes.c_int
         L.cr_profile_reset.argtypes = []
         L.cr_profile_reset.restype = None
         L.cr_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),

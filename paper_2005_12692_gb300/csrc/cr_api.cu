@@ -130,7 +130,12 @@ static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
     if (worst) {
         uf = al((size_t)nodes * 45) + al((size_t)(3 * P.vtot) * 32) + (1 << 20);
     } else {
-        uf = al((size_t)nodes * 16) + al((size_t)P.vtot * 48) + (8 << 20);
+        // the dual graph of a volume keeps most of its 3 faces per voxel as
+        // cross edges (its first groups are small: the cubes around one
+        // maximal vertex), so volumes get room for ~2.5 edges per voxel
+        int edim = 1;
+        for (const Seg &S : P.segs) edim = S.edim > edim ? S.edim : edim;
+        uf = al((size_t)nodes * 16) + al((size_t)P.vtot * (edim == 3 && P.any_dual ? 96 : 48)) + (8 << 20);
     }
     if (P.any_mid) {
         int64_t nw;

@@ -23,6 +23,7 @@ struct Pending {
 
 static std::mutex g_mu;
 static bool g_on = false;
+static uint32_t g_mask = 0xFFFFFFFFu;  // stages that record events
 static std::vector<cudaEvent_t> g_pool;
 static std::vector<Pending> g_pending;
 static std::vector<Pending> g_open;  // begun, not ended
@@ -42,7 +43,7 @@ static cudaEvent_t take_event() {
 }
 
 void prof_begin(cudaStream_t st, int stage) {
-    if (!g_on) return;
+    if (!g_on || !((g_mask >> stage) & 1u)) return;
     std::lock_guard<std::mutex> lk(g_mu);
     Pending p{stage, take_event(), nullptr, 0.0};
     cudaEventRecord(p.a, st);
@@ -50,7 +51,7 @@ void prof_begin(cudaStream_t st, int stage) {
 }
 
 void prof_end(cudaStream_t st, int stage, double bytes) {
-    if (!g_on) return;
+    if (!g_on || !((g_mask >> stage) & 1u)) return;
     std::lock_guard<std::mutex> lk(g_mu);
     for (size_t i = g_open.size(); i-- > 0;) {
         if (g_open[i].stage == stage) {
@@ -67,7 +68,7 @@ void prof_end(cudaStream_t st, int stage, double bytes) {
 
 // bytes known only after the stream reached this point (device counters)
 void prof_add_bytes(int stage, double bytes) {
-    if (!g_on) return;
+    if (!g_on || !((g_mask >> stage) & 1u)) return;
     std::lock_guard<std::mutex> lk(g_mu);
     g_bytes[stage] += bytes;
 }
@@ -95,6 +96,12 @@ extern "C" {
 int cr_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(cr::g_mu);
     cr::g_on = on != 0;
+    return CR_OK;
+}
+
+int cr_profile_select(uint32_t stage_mask) {
+    std::lock_guard<std::mutex> lk(cr::g_mu);
+    cr::g_mask = stage_mask;
     return CR_OK;
 }
 
