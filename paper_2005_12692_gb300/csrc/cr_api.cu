@@ -113,7 +113,7 @@ static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 static size_t fixed_bytes(const HostPlan &P) {
     size_t b = 0;
     b += al(P.segs.size() * sizeof(Seg));
-    b += al(64 * sizeof(unsigned long long));  // status + counters
+    b += al(CR_CNT_SLOTS * sizeof(unsigned long long));  // status + counters
     int64_t nodes = P.vtot > P.ctot ? P.vtot : P.ctot;
     b += al((size_t)nodes * sizeof(uint32_t));  // labels
     b += al((size_t)P.vtot);                    // primal hooks
@@ -274,7 +274,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     if (!ws || ws_bytes < need_min) { g_detail = SITE_FIXED; return CR_ERR_WORKSPACE; }
     Carver C(ws, ws_bytes);
     Seg *segs = C.take<Seg>(n);
-    unsigned long long *cnt = C.take<unsigned long long>(64);
+    unsigned long long *cnt = C.take<unsigned long long>(CR_CNT_SLOTS);
     int64_t nodes = P.vtot > P.ctot ? P.vtot : P.ctot;
     uint32_t *lab = C.take<uint32_t>(nodes);
     uint8_t *dd = C.take<uint8_t>(P.vtot);
@@ -288,7 +288,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     unsigned long long *pair_count = &cnt[1];
 
     cudaMemcpyAsync(segs, P.segs.data(), n * sizeof(Seg), cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(cnt, 0, 64 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(cnt, 0, CR_CNT_SLOTS * sizeof(unsigned long long), st);
     if (P.any_mid) cudaMemsetAsync(extra, 0, (size_t)mask_words * 4, st);
 
     PairBuf pb;
@@ -305,7 +305,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         UF u;
         u.lab = lab;
         u.dd = dd;
-        u.cnt = &cnt[8];
+        u.cnt = &cnt[CNT_H0];
         u.hcnt = hc;
         // groups: the number of roots is not known yet; give the union-find a
         // share of the region proportional to the node count and the rest to edges
@@ -351,7 +351,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         B.P = R.take<int>(B.P_len);
         B.appmask = R.take<uint32_t>((3 * P.vtot + 31) / 32);
         B.scratch = R.take<uint64_t>((size_t)nw * 2 * ml);
-        B.cnt = &cnt[16];
+        B.cnt = &cnt[CNT_H1];
         if (!R.ok) return CR_ERR_WORKSPACE;
         size_t left = R.cap - R.used;
         // columns (32 B each + sort temp) get up to half of what is left, the arena the rest
@@ -387,7 +387,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         UF u;
         u.lab = lab;
         u.dd = ddc;
-        u.cnt = &cnt[48];
+        u.cnt = &cnt[CNT_DUAL];
         u.hcnt = hc;
         int64_t max_groups = P.ctot;
         size_t gbytes = (size_t)max_groups * 45 + 8 * 256;
@@ -413,14 +413,14 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         }
         u.max_edges = max_edges;
         if (!R.ok) return CR_ERR_WORKSPACE;
-        rc = run_dual(imgs, segs, n, P.vtot, P.ctot, P.ntiles, u, pb, flags, status, st);
+        rc = run_dual(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, u, pb, flags, status, st);
         if (rc) return rc;
     }
 
     // ---- count, status ----
     int hstatus[16] = {0};
-    unsigned long long ufc[64];
-    cudaMemcpyAsync(ufc, cnt, 64 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    unsigned long long ufc[CR_CNT_SLOTS];
+    cudaMemcpyAsync(ufc, cnt, CR_CNT_SLOTS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hc, pair_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hstatus, status, 16 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
@@ -432,7 +432,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     // 104 B (phase B: the edge, both ends' min edge and age key; phase D: the
     // edge, both ends' root, the kept edge and both min-edge updates), per
     // group and round 12 B (min-edge reset, hook read); counters of both runs
-    for (int base : {8, 48}) {
+    for (int base : {CNT_H0, CNT_DUAL}) {
         double e = (double)ufc[base + 3], r = (double)ufc[base + 6], g = (double)ufc[base + 0];
         prof_add_bytes(STAGE_UF_ROUND, 104.0 * e + 12.0 * g * r);
     }

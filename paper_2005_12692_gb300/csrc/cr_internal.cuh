@@ -104,35 +104,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, long long limit) {
 }
 
 
-// wait on the given phase parity of an mbarrier, at most `limit` polls
-__device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity, long long limit) {
-    uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < limit; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void mbar_init1(uint64_t *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// arm the barrier for one box and issue the copy (one thread)
-__device__ __forceinline__ void tma_issue_box(const void *tmap, float *dst, uint64_t *bar, int x0, int y0, int z0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(TMA_BYTES)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"(tmap), "r"(x0 - 4), "r"(y0 - 1), "r"(z0 - 1), "r"(smem_u32(bar))
-        : "memory");
-}
 // origin of tile t of a single image
 __device__ __forceinline__ void tile_origin(const Seg &S, uint32_t t, int &x0, int &y0, int &z0) {
     const uint32_t tix = t % (uint32_t)S.tiles_x;
@@ -143,20 +114,31 @@ __device__ __forceinline__ void tile_origin(const Seg &S, uint32_t t, int &x0, i
     y0 = (int)tiy * TILE_Y;
     z0 = (int)tiz * TILE_Z;
 }
-constexpr long long TMA_WAIT = 1ll << 24;
+
+// One thread: initialise the mbarrier, arm it for `bytes` and issue the 3D
+// tensor copy of the box whose first element is (cx, cy, cz).  cx * 4 bytes
+// must be a multiple of 16; outside the tensor the box is zero-filled.
+__device__ __forceinline__ void tma_load_3d(const void *tmap, void *dst, uint64_t *bar, uint32_t bytes, int cx, int cy,
+                                            int cz) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(tmap), "r"(cx), "r"(cy), "r"(cz), "r"(smem_u32(bar))
+        : "memory");
+}
 
 // TMA copy of the box around a tile: x starts 4 voxels early (16-byte
 // boundary), y and z one voxel early; issued by one thread, completion on bar
 __device__ __forceinline__ void tma_load_box(const void *tmap, float *dst, uint64_t *bar, int x0, int y0, int z0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(TMA_BYTES)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"(tmap), "r"(x0 - 4), "r"(y0 - 1), "r"(z0 - 1), "r"(smem_u32(bar))
-        : "memory");
+    tma_load_3d(tmap, dst, bar, TMA_BYTES, x0 - 4, y0 - 1, z0 - 1);
 }
+
+// box of the dual stencil: a cube and its neighbours across each facet reach
+// two voxels past the tile in +y and +z
+constexpr int DUAL_BX = TILE_X + 8, DUAL_BY = TILE_Y + 3, DUAL_BZ3 = TILE_Z + 3;
 
 // Tile-grid launches (grid = tiles, block = TILE_X*TILE_Y threads): the
 // block's image, looked up once, and this thread's column of the tile.
@@ -273,6 +255,17 @@ __device__ __forceinline__ void emit_pair(const PairBuf &pb, uint32_t seg, int d
     }
 }
 
+// device counter block: status words and pair count in slots 0..7, the middle
+// dimension's counters at 16.., each union-find run's UF_CNT counters at
+// CNT_H0 / CNT_DUAL
+constexpr int CR_CNT_SLOTS = 128, CNT_H1 = 16, CNT_H0 = 64, CNT_DUAL = 96, UF_CNT = 16;
+// slots of a union-find run: 0 groups, 1-2 edges in the two edge buffers,
+// 3 edges visited by the rounds, 4 barrier of the rounds, 5 barrier of the
+// basin kernel, 6 rounds, 7 live edges (in-place list), 8-10 pointers changed
+// per doubling pass, 11 doubling passes
+enum UfSlot { UFC_GROUPS = 0, UFC_E0 = 1, UFC_E1 = 2, UFC_VISITED = 3, UFC_BAR_ROUNDS = 4, UFC_BAR_BASINS = 5,
+              UFC_ROUNDS = 6, UFC_LIVE = 7, UFC_CHANGED = 8, UFC_PASSES = 11 };
+
 // union-find buffers (cr_uf.cu)
 struct UF {
     uint32_t *lab;   // node -> parent, then node -> group
@@ -291,7 +284,8 @@ struct UF {
 };
 int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ntiles, UF &u,
            const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status, cudaStream_t st);
-int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, int64_t ntiles, UF &u,
+int run_dual(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ctot,
+             int64_t ntiles, UF &u,
              const PairBuf &pb, uint32_t flags, int *status, cudaStream_t st);
 
 // middle-dimension buffers (cr_h1.cu)
@@ -316,7 +310,8 @@ struct H1Bufs {
 };
 int h1_stats(int64_t *out, int n);
 // tensor map over one image as an (nx, ny, nz) float32 tensor with the tile box; false if TMA cannot serve it
-bool make_image_map(CUtensorMap *m, const float *img, const Seg &S);
+bool make_image_map(CUtensorMap *m, const float *img, const Seg &S, int bx = TMA_BX, int by = TMA_BY,
+                    int bz = TMA_BZ);
 int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, const Seg *hseg, int nseg,
            int64_t vtot, int64_t ntiles, H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status,
            int64_t *ncols_out, cudaStream_t st);

@@ -168,47 +168,35 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tiled(const float
         if (inxy) {
             const uint32_t lv = zoff + (uint32_t)y * nx + x;
             const uint32_t ov = cur;
-            const uint64_t kv = make_key(ov, lv);
-            uint64_t best = ~0ull;
-            int bestdir = 0;
-            uint32_t bestou = 0, bestlu = 0;
-            // neighbours: -x, +x, -y, +y, -z, +z
-#pragma unroll
-            for (int d = 0; d < 6; d++) {
-                int ax = d >> 1;
-                bool pos = d & 1;
-                bool ok;
-                uint32_t ou, lu, la;
-                if (ax == 0) {
-                    ok = pos ? x + 1 < nx : x > 0;
-                    ou = pl[threadIdx.y + 1][threadIdx.x + (pos ? 2 : 0)];
-                    lu = pos ? lv + 1 : lv - 1;
-                    la = pos ? lv : lv - 1;
-                } else if (ax == 1) {
-                    ok = pos ? y + 1 < ny : y > 0;
-                    ou = pl[threadIdx.y + (pos ? 2 : 0)][threadIdx.x + 1];
-                    lu = pos ? lv + nx : lv - nx;
-                    la = (pos ? lv : lv - nx) + plane * (uint32_t)nz;
-                } else {
-                    ok = pos ? z + 1 < nz : z > 0;
-                    ou = pos ? above : below;
-                    lu = pos ? lv + plane : lv - plane;
-                    la = (pos ? lv : lv - plane) + 2u * plane * (uint32_t)nz;
-                }
-                if (!ok) continue;
-                uint64_t ek = make_key(ov > ou ? ov : ou, la);
-                if (ek < best) {
-                    best = ek;
-                    bestdir = d + 1;
-                    bestou = ou;
-                    bestlu = lu;
-                }
+            // the first neighbour with ord <= ord(v) in descending edge-L
+            // order (+z, -z, +y, -y, +x, -x) gives the minimum edge
+            int dir = 0;
+            uint32_t ou = 0;
+#define CR_NB(OK, VAL, DIR)                 \
+            {                               \
+                const uint32_t o_ = (VAL);  \
+                if ((OK) && o_ <= ov) {     \
+                    dir = (DIR);            \
+                    ou = o_;                \
+                }                           \
             }
+            CR_NB(x > 0, pl[threadIdx.y + 1][threadIdx.x], 1)
+            CR_NB(x + 1 < nx, pl[threadIdx.y + 1][threadIdx.x + 2], 2)
+            CR_NB(y > 0, pl[threadIdx.y][threadIdx.x + 1], 3)
+            CR_NB(y + 1 < ny, pl[threadIdx.y + 2][threadIdx.x + 1], 4)
+            CR_NB(z > 0, below, 5)
+            CR_NB(z + 1 < nz, above, 6)
+#undef CR_NB
             const int64_t gv = S.voff + lv;
-            if (bestdir && make_key(bestou, bestlu) < kv) {
-                parent[gv] = (uint32_t)(S.voff + bestlu);
-                dd[gv] = (uint8_t)bestdir;
-                if (flags & CR_KEEP_ZERO) emit_pair(pb, (uint32_t)si, 0, unord32(ov), key_value(best), lv, key_L(best), 0);
+            if (dir && (ou < ov || !(dir & 1))) {
+                const uint32_t st = dir <= 2 ? 1u : (dir <= 4 ? (uint32_t)nx : plane);
+                const uint32_t lu = (dir & 1) ? lv - st : lv + st;
+                parent[gv] = (uint32_t)(S.voff + lu);
+                dd[gv] = (uint8_t)dir;
+                if (flags & CR_KEEP_ZERO) {
+                    const uint32_t la = ((dir & 1) ? lu : lv) + (uint32_t)((dir - 1) >> 1) * plane * (uint32_t)nz;
+                    emit_pair(pb, (uint32_t)si, 0, unord32(ov), unord32(ov), lv, la, 0);
+                }
             } else {
                 parent[gv] = (uint32_t)gv;
                 dd[gv] = 0;
@@ -274,34 +262,40 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tma(const __grid_
         const int z = z0 + zz, bz = zz + 1;
         const float fv = box[bz][by][bx];
         nan_seen |= isnan(fv);
-        const uint32_t ov = ord32(fv);
         const uint32_t lv = (uint32_t)z * plane + (uint32_t)y * nx + x;
-        // edges in descending L: +z, -z, +y, -y, +x, -x; a strictly smaller
-        // value wins, so among equal values the larger L (the earlier edge) stays
-        uint32_t bval = 0xFFFFFFFFu, bou = 0, blu = 0, bL = 0;
-        int bdir = 0;
-#define CR_EDGE(OK, UF, LU, LA, DIR)                           \
-        if (OK) {                                              \
-            const uint32_t ou_ = ord32(UF);                    \
-            const uint32_t ev_ = ov > ou_ ? ov : ou_;          \
-            if (bdir == 0 || ev_ < bval) {                     \
-                bval = ev_; bou = ou_; blu = (LU); bL = (LA); bdir = (DIR); \
-            }                                                  \
+        // Every edge to a neighbour u with phi(u) <= phi(v) has value phi(v),
+        // and any other edge is larger, so the minimum edge is the first such
+        // neighbour in descending edge-L order (+z, -z, +y, -y, +x, -x).
+        // Float comparisons order like ord32 here (-0 == +0; NaN is flagged).
+        int dir = 0;
+        float fu = 0.f;
+#define CR_NB(OK, VAL, DIR)                  \
+        {                                    \
+            const float f_ = (VAL);          \
+            if ((OK) && f_ <= fv) {          \
+                dir = (DIR);                 \
+                fu = f_;                     \
+            }                                \
         }
-        CR_EDGE(z + 1 < nz, box[bz + 1][by][bx], lv + plane, lv + 2u * P, 6)
-        CR_EDGE(z > 0, box[bz - 1][by][bx], lv - plane, lv - plane + 2u * P, 5)
-        CR_EDGE(y + 1 < ny, box[bz][by + 1][bx], lv + nx, lv + P, 4)
-        CR_EDGE(y > 0, box[bz][by - 1][bx], lv - nx, lv - nx + P, 3)
-        CR_EDGE(x + 1 < nx, box[bz][by][bx + 1], lv + 1, lv, 2)
-        CR_EDGE(x > 0, box[bz][by][bx - 1], lv - 1, lv - 1, 1)
-#undef CR_EDGE
-        // the neighbour is older iff (value, -L) is smaller
-        const bool older = bdir && (bou < ov || (bou == ov && blu > lv));
-        if (older) {
-            parent[lv] = blu;
-            dd[lv] = (uint8_t)bdir;
-            if (flags & CR_KEEP_ZERO)
-                emit_pair(pb, 0u, 0, unord32(ov), unord32(bval), lv, bL, 0);
+        CR_NB(x > 0, box[bz][by][bx - 1], 1)
+        CR_NB(x + 1 < nx, box[bz][by][bx + 1], 2)
+        CR_NB(y > 0, box[bz][by - 1][bx], 3)
+        CR_NB(y + 1 < ny, box[bz][by + 1][bx], 4)
+        CR_NB(z > 0, box[bz - 1][by][bx], 5)
+        CR_NB(z + 1 < nz, box[bz + 1][by][bx], 6)
+#undef CR_NB
+        // the neighbour is older iff its value is smaller, or equal with a
+        // larger L (a neighbour in the + direction)
+        if (dir && (fu < fv || !(dir & 1))) {
+            const uint32_t st = dir <= 2 ? 1u : (dir <= 4 ? (uint32_t)nx : plane);
+            const uint32_t lu = (dir & 1) ? lv - st : lv + st;
+            parent[lv] = lu;
+            dd[lv] = (uint8_t)dir;
+            if (flags & CR_KEEP_ZERO) {
+                const uint32_t la = ((dir & 1) ? lu : lv) + (uint32_t)((dir - 1) >> 1) * P;
+                const float cv = unord32(ord32(fv));
+                emit_pair(pb, 0u, 0, cv, cv, lv, la, 0);
+            }
         } else {
             parent[lv] = lv;
             dd[lv] = 0;
@@ -326,13 +320,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // a tensor map over one image as an (nx, ny, nz) float32 tensor; false if TMA cannot serve it
-bool make_image_map(CUtensorMap *m, const float *img, const Seg &S) {
+bool make_image_map(CUtensorMap *m, const float *img, const Seg &S, int bx, int by, int bz) {
     if (((uintptr_t)img & 15) || (S.nx % 4) != 0) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)S.nx, (cuuint64_t)S.ny, (cuuint64_t)S.nz};
     cuuint64_t strides[2] = {(cuuint64_t)S.nx * 4, (cuuint64_t)S.nx * S.ny * 4};
-    cuuint32_t box[3] = {(cuuint32_t)TMA_BX, (cuuint32_t)TMA_BY, (cuuint32_t)TMA_BZ};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)img, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -589,6 +583,138 @@ __global__ void k_dual_stencil(const float *__restrict__ img, const Seg *__restr
     }
 }
 
+// ---------------------------------------------------------------------------
+// The dual stencil fed by TMA (single 2D/3D images whose rows are 16-byte
+// multiples).  The block's cubes, their vertices and the far vertices of every
+// neighbour cube sit in one box (x from 4 voxels early, y and z from one
+// voxel early, two past the tile in +y and +z).
+// In the reversed order a cube's minimum dual edge is its facet with the
+// largest key: the facets holding a vertex of the cube's value phi(c) all
+// have value phi(c), the others less, and among those the smallest L wins,
+// which is the first in the order -z, +z, -y, +y, -x, +x (2D: -y, +y, -x, +x).
+// The neighbour across it shares that facet, so its value is at least phi(c):
+// it is older if larger, or equal and on the - side (smaller L).
+// ---------------------------------------------------------------------------
+template <int EDIM>
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_dual_stencil_tma(const __grid_constant__ CUtensorMap tmap,
+                                                                    const Seg *__restrict__ segs,
+                                                                    uint32_t *__restrict__ parent,
+                                                                    uint8_t *__restrict__ dd, int *status,
+                                                                    PairBuf pb, uint32_t flags) {
+    constexpr int BZ = EDIM == 3 ? DUAL_BZ3 : 1;
+    constexpr uint32_t BOX_BYTES = (uint32_t)BZ * DUAL_BY * DUAL_BX * 4;
+    __shared__ __align__(128) float box[BZ][DUAL_BY][DUAL_BX];
+    __shared__ __align__(8) uint64_t bar;
+    const Seg S = segs[0];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    int x0, y0, z0;
+    tile_origin(S, blockIdx.x, x0, y0, z0);
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    if (leader) {
+        if (blockIdx.x == 0) {  // the outer node
+            parent[S.coff + S.ncell] = (uint32_t)(S.coff + S.ncell);
+            dd[S.coff + S.ncell] = 0;
+        }
+        tma_load_3d(&tmap, &box[0][0][0], &bar, BOX_BYTES, x0 - 4, y0 - 1, EDIM == 3 ? z0 - 1 : 0);
+    }
+    __syncthreads();
+    if (!mbar_wait(&bar, 1ll << 24)) {
+        set_status(status, CR_ERR_TIMEOUT);
+        mbar_wait(&bar, 1ll << 24);
+        return;
+    }
+    const int cx = nx - 1, cy = ny - 1, cz = EDIM == 3 ? nz - 1 : 1;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= cx || y >= cy) return;
+    const int bx = threadIdx.x + 4, by = threadIdx.y + 1;
+    const int zend = EDIM == 3 ? min(TILE_Z, cz - z0) : 1;
+    const uint32_t outer = (uint32_t)(S.coff + S.ncell);
+    bool nan_seen = false;
+    for (int zz = 0; zz < zend; zz++) {
+        const int z = z0 + zz, bz = EDIM == 3 ? zz + 1 : 0;
+        const uint32_t c = ((uint32_t)z * (uint32_t)cy + (uint32_t)y) * (uint32_t)cx + (uint32_t)x;
+        float fc;
+        int f;
+        if (EDIM == 3) {
+            const float v000 = box[bz][by][bx], v001 = box[bz][by][bx + 1];
+            const float v010 = box[bz][by + 1][bx], v011 = box[bz][by + 1][bx + 1];
+            const float v100 = box[bz + 1][by][bx], v101 = box[bz + 1][by][bx + 1];
+            const float v110 = box[bz + 1][by + 1][bx], v111 = box[bz + 1][by + 1][bx + 1];
+            const float sum = ((v000 + v001) + (v010 + v011)) + ((v100 + v101) + (v110 + v111));
+            if (sum != sum)  // a NaN, or infinities of both signs
+                nan_seen |= v000 != v000 || v001 != v001 || v010 != v010 || v011 != v011 || v100 != v100 ||
+                            v101 != v101 || v110 != v110 || v111 != v111;
+            const float zlo = fmaxf(fmaxf(v000, v001), fmaxf(v010, v011));
+            const float zhi = fmaxf(fmaxf(v100, v101), fmaxf(v110, v111));
+            const float ylo = fmaxf(fmaxf(v000, v001), fmaxf(v100, v101));
+            const float yhi = fmaxf(fmaxf(v010, v011), fmaxf(v110, v111));
+            const float xlo = fmaxf(fmaxf(v000, v010), fmaxf(v100, v110));
+            fc = fmaxf(zlo, zhi);
+            f = zlo == fc ? 0 : zhi == fc ? 1 : ylo == fc ? 2 : yhi == fc ? 3 : xlo == fc ? 4 : 5;
+        } else {
+            const float v00 = box[0][by][bx], v01 = box[0][by][bx + 1];
+            const float v10 = box[0][by + 1][bx], v11 = box[0][by + 1][bx + 1];
+            const float sum = (v00 + v01) + (v10 + v11);
+            if (sum != sum) nan_seen |= v00 != v00 || v01 != v01 || v10 != v10 || v11 != v11;
+            const float ylo = fmaxf(v00, v01), yhi = fmaxf(v10, v11), xlo = fmaxf(v00, v10);
+            fc = fmaxf(ylo, yhi);
+            f = ylo == fc ? 0 : yhi == fc ? 1 : xlo == fc ? 2 : 3;
+        }
+        // the neighbour across facet f: outside the image (the outer node), or
+        // the cube whose far vertices lie one step further
+        const int axis = EDIM == 3 ? 2 - (f >> 1) : 1 - (f >> 1);  // 0 x, 1 y, 2 z
+        const bool up = f & 1;
+        const int coord = axis == 0 ? x : (axis == 1 ? y : z);
+        const int ext = axis == 0 ? cx : (axis == 1 ? cy : cz);
+        const bool outside = up ? coord + 1 >= ext : coord == 0;
+        bool hook = true;
+        uint32_t other = outer;
+        if (!outside) {
+            float fo;
+            if (axis == 0) {
+                const int xx = up ? bx + 2 : bx - 1;
+                fo = fmaxf(box[bz][by][xx], box[bz][by + 1][xx]);
+                if (EDIM == 3) fo = fmaxf(fo, fmaxf(box[bz + 1][by][xx], box[bz + 1][by + 1][xx]));
+                other = up ? c + 1 : c - 1;
+            } else if (axis == 1) {
+                const int yy = up ? by + 2 : by - 1;
+                fo = fmaxf(box[bz][yy][bx], box[bz][yy][bx + 1]);
+                if (EDIM == 3) fo = fmaxf(fo, fmaxf(box[bz + 1][yy][bx], box[bz + 1][yy][bx + 1]));
+                other = up ? c + (uint32_t)cx : c - (uint32_t)cx;
+            } else {
+                const int zb = up ? bz + 2 : bz - 1;
+                fo = fmaxf(fmaxf(box[zb][by][bx], box[zb][by][bx + 1]),
+                           fmaxf(box[zb][by + 1][bx], box[zb][by + 1][bx + 1]));
+                const uint32_t pl = (uint32_t)cx * (uint32_t)cy;
+                other = up ? c + pl : c - pl;
+            }
+            hook = fo > fc || (fo == fc && !up);
+            other += (uint32_t)S.coff;
+        }
+        const uint32_t gc = (uint32_t)S.coff + c;
+        if (hook) {
+            parent[gc] = other;
+            dd[gc] = (uint8_t)(f + 1);
+            if (flags & CR_KEEP_ZERO) {
+                uint32_t fl;
+                if (EDIM == 3) {
+                    const int m = 2 - axis;  // face type: 0 normal z, 1 normal y, 2 normal x
+                    fl = cube_L(S, m, x + (axis == 0 && up), y + (axis == 1 && up), z + (axis == 2 && up));
+                } else {
+                    const int m = 1 - axis;  // 0 x-edge (normal y), 1 y-edge (normal x)
+                    fl = cube_L(S, m, x + (axis == 0 && up), y + (axis == 1 && up), 0);
+                }
+                const float cv = unord32(ord32(fc));
+                emit_pair(pb, 0u, EDIM - 1, cv, cv, fl, cube_L(S, 0, x, y, z), 0);
+            }
+        } else {
+            parent[gc] = gc;
+            dd[gc] = 0;
+        }
+    }
+    if (nan_seen) set_status(status, CR_ERR_NAN);
+}
+
 __global__ void k_dual_roots(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t ctot,
                              uint32_t *__restrict__ lab, unsigned long long *ngroups, int64_t max_groups,
                              uint64_t *__restrict__ gkey, uint32_t *__restrict__ groot, uint32_t *__restrict__ gseg,
@@ -752,6 +878,114 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int &
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Basins in one cooperative launch (one 1024-thread block per SM):
+//   passes of in-place pointer doubling until a pass changes nothing (every
+//   write stores an ancestor, and a pass without writes saw every node
+//   pointing at a root);
+//   roots take group ids (primal: age key of the root vertex; dual: reversed
+//   key of the root cube, the outer node oldest);
+//   every node's label becomes its root's group id.
+// ---------------------------------------------------------------------------
+constexpr int BASIN_THREADS = 1024;
+struct BasinArgs {
+    const float *img;
+    const Seg *segs;
+    int nseg;
+    int mode;  // 0 primal vertices, 1 dual nodes (top cubes + outer nodes)
+    int64_t n;
+    uint32_t *lab;
+    unsigned long long *cnt;  // the run's counter slots
+    int64_t max_groups;
+    uint64_t *gkey;
+    uint32_t *groot, *gseg;
+    int *status;
+};
+
+__global__ void __launch_bounds__(BASIN_THREADS, 1) k_basins(BasinArgs A) {
+    if (*(volatile int *)A.status) return;
+    unsigned int *bar = (unsigned int *)&A.cnt[UFC_BAR_BASINS];
+    unsigned int target = 0;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n = A.n;
+    uint32_t *lab = A.lab;
+    for (int pass = 0; pass < 64; pass++) {
+        unsigned long long *changed = &A.cnt[UFC_CHANGED + pass % 3];
+        if (tid == 0) {
+            A.cnt[UFC_CHANGED + (pass + 1) % 3] = 0;  // last read two barriers ago
+            A.cnt[UFC_PASSES] += 1ull;
+        }
+        int ch = 0;
+        int64_t i = tid;
+        for (; i + 3 * nthr < n; i += 4 * nthr) {
+            uint32_t a[4], b[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) a[k] = __ldcg(lab + i + k * nthr);
+#pragma unroll
+            for (int k = 0; k < 4; k++) b[k] = __ldcg(lab + a[k]);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (b[k] != a[k]) {
+                    lab[i + k * nthr] = b[k];
+                    ch = 1;
+                }
+        }
+        for (; i < n; i += nthr) {
+            const uint32_t a = __ldcg(lab + i), b = __ldcg(lab + a);
+            if (b != a) {
+                lab[i] = b;
+                ch = 1;
+            }
+        }
+        if (__syncthreads_or(ch) && threadIdx.x == 0) atomicAdd(changed, 1ull);
+        if (!grid_barrier(bar, target, A.status)) return;
+        if (__ldcg(changed) == 0) break;
+        if (pass == 63) {
+            set_status(A.status, CR_ERR_INTERNAL);
+            return;
+        }
+    }
+    // roots
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += nthr) {
+        const int64_t v = base + threadIdx.x;
+        const bool isroot = v < n && __ldcg(lab + v) == (uint32_t)v;
+        const int64_t g = warp_append(isroot, &A.cnt[UFC_GROUPS]);
+        if (!isroot) continue;
+        if (g >= A.max_groups) {
+            fail_ws(A.status, SITE_GROUPS);
+            lab[v] = 0x80000000u;
+            continue;
+        }
+        uint64_t key;
+        int si;
+        if (A.mode == 0) {
+            si = seg_of(A.segs, A.nseg, v);
+            const int64_t lv = v - A.segs[si].voff;
+            key = make_key(ord32(A.img[v]), (uint32_t)lv);
+        } else {
+            si = seg_of_node(A.segs, A.nseg, v);
+            const Seg S = A.segs[si];
+            const int64_t c = v - S.coff;
+            key = 0;  // outer node: oldest
+            if (c < S.ncell) {
+                const CellPos p = cell_pos(S, c);
+                key = ~top_key(A.img, S, p.x, p.y, p.z);
+            }
+        }
+        A.gkey[g] = key;
+        A.groot[g] = (uint32_t)v;
+        A.gseg[g] = (uint32_t)si;
+        lab[v] = 0x80000000u | (uint32_t)g;
+    }
+    if (!grid_barrier(bar, target, A.status)) return;
+    // labels -> group ids (roots are marked; every other node points at a root)
+    for (int64_t i = tid; i < n; i += nthr) {
+        const uint32_t v = __ldcg(lab + i);
+        lab[i] = (v & 0x80000000u) ? (v & 0x7FFFFFFFu) : (__ldcg(lab + v) & 0x7FFFFFFFu);
+    }
 }
 
 constexpr int UF_THREADS = 1024;
@@ -1020,9 +1254,24 @@ static int rounds_coop(UF &u, int64_t work_estimate, const Seg *segs, int mode, 
     return e == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
+static int basins_coop(const float *img, const Seg *segs, int nseg, int mode, int64_t n, UF &u, int *status,
+                       cudaStream_t st) {
+    int64_t want = n / (8 * BASIN_THREADS) + 1;
+    int64_t maxb = sm_count();  // one block per SM keeps barriers short
+    int blocks = (int)(want < maxb ? want : maxb);
+    if (blocks < 1) blocks = 1;
+    BasinArgs A{img, segs, nseg, mode, n, u.lab, u.cnt, u.max_groups, u.gkey, u.groot, u.gseg, status};
+    void *args[] = {&A};
+    prof_begin(st, STAGE_JUMP);
+    CR_NOTE_LAUNCH();
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_basins, dim3(blocks), dim3(BASIN_THREADS), args, 0, st);
+    prof_end(st, STAGE_JUMP, 8.0 * (double)n);
+    return e == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+}
+
 int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ntiles, UF &u,
            const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status, cudaStream_t st) {
-    cudaMemsetAsync(u.cnt, 0, 8 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(u.cnt, 0, UF_CNT * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_H0_STENCIL);
     CR_NOTE_LAUNCH();
     CUtensorMap tmap;
@@ -1034,22 +1283,10 @@ int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
                                                                               pb, flags);
     }
     prof_end(st, STAGE_H0_STENCIL, 9.0 * vtot);
-    prof_begin(st, STAGE_JUMP);
-    CR_NOTE_LAUNCH();
-    for (int pass = 0; pass < 5; pass++) {
-        if (pass) CR_NOTE_LAUNCH();
-        k_double<<<nb(vtot), 256, 0, st>>>(u.lab, vtot);
+    {
+        int rc = basins_coop(img, segs, nseg, 0, vtot, u, status, st);
+        if (rc) return rc;
     }
-    CR_NOTE_LAUNCH();
-    k_find_root<<<nb(vtot), 256, 0, st>>>(u.lab, vtot, status);
-    prof_end(st, STAGE_JUMP, 8.0 * vtot);
-    CR_NOTE_LAUNCH();
-    k_h0_roots<<<nb(vtot), 256, 0, st>>>(img, segs, nseg, vtot, u.lab, &u.cnt[0], u.max_groups, u.gkey, u.groot,
-                                         u.gseg, status);
-    CR_NOTE_LAUNCH();
-    k_relabel<<<nb(vtot), 256, 0, st>>>(u.lab, vtot);
-    CR_NOTE_LAUNCH();
-    k_unmark<<<nb(vtot), 256, 0, st>>>(u.lab, vtot);
     prof_begin(st, STAGE_H0_CROSS);
     CR_NOTE_LAUNCH();
     k_h0_cross<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, u.ek[0], u.ea[0],
@@ -1062,29 +1299,30 @@ int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
-int run_dual(const float *img, const Seg *segs, int nseg, int64_t vtot, int64_t ctot, int64_t ntiles, UF &u,
+int run_dual(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ctot,
+             int64_t ntiles, UF &u,
              const PairBuf &pb, uint32_t flags, int *status, cudaStream_t st) {
-    cudaMemsetAsync(u.cnt, 0, 8 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(u.cnt, 0, UF_CNT * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_DUAL_STENCIL);
     CR_NOTE_LAUNCH();
-    k_dual_stencil<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, pb, flags);
-    prof_end(st, STAGE_DUAL_STENCIL, 4.0 * vtot + 5.0 * ctot);
-    prof_begin(st, STAGE_JUMP);
-    CR_NOTE_LAUNCH();
-    for (int pass = 0; pass < 5; pass++) {
-        if (pass) CR_NOTE_LAUNCH();
-        k_double<<<nb(ctot), 256, 0, st>>>(u.lab, ctot);
+    CUtensorMap tmap;
+    const int edim = hsegs[0].edim;
+    if (nseg == 1 && (edim == 2 || edim == 3) &&
+        make_image_map(&tmap, img, hsegs[0], DUAL_BX, DUAL_BY, edim == 3 ? DUAL_BZ3 : 1)) {
+        if (edim == 3)
+            k_dual_stencil_tma<3><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd, status,
+                                                                                   pb, flags);
+        else
+            k_dual_stencil_tma<2><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd, status,
+                                                                                   pb, flags);
+    } else {
+        k_dual_stencil<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, pb, flags);
     }
-    CR_NOTE_LAUNCH();
-    k_find_root<<<nb(ctot), 256, 0, st>>>(u.lab, ctot, status);
-    prof_end(st, STAGE_JUMP, 8.0 * ctot);
-    CR_NOTE_LAUNCH();
-    k_dual_roots<<<nb(ctot), 256, 0, st>>>(img, segs, nseg, ctot, u.lab, &u.cnt[0], u.max_groups, u.gkey, u.groot,
-                                           u.gseg, status);
-    CR_NOTE_LAUNCH();
-    k_relabel<<<nb(ctot), 256, 0, st>>>(u.lab, ctot);
-    CR_NOTE_LAUNCH();
-    k_unmark<<<nb(ctot), 256, 0, st>>>(u.lab, ctot);
+    prof_end(st, STAGE_DUAL_STENCIL, 4.0 * vtot + 5.0 * ctot);
+    {
+        int rc = basins_coop(img, segs, nseg, 1, ctot, u, status, st);
+        if (rc) return rc;
+    }
     prof_begin(st, STAGE_DUAL_CROSS);
     CR_NOTE_LAUNCH();
     k_dual_cross<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, u.ek[0], u.ea[0],
