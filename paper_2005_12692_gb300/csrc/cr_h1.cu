@@ -200,130 +200,255 @@ __global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, uint64
 }
 
 // ---------------------------------------------------------------------------
-// The scan fed by TMA (single volumes whose rows are 16-byte multiples): the
-// block's 32x8x16 tile plus halo is one cp.async.bulk.tensor box in shared
-// memory; every edge, face and key is computed from it with 32-bit values.
+// The scan fed by TMA (single volumes whose rows are 16-byte multiples).  A
+// block owns a 32x8x16 tile.  One mbarrier covers two tensor copies: the
+// tile's values with a halo (float box) and, when rows are 16-byte multiples
+// of bytes, the tile's stencil hook codes up to one voxel past the tile in +x,
+// +y, +z (byte box; otherwise the threads stage them).  Meanwhile the threads
+// stage the words of the dimension-0 death mask covering the tile's edges.
+// Apparent pivots are collected in a shared bitmask of the tile's faces and
+// merged into the global mask once per word at the end; residual columns are
+// buffered per tile and appended with one global reservation per run.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_constant__ CUtensorMap tmap, Img3 I,
-                                                               const Seg *__restrict__ segs,
+constexpr int SC_DX = 48, SC_DY = TILE_Y + 1, SC_DZ = TILE_Z + 1;  // hook-code box (x0..x0+47)
+constexpr int SC_DD_BYTES = SC_DX * SC_DY * SC_DZ;
+constexpr int SC_CAP = 1536;  // residual columns buffered per tile (at most 3 per voxel per plane)
+constexpr int SCAN_DYN_SMEM = TMA_BYTES + SC_DD_BYTES + 128;
+static_assert(TMA_BYTES % 128 == 0, "hook-code box must start on a 128-byte boundary");
+
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_constant__ CUtensorMap tmap,
+                                                               const __grid_constant__ CUtensorMap tmap_dd,
+                                                               int dd_by_tma, Img3 I, const Seg *__restrict__ segs,
                                                                uint64_t *__restrict__ colkey,
                                                                uint32_t *__restrict__ colseg,
                                                                unsigned long long *ncol, int64_t max_cols,
                                                                PairBuf pb, uint32_t flags, int *status) {
-    __shared__ __align__(128) float box[TMA_BZ][TMA_BY][TMA_BX];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    unsigned char *dyn = dyn_smem + ((128u - (smem_u32(dyn_smem) & 127u)) & 127u);
+    float(*box)[TMA_BY][TMA_BX] = reinterpret_cast<float(*)[TMA_BY][TMA_BX]>(dyn);
+    uint8_t(*dds)[SC_DY][SC_DX] = reinterpret_cast<uint8_t(*)[SC_DY][SC_DX]>(dyn + TMA_BYTES);
     __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t ext[3][TILE_Z][TILE_Y][2];          // death-mask words of each edge row
+    __shared__ uint32_t app[3][TILE_Z + 1][TILE_Y + 1][2];  // apparent pivots, face rows from y0-1, z0-1
+    __shared__ uint64_t cbuf[SC_CAP];                       // residual columns of the tile
+    __shared__ int cn;
+    __shared__ unsigned long long cbase;
     const Seg S = segs[0];
     const int nx = S.nx, ny = S.ny, nz = S.nz;
-    uint32_t t = blockIdx.x;
-    const int tix = (int)(t % (uint32_t)S.tiles_x);
-    t /= (uint32_t)S.tiles_x;
-    const int tiy = (int)(t % (uint32_t)S.tiles_y);
-    const int tiz = (int)(t / (uint32_t)S.tiles_y);
-    const int x0 = tix * TILE_X, y0 = tiy * TILE_Y, z0 = tiz * TILE_Z;
-    if (threadIdx.x == 0) tma_load_box(&tmap, &box[0][0][0], &bar, x0, y0, z0);
+    int x0, y0, z0;
+    tile_origin(S, blockIdx.x, x0, y0, z0);
+    const uint32_t plane = (uint32_t)nx * (uint32_t)ny, P = plane * (uint32_t)nz;
+    if (threadIdx.x == 0) {
+        const uint32_t b = smem_u32(&bar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const uint32_t bytes = (uint32_t)TMA_BYTES + (dd_by_tma ? (uint32_t)SC_DD_BYTES : 0u);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+            ::"r"(smem_u32(dyn)), "l"(&tmap), "r"(x0 - 4), "r"(y0 - 1), "r"(z0 - 1), "r"(b)
+            : "memory");
+        if (dd_by_tma)
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                ::"r"(smem_u32(dyn + TMA_BYTES)), "l"(&tmap_dd), "r"(x0), "r"(y0), "r"(z0), "r"(b)
+                : "memory");
+    }
+    if (!dd_by_tma) {
+        for (int i = threadIdx.x; i < SC_DZ * SC_DY * (TILE_X + 1); i += TILE_X * TILE_Y) {
+            const int dx = i % (TILE_X + 1), r = i / (TILE_X + 1);
+            const int dy = r % SC_DY, dz = r / SC_DY;
+            const int gx = x0 + dx, gy = y0 + dy, gz = z0 + dz;
+            uint8_t c = 0;
+            if (gx < nx && gy < ny && gz < nz) c = I.dd[S.voff + (int64_t)gz * plane + (int64_t)gy * nx + gx];
+            dds[dz][dy][dx] = c;
+        }
+    }
+    for (int i = threadIdx.x; i < 3 * TILE_Z * TILE_Y; i += TILE_X * TILE_Y) {
+        const int dy = i % TILE_Y, r = i / TILE_Y;
+        const int dz = r % TILE_Z, ax = r / TILE_Z;
+        const int gy = y0 + dy, gz = z0 + dz;
+        uint32_t w0 = 0, w1 = 0;
+        if (gy < ny && gz < nz) {
+            const int64_t bit = S.loff + (int64_t)ax * P + (int64_t)gz * plane + (int64_t)gy * nx + x0;
+            const int64_t last = (S.loff + (int64_t)3 * P + 31) >> 5;  // words of the mask
+            w0 = __ldg(I.extra + (bit >> 5));
+            if ((bit >> 5) + 1 < last) w1 = __ldg(I.extra + (bit >> 5) + 1);
+        }
+        ext[ax][dz][dy][0] = w0;
+        ext[ax][dz][dy][1] = w1;
+    }
+    for (int i = threadIdx.x; i < 3 * (TILE_Z + 1) * (TILE_Y + 1) * 2; i += TILE_X * TILE_Y)
+        (&app[0][0][0][0])[i] = 0u;
+    if (threadIdx.x == 0) cn = 0;
     __syncthreads();
     if (!mbar_wait(&bar, 1ll << 24)) {
         set_status(status, CR_ERR_TIMEOUT);
         mbar_wait(&bar, 1ll << 24);
         return;
     }
-    const int tx = threadIdx.x & (TILE_X - 1), ty = threadIdx.x / TILE_X;
+    const int tx = threadIdx.x & (TILE_X - 1), ty = threadIdx.x / TILE_X, lane = threadIdx.x & 31;
     const int x = x0 + tx, y = y0 + ty;
     const bool inxy = x < nx && y < ny;
-    const uint32_t plane = (uint32_t)nx * (uint32_t)ny, P = plane * (uint32_t)nz;
-    const int ext[3] = {nx, ny, nz};
     const int bx = tx + 4, by = ty + 1;
     const int zend = min(TILE_Z, nz - z0);
+    const bool keep_zero = (flags & CR_KEEP_ZERO) != 0;
+    const uint32_t lo = (uint32_t)S.loff;  // only its low bits matter for positions within mask words
+    const bool hx = x + 1 < nx, hy = y + 1 < ny, my = y > 0;
+    // Values of this thread's column roll through registers: f(x,y,z), f(x+1,y,z),
+    // f(x,y+1,z) and the x- and y-edge values of planes z-1, z (and z+1 once read).
+    // Out-of-image entries of the box are zero and never decide anything: each
+    // use is guarded by the existence of the cell it belongs to.
+    float fa = box[1][by][bx], fb = box[1][by][bx + 1], fc = box[1][by + 1][bx];
+    float exc = fmaxf(fa, fb), eyc = fmaxf(fa, fc);
+    float exp_ = fmaxf(box[0][by][bx], box[0][by][bx + 1]), eyp = fmaxf(box[0][by][bx], box[0][by + 1][bx]);
     for (int zz = 0; zz < zend; zz++) {
         const int z = z0 + zz, bz = zz + 1;
-        const int co[3] = {x, y, z};
-        const uint32_t lv = (uint32_t)z * plane + (uint32_t)y * nx + x;
-        const int64_t gv = S.voff + lv;
-        // ord value of the vertex at offset (dx, dy, dz) from this voxel
-        auto V = [&](int dx, int dy, int dz) -> uint32_t { return ord32(box[bz + dz][by + dy][bx + dx]); };
-        const uint32_t stride[3] = {1u, (uint32_t)nx, plane};
-        uint64_t keep0 = 0, keep1 = 0, keep2 = 0;
-        bool kf0 = false, kf1 = false, kf2 = false;
-        const uint8_t dv = inxy ? I.dd[gv] : 0;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            bool keep = false;
-            uint64_t sk = 0;
-            do {
-                if (!inxy || co[a] + 1 >= ext[a]) break;
-                // killed in dimension 0?
-                if (dv == (uint8_t)(2 * a + 2) || I.dd[gv + stride[a]] == (uint8_t)(2 * a + 1)) break;
-                const uint32_t sL = lv + (uint32_t)a * P;
-                if ((I.extra[(S.loff + sL) >> 5] >> ((S.loff + sL) & 31)) & 1u) break;
-                const int ax0 = a == 0, ay0 = a == 1, az0 = a == 2;
-                const uint32_t v0 = V(0, 0, 0), v1 = V(ax0, ay0, az0);
-                sk = make_key(v0 > v1 ? v0 : v1, sL);
-                // earliest cofacet: faces spanning {a, b}, anchored here or one step back in b
-                uint64_t tk = ~0ull;
-                int tb = 0, toff = 0;
-#pragma unroll
-                for (int b = 0; b < 3; b++) {
-                    if (b == a) continue;
-                    const int bx0 = b == 0, by0 = b == 1, bz0 = b == 2;
-                    const uint32_t ftype = (uint32_t)(a + b - 1);
-#pragma unroll
-                    for (int back = 0; back < 2; back++) {
-                        if (back == 0 ? co[b] + 1 >= ext[b] : co[b] < 1) continue;
-                        const int o = back ? -1 : 0;
-                        const int wx = o * bx0, wy = o * by0, wz = o * bz0;
-                        uint32_t m = V(wx, wy, wz), q;
-                        q = V(wx + ax0, wy + ay0, wz + az0);
-                        m = q > m ? q : m;
-                        q = V(wx + bx0, wy + by0, wz + bz0);
-                        m = q > m ? q : m;
-                        q = V(wx + ax0 + bx0, wy + ay0 + by0, wz + az0 + bz0);
-                        m = q > m ? q : m;
-                        const uint64_t fk = make_key(m, ftype * P + (back ? lv - stride[b] : lv));
-                        if (fk < tk) { tk = fk; tb = b; toff = o; }
+        const uint32_t rowL = (uint32_t)z * plane + (uint32_t)y * nx + (uint32_t)x0;  // L of (x0, y, z)
+        const uint32_t lv = rowL + (uint32_t)tx;
+        const bool hz = z + 1 < nz, mz = z > 0;
+        const float fa1 = box[bz + 1][by][bx], fb1 = box[bz + 1][by][bx + 1], fc1 = box[bz + 1][by + 1][bx];
+        const float exn = fmaxf(fa1, fb1), eyn = fmaxf(fa1, fc1);
+        float fsx = exc, fsy = eyc, fsz = fmaxf(fa, fa1);
+        bool colx = false, coly = false, colz = false;
+        int sx = 0, sy = 0;  // face of an apparent x- / y-edge (0: none)
+        if (inxy) {
+            const uint8_t dv = dds[zz][ty][tx];
+            // bit of this thread's x in a mask row whose first L-index is r0
+#define RB(r0) ((int)((lo + (r0)) & 31u) + tx)
+            // an edge killed in dimension 0 (a stencil hook or a later round's
+            // death) is not a column (and is never apparent, being paired with a vertex)
+#define KILLED(AX, DU)                                                         \
+            (dv == (uint8_t)(2 * (AX) + 2) || (DU) == (uint8_t)(2 * (AX) + 1) || \
+             ((ext[AX][zz][ty][RB((AX) * P + rowL) >> 5] >> (RB((AX) * P + rowL) & 31)) & 1u))
+            // Candidates for the earliest cofacet of an edge sigma come in
+            // descending face-L order; the first whose parallel edge sigma' has
+            // value <= value(sigma) gives a face of value value(sigma), the least
+            // possible.  sigma is that face's latest facet unless an edge of the
+            // face with equal value has a smaller L: sigma' on the - side with
+            // equal value, or one of the two edges along the other axis b when
+            // b < a (one of them always has value(sigma)).  With no such
+            // candidate the earliest cofacet is larger than sigma and sigma is not
+            // its latest facet.  So z-edges (b < a always) are never apparent,
+            // y-edges only through their +-z faces, x-edges through any.
+            // -- x-edge (v, v+x): faces +z, -z ({x,z}, type 1), +y, -y ({x,y}, type 0)
+            if (hx) {
+                const float fs = exc;
+                const float cpy = fmaxf(fc, box[bz][by + 1][bx + 1]);
+                const float cmy = fmaxf(box[bz][by - 1][bx], box[bz][by - 1][bx + 1]);
+                int side = 0;  // 1 +z, 2 -z, 3 +y, 4 -y; the first qualifying wins
+                float fp = 0.f;
+                if (my && cmy <= fs) { side = 4; fp = cmy; }
+                if (hy && cpy <= fs) { side = 3; fp = cpy; }
+                if (mz && exp_ <= fs) { side = 2; fp = exp_; }
+                if (hz && exn <= fs) { side = 1; fp = exn; }
+                if (side != 0 && ((side & 1) || fp < fs)) {
+                    sx = side;
+                    if (keep_zero) {
+                        const int m = side <= 2 ? 1 : 0;
+                        const int dyf = side == 4 ? -1 : 0, dzf = side == 2 ? -1 : 0;
+                        const uint32_t fr = (uint32_t)m * P + rowL + (uint32_t)(dzf * (int)plane + dyf * nx);
+                        const float cv = unord32(ord32(fs));
+                        emit_pair(pb, 0u, 1, cv, cv, lv, fr + (uint32_t)tx, 0);
                     }
-                }
-                if (tk == ~0ull) { set_status(status, CR_ERR_INTERNAL); break; }
-                // is this edge the latest facet of that face?  Its edges: along a at w
-                // and w+e_b, along b at w and w+e_a (w = the face's anchor)
-                const int bx0 = tb == 0, by0 = tb == 1, bz0 = tb == 2;
-                const int wx = toff * bx0, wy = toff * by0, wz = toff * bz0;
-                const uint32_t wL = toff ? lv - stride[tb] : lv;
-                const uint32_t sb = tb == 0 ? 1u : (tb == 1 ? (uint32_t)nx : plane);
-                const uint32_t sa = stride[a];
-                uint32_t u0, u1;
-                uint64_t best;
-                u0 = V(wx, wy, wz); u1 = V(wx + ax0, wy + ay0, wz + az0);                       // along a at w
-                best = make_key(u0 > u1 ? u0 : u1, wL + (uint32_t)a * P);
-                u0 = V(wx + bx0, wy + by0, wz + bz0); u1 = V(wx + bx0 + ax0, wy + by0 + ay0, wz + bz0 + az0);  // along a at w+e_b
-                uint64_t e2 = make_key(u0 > u1 ? u0 : u1, wL + sb + (uint32_t)a * P);
-                best = e2 > best ? e2 : best;
-                u0 = V(wx, wy, wz); u1 = V(wx + bx0, wy + by0, wz + bz0);                       // along b at w
-                e2 = make_key(u0 > u1 ? u0 : u1, wL + (uint32_t)tb * P);
-                best = e2 > best ? e2 : best;
-                u0 = V(wx + ax0, wy + ay0, wz + az0); u1 = V(wx + ax0 + bx0, wy + ay0 + by0, wz + az0 + bz0);  // along b at w+e_a
-                e2 = make_key(u0 > u1 ? u0 : u1, wL + sa + (uint32_t)tb * P);
-                best = e2 > best ? e2 : best;
-                if (best == sk) {
-                    const int64_t bit = S.loff + key_L(tk);
-                    atomicOr(&I.appmask[bit >> 5], 1u << (bit & 31));
-                    if (flags & CR_KEEP_ZERO) emit_pair(pb, 0u, 1, key_value(sk), key_value(tk), sL, key_L(tk), 0);
                 } else {
-                    keep = true;
+                    colx = !KILLED(0, dds[zz][ty][tx + 1]);
                 }
-            } while (0);
-            if (a == 0) { keep0 = sk; kf0 = keep; }
-            if (a == 1) { keep1 = sk; kf1 = keep; }
-            if (a == 2) { keep2 = sk; kf2 = keep; }
+            }
+            // -- y-edge (v, v+y): only the {y,z} faces (+z, -z, type 2) can make it apparent
+            if (hy) {
+                const float fs = eyc;
+                const bool pz = hz && eyn <= fs;
+                const bool qz = !pz && mz && eyp < fs;
+                if (pz || qz) {
+                    sy = pz ? 1 : 2;
+                    if (keep_zero) {
+                        const uint32_t fr = 2u * P + rowL - (qz ? plane : 0u);
+                        const float cv = unord32(ord32(fs));
+                        emit_pair(pb, 0u, 1, cv, cv, lv + P, fr + (uint32_t)tx, 0);
+                    }
+                } else {
+                    coly = !KILLED(1, dds[zz][ty + 1][tx]);
+                }
+            }
+            // -- z-edge (v, v+z): a column whenever it survives dimension 0
+            if (hz) colz = !KILLED(2, dds[zz + 1][ty][tx]);
+#undef KILLED
+#undef RB
         }
-        const int cnt = (int)kf0 + (int)kf1 + (int)kf2;
-        int64_t i0 = block_append(cnt, ncol);
-        if (i0 + cnt > max_cols) {
-            if (cnt) fail_ws(status, SITE_COLUMNS);
-        } else {
-            if (kf0) { colkey[i0] = ~keep0; colseg[i0++] = 0u; }
-            if (kf1) { colkey[i0] = ~keep1; colseg[i0++] = 0u; }
-            if (kf2) { colkey[i0] = ~keep2; colseg[i0++] = 0u; }
+        // apparent pivots: a warp's lanes are 32 consecutive x of one row, so
+        // each (face type, anchor row) gives one ballot, OR-ed into the tile
+        // mask (two words: the row need not start on a word boundary)
+        {
+            const unsigned m1 = __ballot_sync(0xFFFFFFFFu, sx == 1), m2 = __ballot_sync(0xFFFFFFFFu, sx == 2);
+            const unsigned m3 = __ballot_sync(0xFFFFFFFFu, sx == 3), m4 = __ballot_sync(0xFFFFFFFFu, sx == 4);
+            const unsigned m5 = __ballot_sync(0xFFFFFFFFu, sy == 1), m6 = __ballot_sync(0xFFFFFFFFu, sy == 2);
+            if (lane < 6) {
+                // lane k: x-edge +z, -z (type 1), +y, -y (type 0); y-edge +z, -z (type 2)
+                const unsigned msk = lane == 0 ? m1 : lane == 1 ? m2 : lane == 2 ? m3 : lane == 3 ? m4 : lane == 4 ? m5 : m6;
+                if (msk) {
+                    const int m = lane < 2 ? 1 : (lane < 4 ? 0 : 2);
+                    const int dzf = (lane == 1 || lane == 5) ? -1 : 0, dyf = lane == 3 ? -1 : 0;
+                    const uint32_t fr = (uint32_t)m * P + rowL + (uint32_t)(dzf * (int)plane + dyf * nx);
+                    const int off = (int)((lo + fr) & 31u);
+                    uint32_t *w = &app[m][zz + 1 + dzf][ty + 1 + dyf][0];
+                    atomicOr(w, msk << off);
+                    if (off) atomicOr(w + 1, msk >> (32 - off));
+                }
+            }
         }
+        fa = fa1;
+        fb = fb1;
+        fc = fc1;
+        exp_ = exc;
+        exc = exn;
+        eyp = eyc;
+        eyc = eyn;
+        // residual columns: a warp reserves its run in the tile buffer with one
+        // shared atomic; the buffer goes out with one global reservation when
+        // the next plane could overflow it, and at the end of the tile
+        const int cnt = (int)colx + (int)coly + (int)colz;
+        const unsigned b0 = __ballot_sync(0xFFFFFFFFu, cnt & 1), b1 = __ballot_sync(0xFFFFFFFFu, cnt & 2);
+        const int total = __popc(b0) + 2 * __popc(b1);
+        if (total) {
+            const unsigned lt = (1u << lane) - 1u;
+            int wb = 0;
+            if (lane == 0) wb = atomicAdd(&cn, total);
+            wb = __shfl_sync(0xFFFFFFFFu, wb, 0);
+            int j = wb + __popc(b0 & lt) + 2 * __popc(b1 & lt);
+            if (colx) cbuf[j++] = ~make_key(ord32(fsx), lv);
+            if (coly) cbuf[j++] = ~make_key(ord32(fsy), lv + P);
+            if (colz) cbuf[j++] = ~make_key(ord32(fsz), lv + 2u * P);
+        }
+        __syncthreads();
+        const int n = cn;
+        if (n > SC_CAP - 3 * TILE_X * TILE_Y || (zz == zend - 1 && n > 0)) {
+            if (threadIdx.x == 0) cbase = atomicAdd(ncol, (unsigned long long)n);
+            __syncthreads();
+            const int64_t b0g = (int64_t)cbase;
+            if (b0g + n > max_cols) {
+                if (threadIdx.x == 0) fail_ws(status, SITE_COLUMNS);
+            } else {
+                for (int i = threadIdx.x; i < n; i += TILE_X * TILE_Y) {
+                    colkey[b0g + i] = cbuf[i];
+                    colseg[b0g + i] = 0u;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) cn = 0;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // merge the tile's apparent pivots into the global mask, one atomic per nonzero word
+    for (int i = threadIdx.x; i < 3 * (TILE_Z + 1) * (TILE_Y + 1) * 2; i += TILE_X * TILE_Y) {
+        const uint32_t w = (&app[0][0][0][0])[i];
+        if (!w) continue;
+        const int half = i & 1, r = i >> 1;
+        const int dy = r % (TILE_Y + 1), r2 = r / (TILE_Y + 1);
+        const int dz = r2 % (TILE_Z + 1), m = r2 / (TILE_Z + 1);
+        const int64_t r0 = S.loff + (int64_t)m * P + (int64_t)(z0 - 1 + dz) * plane + (int64_t)(y0 - 1 + dy) * nx + x0;
+        atomicOr(&I.appmask[(r0 >> 5) + half], w);
     }
 }
 
@@ -1296,10 +1421,19 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     cudaMemsetAsync(B.cnt, 0, 24 * sizeof(unsigned long long), st);
     prof_begin(st, STAGE_H1_SCAN);
     CR_NOTE_LAUNCH();
-    CUtensorMap tmap;
+    CUtensorMap tmap, tmap_dd;
     if (nseg == 1 && hseg && hseg->edim == 3 && make_image_map(&tmap, img, *hseg)) {
-        k_h1_scan_tma<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(tmap, I, segs, B.colkey, B.colseg, &B.cnt[0],
-                                                                    B.max_cols, pb, flags, status);
+        static int attr_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (attr_dev != dev) {
+            cudaFuncSetAttribute(k_h1_scan_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, SCAN_DYN_SMEM);
+            attr_dev = dev;
+        }
+        const int dd_tma = make_u8_map(&tmap_dd, dd, *hseg, SC_DX, SC_DY, SC_DZ) ? 1 : 0;
+        if (!dd_tma) memset(&tmap_dd, 0, sizeof(tmap_dd));
+        k_h1_scan_tma<<<(unsigned)ntiles, TILE_X * TILE_Y, SCAN_DYN_SMEM, st>>>(
+            tmap, tmap_dd, dd_tma, I, segs, B.colkey, B.colseg, &B.cnt[0], B.max_cols, pb, flags, status);
     } else {
         k_h1_scan<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(I, segs, nseg, B.colkey, B.colseg, &B.cnt[0],
                                                                 B.max_cols, pb, flags, status);

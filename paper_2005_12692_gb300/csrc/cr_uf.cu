@@ -334,6 +334,22 @@ bool make_image_map(CUtensorMap *m, const float *img, const Seg &S, int bx, int 
     return r == CUDA_SUCCESS;
 }
 
+// a tensor map over one image's 1-byte-per-voxel array (nx, ny, nz); rows must
+// be 16-byte multiples
+bool make_u8_map(CUtensorMap *m, const uint8_t *p, const Seg &S, int bx, int by, int bz) {
+    if (((uintptr_t)p & 15) || (S.nx % 16) != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)S.nx, (cuuint64_t)S.ny, (cuuint64_t)S.nz};
+    cuuint64_t strides[2] = {(cuuint64_t)S.nx, (cuuint64_t)S.nx * S.ny};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)p, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // ===========================================================================
 // pointer jumping.  Pass 1 halves paths in place (every write stores an
 // ancestor, so the forest stays valid); pass 2 lets each node chase to its
