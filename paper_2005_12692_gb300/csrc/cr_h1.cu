@@ -282,9 +282,12 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         (&app[0][0][0][0])[i] = 0u;
     if (threadIdx.x == 0) cn = 0;
     __syncthreads();
-    if (!mbar_wait(&bar, 1ll << 24)) {
-        set_status(status, CR_ERR_TIMEOUT);
-        mbar_wait(&bar, 1ll << 24);
+    // the wait's outcome is made uniform so that no thread is left at a later barrier
+    if (!__syncthreads_and(mbar_wait(&bar, 1ll << 24))) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            set_status(status, CR_ERR_TIMEOUT);
+            mbar_wait(&bar, 1ll << 24);  // let a copy still in flight land before the block exits
+        }
         return;
     }
     const int tx = threadIdx.x & (TILE_X - 1), ty = threadIdx.x / TILE_X, lane = threadIdx.x & 31;

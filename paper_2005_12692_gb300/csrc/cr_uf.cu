@@ -63,56 +63,7 @@ __device__ __forceinline__ int64_t warp_append(bool pred, unsigned long long *co
 // primal H0, round 0: each vertex's minimum incident edge
 // direction codes: 1 -x, 2 +x, 3 -y, 4 +y, 5 -z, 6 +z, 0 = no hook
 // ===========================================================================
-__global__ void k_h0_stencil(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t vtot,
-                             uint32_t *__restrict__ parent, uint8_t *__restrict__ dd, int *status, PairBuf pb,
-                             uint32_t flags) {
-    int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gv >= vtot) return;
-    const int si = seg_of(segs, nseg, gv);
-    const Seg S = segs[si];
-    int64_t lv = gv - S.voff;
-    int x = (int)(lv % S.nx);
-    int y = (int)((lv / S.nx) % S.ny);
-    int z = (int)(lv / ((int64_t)S.nx * S.ny));
-    float fv = img[gv];
-    if (isnan(fv)) set_status(status, CR_ERR_NAN);
-    uint32_t ov = ord32(fv);
-    uint64_t kv = make_key(ov, (uint32_t)lv);
-    uint64_t best = ~0ull;
-    int bestdir = 0;
-    uint32_t bestou = 0, bestlu = 0;
-    int64_t bestu = gv;
-#pragma unroll
-    for (int d = 0; d < 6; d++) {
-        int ax = d >> 1, sgn = (d & 1) ? 1 : -1;
-        int nxp = x + (ax == 0 ? sgn : 0), nyp = y + (ax == 1 ? sgn : 0), nzp = z + (ax == 2 ? sgn : 0);
-        if (nxp < 0 || nxp >= S.nx || nyp < 0 || nyp >= S.ny || nzp < 0 || nzp >= S.nz) continue;
-        int64_t du = ax == 0 ? 1 : (ax == 1 ? (int64_t)S.nx : (int64_t)S.nx * S.ny);
-        int64_t u = gv + sgn * du;
-        uint32_t ou = ord32(img[u]);
-        int axp = sgn > 0 ? x : nxp, ayp = sgn > 0 ? y : nyp, azp = sgn > 0 ? z : nzp;
-        uint64_t ek = make_key(ov > ou ? ov : ou, cube_L(S, ax, axp, ayp, azp));
-        if (ek < best) {
-            best = ek;
-            bestdir = d + 1;
-            bestu = u;
-            bestou = ou;
-            bestlu = (uint32_t)(lv + sgn * du);
-        }
-    }
-    if (bestdir && make_key(bestou, bestlu) < kv) {
-        parent[gv] = (uint32_t)bestu;
-        dd[gv] = (uint8_t)bestdir;
-        if (flags & CR_KEEP_ZERO)
-            emit_pair(pb, (uint32_t)si, 0, unord32(ov), key_value(best), lv, key_L(best), 0);
-    } else {
-        parent[gv] = (uint32_t)gv;
-        dd[gv] = 0;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// The same stencil, tiled: a block owns TILE_X x TILE_Y voxels of one image
+// The stencil, tiled: a block owns TILE_X x TILE_Y voxels of one image
 // and marches TILE_Z planes in z.  Each xy-plane is staged with a one-voxel
 // halo in shared memory; the z neighbours come from registers.  All index
 // arithmetic is 32-bit within the image.
@@ -215,51 +166,55 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tiled(const float
 // halo (a 40x10x18 box, x starting 4 voxels early so the copy starts on a
 // 16-byte boundary; outside the image the box is zero-filled and never used)
 // into shared memory, completing on an mbarrier.  Single images whose rows
-// are a multiple of 16 bytes.
+// are a multiple of 16 bytes; FLAT is the 2D case (one 40x10 plane).
+// The hooks are then followed inside the tile, in shared memory, so that
+// every voxel leaves with the first ancestor outside the tile or its in-tile
+// root: the global pointer jumping starts from paths shortened by the tile.
 // ---------------------------------------------------------------------------
+template <bool FLAT>
 __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tma(const __grid_constant__ CUtensorMap tmap,
                                                                   const Seg *__restrict__ segs,
                                                                   uint32_t *__restrict__ parent,
                                                                   uint8_t *__restrict__ dd, int *status, PairBuf pb,
                                                                   uint32_t flags) {
-    __shared__ __align__(128) float box[TMA_BZ][TMA_BY][TMA_BX];
+    constexpr int BZ = FLAT ? 1 : TMA_BZ, TZ = FLAT ? 1 : TILE_Z;
+    constexpr uint32_t GLOBAL = 0x80000000u;  // lp entry: ancestor outside the tile (global index)
+    __shared__ __align__(128) float box[BZ][TMA_BY][TMA_BX];
+    __shared__ uint32_t lp[FLAT ? TILE_Y * TILE_X : 1];  // in-tile hooks (2D only)
     __shared__ __align__(8) uint64_t bar;
     const Seg S = segs[0];
     const int nx = S.nx, ny = S.ny, nz = S.nz;
-    uint32_t t = blockIdx.x;
-    const int tix = (int)(t % (uint32_t)S.tiles_x);
-    t /= (uint32_t)S.tiles_x;
-    const int tiy = (int)(t % (uint32_t)S.tiles_y);
-    const int tiz = (int)(t / (uint32_t)S.tiles_y);
-    const int x0 = tix * TILE_X, y0 = tiy * TILE_Y, z0 = tiz * TILE_Z;
+    int x0, y0, z0;
+    tile_origin(S, blockIdx.x, x0, y0, z0);
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
-    if (leader) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (leader)
+        tma_load_3d(&tmap, &box[0][0][0], &bar, (uint32_t)(BZ * TMA_BY * TMA_BX * 4), x0 - 4, y0 - 1,
+                    FLAT ? 0 : z0 - 1);
     __syncthreads();
-    if (leader) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(TMA_BYTES)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-            ::"r"(smem_u32(&box[0][0][0])), "l"(&tmap), "r"(x0 - 4), "r"(y0 - 1), "r"(z0 - 1), "r"(smem_u32(&bar))
-            : "memory");
-    }
-    if (!mbar_wait(&bar, 1ll << 24)) {
-        set_status(status, CR_ERR_TIMEOUT);
-        mbar_wait(&bar, 1ll << 24);  // give the copy in flight a chance to land before the block exits
+    // the wait's outcome is made uniform so that no thread is left at a later barrier
+    if (!__syncthreads_and(mbar_wait(&bar, 1ll << 24))) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            set_status(status, CR_ERR_TIMEOUT);
+            mbar_wait(&bar, 1ll << 24);  // let a copy still in flight land before the block exits
+        }
         return;
     }
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x >= nx || y >= ny) return;
+    const bool inxy = x < nx && y < ny;
     const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
     const int bx = threadIdx.x + 4, by = threadIdx.y + 1;
     bool nan_seen = false;
-    const int zend = min(TILE_Z, nz - z0);
+    const int zend = FLAT ? 1 : min(TILE_Z, nz - z0);
     const uint32_t P = plane * (uint32_t)nz;  // size of one type's L-range
-    for (int zz = 0; zz < zend; zz++) {
-        const int z = z0 + zz, bz = zz + 1;
+    const int tl = threadIdx.y * TILE_X + threadIdx.x;  // local index in a plane of the tile
+#pragma unroll 1
+    for (int zz = 0; zz < TZ; zz++) {
+        const int li = zz * TILE_X * TILE_Y + tl;
+        if (zz >= zend || !inxy) {
+            if (FLAT) lp[li] = (uint32_t)li;  // outside the image: never referenced
+            continue;
+        }
+        const int z = z0 + zz, bz = FLAT ? 0 : zz + 1;
         const float fv = box[bz][by][bx];
         nan_seen |= isnan(fv);
         const uint32_t lv = (uint32_t)z * plane + (uint32_t)y * nx + x;
@@ -281,15 +236,27 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tma(const __grid_
         CR_NB(x + 1 < nx, box[bz][by][bx + 1], 2)
         CR_NB(y > 0, box[bz][by - 1][bx], 3)
         CR_NB(y + 1 < ny, box[bz][by + 1][bx], 4)
-        CR_NB(z > 0, box[bz - 1][by][bx], 5)
-        CR_NB(z + 1 < nz, box[bz + 1][by][bx], 6)
+        if (!FLAT) {
+            CR_NB(z > 0, box[bz - 1][by][bx], 5)
+            CR_NB(z + 1 < nz, box[bz + 1][by][bx], 6)
+        }
 #undef CR_NB
         // the neighbour is older iff its value is smaller, or equal with a
         // larger L (a neighbour in the + direction)
         if (dir && (fu < fv || !(dir & 1))) {
             const uint32_t st = dir <= 2 ? 1u : (dir <= 4 ? (uint32_t)nx : plane);
             const uint32_t lu = (dir & 1) ? lv - st : lv + st;
-            parent[lv] = lu;
+            // the same step inside the tile, when it stays there
+            const int lstep = dir <= 2 ? 1 : (dir <= 4 ? TILE_X : TILE_X * TILE_Y);
+            const bool inside = dir == 1 ? threadIdx.x > 0
+                              : dir == 2 ? threadIdx.x + 1 < TILE_X
+                              : dir == 3 ? threadIdx.y > 0
+                              : dir == 4 ? threadIdx.y + 1 < TILE_Y
+                              : dir == 5 ? zz > 0 : zz + 1 < TILE_Z;
+            if (FLAT)
+                lp[li] = inside ? (uint32_t)((dir & 1) ? li - lstep : li + lstep) : (GLOBAL | lu);
+            else
+                parent[lv] = lu;
             dd[lv] = (uint8_t)dir;
             if (flags & CR_KEEP_ZERO) {
                 const uint32_t la = ((dir & 1) ? lu : lv) + (uint32_t)((dir - 1) >> 1) * P;
@@ -297,11 +264,46 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h0_stencil_tma(const __grid_
                 emit_pair(pb, 0u, 0, cv, cv, lv, la, 0);
             }
         } else {
-            parent[lv] = lv;
+            if (FLAT)
+                lp[li] = (uint32_t)li;
+            else
+                parent[lv] = lv;
             dd[lv] = 0;
         }
     }
     if (nan_seen) set_status(status, CR_ERR_NAN);
+    if (!FLAT) return;
+    __syncthreads();
+    // pointer jumping inside the tile (every write stores an ancestor)
+    for (int it = 0; it < 64; it++) {
+        int ch = 0;
+#pragma unroll 1
+        for (int zz = 0; zz < TZ; zz++) {
+            const int li = zz * TILE_X * TILE_Y + tl;
+            const uint32_t p = lp[li];
+            if (p & GLOBAL) continue;
+            const uint32_t q = lp[p];
+            if (q != p) {
+                lp[li] = q;
+                ch = 1;
+            }
+        }
+        if (!__syncthreads_or(ch)) break;
+    }
+    if (!inxy) return;
+#pragma unroll 1
+    for (int zz = 0; zz < zend; zz++) {
+        const int li = zz * TILE_X * TILE_Y + tl;
+        const uint32_t p = lp[li];
+        uint32_t g;
+        if (p & GLOBAL) {
+            g = p & ~GLOBAL;
+        } else {
+            const int pz = p / (TILE_X * TILE_Y), py = (p / TILE_X) % TILE_Y, px = p % TILE_X;
+            g = (uint32_t)(z0 + pz) * plane + (uint32_t)(y0 + py) * nx + (uint32_t)(x0 + px);
+        }
+        parent[(uint32_t)(z0 + zz) * plane + (uint32_t)y * nx + x] = g;
+    }
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -350,80 +352,10 @@ bool make_u8_map(CUtensorMap *m, const uint8_t *p, const Seg &S, int bx, int by,
     return r == CUDA_SUCCESS;
 }
 
-// ===========================================================================
-// pointer jumping.  Pass 1 halves paths in place (every write stores an
-// ancestor, so the forest stays valid); pass 2 lets each node chase to its
-// root and write only its own entry, so no later write can replace a root by
-// a non-root ancestor.
-// ===========================================================================
-// one in-place pointer-doubling step per node (every write stores an ancestor)
-__global__ void k_double(uint32_t *__restrict__ p, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t a = p[i];
-    uint32_t b = p[a];
-    if (b != a) p[i] = b;
-}
 
-__global__ void k_halve(uint32_t *__restrict__ p, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t a = (uint32_t)i;
-    for (int it = 0; it < 64; it++) {
-        uint32_t b = p[a];
-        if (b == a) return;
-        uint32_t c = p[b];
-        if (c == b) return;
-        p[a] = c;
-        a = c;
-    }
-}
 
-__global__ void k_find_root(uint32_t *__restrict__ p, int64_t n, int *status) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t a = p[i];
-    int64_t it = 0;
-    for (;;) {
-        uint32_t b = p[a];
-        if (b == a) break;
-        a = b;
-        if (++it > n) { set_status(status, CR_ERR_INTERNAL); return; }
-    }
-    p[i] = a;
-}
 
-// roots get a group id (kept in the label slot with the top bit set)
-__global__ void k_h0_roots(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t vtot,
-                           uint32_t *__restrict__ lab, unsigned long long *ngroups, int64_t max_groups,
-                           uint64_t *__restrict__ gkey, uint32_t *__restrict__ groot, uint32_t *__restrict__ gseg,
-                           int *status) {
-    int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool isroot = gv < vtot && lab[gv] == (uint32_t)gv;
-    int64_t g = warp_append(isroot, ngroups);
-    if (!isroot) return;
-    if (g >= max_groups) { fail_ws(status, SITE_GROUPS); lab[gv] = 0x80000000u; return; }
-    int si = seg_of(segs, nseg, gv);
-    int64_t lv = gv - segs[si].voff;
-    gkey[g] = make_key(ord32(img[gv]), (uint32_t)lv);
-    groot[g] = (uint32_t)gv;
-    gseg[g] = (uint32_t)si;
-    lab[gv] = 0x80000000u | (uint32_t)g;
-}
 
-// label[v] <- group of its root
-__global__ void k_relabel(uint32_t *__restrict__ lab, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t a = lab[i];
-    if (a & 0x80000000u) return;  // a root: cleared in the second kernel
-    lab[i] = lab[a] & 0x7FFFFFFFu;
-}
-__global__ void k_unmark(uint32_t *__restrict__ lab, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    lab[i] &= 0x7FFFFFFFu;
-}
 
 // edges between different basins; an edge is a stencil (round-0) hook iff
 // one of its endpoints points at the other through it
@@ -620,7 +552,9 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_dual_stencil_tma(const __gri
     constexpr int BZ = EDIM == 3 ? DUAL_BZ3 : 1;
     constexpr uint32_t BOX_BYTES = (uint32_t)BZ * DUAL_BY * DUAL_BX * 4;
     __shared__ __align__(128) float box[BZ][DUAL_BY][DUAL_BX];
+    __shared__ uint32_t lp[EDIM == 2 ? TILE_Y * TILE_X : 1];  // in-tile hooks (2D only)
     __shared__ __align__(8) uint64_t bar;
+    constexpr uint32_t GLOBAL = 0x80000000u;  // lp entry: ancestor outside the tile (global index)
     const Seg S = segs[0];
     const int nx = S.nx, ny = S.ny, nz = S.nz;
     int x0, y0, z0;
@@ -634,19 +568,25 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_dual_stencil_tma(const __gri
         tma_load_3d(&tmap, &box[0][0][0], &bar, BOX_BYTES, x0 - 4, y0 - 1, EDIM == 3 ? z0 - 1 : 0);
     }
     __syncthreads();
-    if (!mbar_wait(&bar, 1ll << 24)) {
-        set_status(status, CR_ERR_TIMEOUT);
-        mbar_wait(&bar, 1ll << 24);
+    // the wait's outcome is made uniform so that no thread is left at a later barrier
+    if (!__syncthreads_and(mbar_wait(&bar, 1ll << 24))) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            set_status(status, CR_ERR_TIMEOUT);
+            mbar_wait(&bar, 1ll << 24);  // let a copy still in flight land before the block exits
+        }
         return;
     }
     const int cx = nx - 1, cy = ny - 1, cz = EDIM == 3 ? nz - 1 : 1;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x >= cx || y >= cy) return;
+    const int tl = threadIdx.y * TILE_X + threadIdx.x;
+    const bool incell = x < cx && y < cy;
+    if (EDIM == 2 && !incell) lp[tl] = (uint32_t)tl;  // never referenced
+    if (EDIM == 3 && !incell) return;
     const int bx = threadIdx.x + 4, by = threadIdx.y + 1;
     const int zend = EDIM == 3 ? min(TILE_Z, cz - z0) : 1;
     const uint32_t outer = (uint32_t)(S.coff + S.ncell);
     bool nan_seen = false;
-    for (int zz = 0; zz < zend; zz++) {
+    for (int zz = 0; zz < zend && incell; zz++) {
         const int z = z0 + zz, bz = EDIM == 3 ? zz + 1 : 0;
         const uint32_t c = ((uint32_t)z * (uint32_t)cy + (uint32_t)y) * (uint32_t)cx + (uint32_t)x;
         float fc;
@@ -709,7 +649,15 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_dual_stencil_tma(const __gri
         }
         const uint32_t gc = (uint32_t)S.coff + c;
         if (hook) {
-            parent[gc] = other;
+            if (EDIM == 2) {
+                // the same hook inside the tile, when it stays there
+                const bool inside = !outside && (axis == 0 ? (up ? threadIdx.x + 1 < TILE_X : threadIdx.x > 0)
+                                                           : (up ? threadIdx.y + 1 < TILE_Y : threadIdx.y > 0));
+                const int lstep = axis == 0 ? 1 : TILE_X;
+                lp[tl] = inside ? (uint32_t)(up ? tl + lstep : tl - lstep) : (GLOBAL | other);
+            } else {
+                parent[gc] = other;
+            }
             dd[gc] = (uint8_t)(f + 1);
             if (flags & CR_KEEP_ZERO) {
                 uint32_t fl;
@@ -724,35 +672,41 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_dual_stencil_tma(const __gri
                 emit_pair(pb, 0u, EDIM - 1, cv, cv, fl, cube_L(S, 0, x, y, z), 0);
             }
         } else {
-            parent[gc] = gc;
+            if (EDIM == 2)
+                lp[tl] = (uint32_t)tl;
+            else
+                parent[gc] = gc;
             dd[gc] = 0;
         }
     }
     if (nan_seen) set_status(status, CR_ERR_NAN);
+    if (EDIM == 3) return;
+    // 2D: follow the hooks inside the tile (every write stores an ancestor)
+    __syncthreads();
+    for (int it = 0; it < 64; it++) {
+        int ch = 0;
+        const uint32_t p = lp[tl];
+        if (!(p & GLOBAL)) {
+            const uint32_t q = lp[p];
+            if (q != p) {
+                lp[tl] = q;
+                ch = 1;
+            }
+        }
+        if (!__syncthreads_or(ch)) break;
+    }
+    if (!incell) return;
+    const uint32_t p = lp[tl];
+    uint32_t g;
+    if (p & GLOBAL) {
+        g = p & ~GLOBAL;
+    } else {
+        const int py = (int)p / TILE_X, px = (int)p % TILE_X;
+        g = (uint32_t)S.coff + (uint32_t)(y0 + py) * (uint32_t)cx + (uint32_t)(x0 + px);
+    }
+    parent[(uint32_t)S.coff + (uint32_t)y * (uint32_t)cx + (uint32_t)x] = g;
 }
 
-__global__ void k_dual_roots(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg, int64_t ctot,
-                             uint32_t *__restrict__ lab, unsigned long long *ngroups, int64_t max_groups,
-                             uint64_t *__restrict__ gkey, uint32_t *__restrict__ groot, uint32_t *__restrict__ gseg,
-                             int *status) {
-    int64_t gc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool isroot = gc < ctot && lab[gc] == (uint32_t)gc;
-    int64_t g = warp_append(isroot, ngroups);
-    if (!isroot) return;
-    if (g >= max_groups) { fail_ws(status, SITE_GROUPS); lab[gc] = 0x80000000u; return; }
-    int si = seg_of_node(segs, nseg, gc);
-    const Seg S = segs[si];
-    int64_t c = gc - S.coff;
-    uint64_t age = 0;  // outer node: oldest
-    if (c < S.ncell) {
-        CellPos p = cell_pos(S, c);
-        age = ~top_key(img, S, p.x, p.y, p.z);
-    }
-    gkey[g] = age;
-    groot[g] = (uint32_t)gc;
-    gseg[g] = (uint32_t)si;
-    lab[gc] = 0x80000000u | (uint32_t)g;
-}
 
 // dual edges = facets of the top cubes, iterated over the L-space of type m
 __global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restrict__ segs, int nseg,
@@ -849,7 +803,6 @@ __global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restric
 // host drivers
 // ===========================================================================
 
-static inline unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------------------
 // All Boruvka rounds in one cooperative kernel: the counts stay on the
@@ -1291,9 +1244,14 @@ int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
     prof_begin(st, STAGE_H0_STENCIL);
     CR_NOTE_LAUNCH();
     CUtensorMap tmap;
-    if (nseg == 1 && make_image_map(&tmap, img, hsegs[0])) {
-        k_h0_stencil_tma<<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd, status, pb,
-                                                                            flags);
+    const bool flat = hsegs[0].nz == 1;
+    if (nseg == 1 && make_image_map(&tmap, img, hsegs[0], TMA_BX, TMA_BY, flat ? 1 : TMA_BZ)) {
+        if (flat)
+            k_h0_stencil_tma<true><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd,
+                                                                                    status, pb, flags);
+        else
+            k_h0_stencil_tma<false><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd,
+                                                                                     status, pb, flags);
     } else {
         k_h0_stencil_tiled<<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(img, segs, nseg, u.lab, u.dd, status,
                                                                               pb, flags);
