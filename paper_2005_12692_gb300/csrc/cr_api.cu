@@ -114,8 +114,8 @@ static size_t fixed_bytes(const HostPlan &P) {
     size_t b = 0;
     b += al(P.segs.size() * sizeof(Seg));
     b += al(CR_CNT_SLOTS * sizeof(unsigned long long));  // status + counters
-    int64_t nodes = P.vtot > P.ctot ? P.vtot : P.ctot;
-    b += al((size_t)nodes * sizeof(uint32_t));  // labels
+    b += al((size_t)P.vtot * sizeof(uint32_t));  // primal labels
+    b += al((size_t)P.ctot * sizeof(uint32_t));  // dual labels
     b += al((size_t)P.vtot);                    // primal hooks
     b += al((size_t)P.ctot);                    // dual hooks
     b += al((size_t)((3 * P.vtot + 31) / 32) * sizeof(uint32_t));  // extra H0 edge mask
@@ -137,6 +137,7 @@ static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
         for (const Seg &S : P.segs) edim = S.edim > edim ? S.edim : edim;
         uf = al((size_t)nodes * 16) + al((size_t)P.vtot * (edim == 3 && P.any_dual ? 96 : 48)) + (8 << 20);
     }
+    if (P.any_h0 && P.any_dual) uf *= 2;  // both union-finds are live at once
     if (P.any_mid) {
         int64_t nw;
         int ml;
@@ -262,6 +263,39 @@ __global__ void k_out_place(const cr_pair *__restrict__ tmp, int np, const uint3
     if (d < (uint32_t)np) pairs[d] = p;
 }
 
+// Group and edge arrays of one union-find in [base, base + cap): the number of
+// roots is not known yet, so the groups get a share proportional to the node
+// count (at most a third) and the edges the rest, two buffers of at most
+// 3 edges per voxel.
+static int carve_uf(char *base, size_t cap, int64_t nodes, int64_t vtot, UF &u) {
+    Carver R(base, cap);
+    int64_t max_groups = nodes;
+    size_t gbytes = (size_t)max_groups * 45 + 8 * 256;
+    if (gbytes > cap / 3) max_groups = (int64_t)((cap / 3) / 45) - 64;
+    if (max_groups < 1) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
+    u.gkey = R.take<uint64_t>(max_groups);
+    u.minE = R.take<uint64_t>(max_groups);
+    u.groot = R.take<uint32_t>(max_groups);
+    u.gseg = R.take<uint32_t>(max_groups);
+    u.minE2 = R.take<uint64_t>(max_groups);
+    u.dkey = R.take<uint64_t>(max_groups);
+    u.hook = R.take<uint32_t>(max_groups);
+    u.gdead = R.take<uint8_t>(max_groups);
+    u.max_groups = max_groups;
+    size_t left = R.cap > R.used ? R.cap - R.used : 0;
+    int64_t max_edges = (int64_t)(left / 32) - 64;
+    if (max_edges > 3 * vtot + 1) max_edges = 3 * vtot + 1;
+    if (max_edges < 1 || !R.ok) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
+    for (int b = 0; b < 2; b++) {
+        u.ek[b] = R.take<uint64_t>(max_edges);
+        u.ea[b] = R.take<uint32_t>(max_edges);
+        u.eb[b] = R.take<uint32_t>(max_edges);
+    }
+    u.max_edges = max_edges;
+    if (!R.ok) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
+    return CR_OK;
+}
+
 // ---------------------------------------------------------------------------
 // the pipeline
 // ---------------------------------------------------------------------------
@@ -275,8 +309,8 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     Carver C(ws, ws_bytes);
     Seg *segs = C.take<Seg>(n);
     unsigned long long *cnt = C.take<unsigned long long>(CR_CNT_SLOTS);
-    int64_t nodes = P.vtot > P.ctot ? P.vtot : P.ctot;
-    uint32_t *lab = C.take<uint32_t>(nodes);
+    uint32_t *lab = C.take<uint32_t>(P.vtot);
+    uint32_t *labc = C.take<uint32_t>(P.ctot);
     uint8_t *dd = C.take<uint8_t>(P.vtot);
     uint8_t *ddc = C.take<uint8_t>(P.ctot);
     int64_t mask_words = (3 * P.vtot + 31) / 32;
@@ -299,42 +333,30 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     unsigned long long hc[4];
     int rc = CR_OK;
 
-    // ---- H0 ----
-    if (P.any_h0) {
-        Carver R(region, region_cap);
-        UF u;
-        u.lab = lab;
-        u.dd = dd;
-        u.cnt = &cnt[CNT_H0];
-        u.hcnt = hc;
-        // groups: the number of roots is not known yet; give the union-find a
-        // share of the region proportional to the node count and the rest to edges
-        int64_t max_groups = P.vtot;
-        size_t gbytes = (size_t)max_groups * 45 + 8 * 256;
-        if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 45) - 64;
-        if (max_groups < 1) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
-        u.gkey = R.take<uint64_t>(max_groups);
-        u.minE = R.take<uint64_t>(max_groups);
-        u.groot = R.take<uint32_t>(max_groups);
-        u.gseg = R.take<uint32_t>(max_groups);
-        u.minE2 = R.take<uint64_t>(max_groups);
-        u.dkey = R.take<uint64_t>(max_groups);
-        u.hook = R.take<uint32_t>(max_groups);
-        u.gdead = R.take<uint8_t>(max_groups);
-        u.max_groups = max_groups;
-        size_t left = R.cap > R.used ? R.cap - R.used : 0;
-        int64_t max_edges = (int64_t)(left / 32) - 64;
-        if (max_edges > 3 * P.vtot + 1) max_edges = 3 * P.vtot + 1;
-        if (max_edges < 1 || !R.ok) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
-        for (int b = 0; b < 2; b++) {
-            u.ek[b] = R.take<uint64_t>(max_edges);
-            u.ea[b] = R.take<uint32_t>(max_edges);
-            u.eb[b] = R.take<uint32_t>(max_edges);
+    // ---- H0 and the top dimension by duality: two independent union-finds,
+    // run side by side in halves of the region ----
+    if (P.any_h0 || P.any_dual) {
+        const bool both = P.any_h0 && P.any_dual;
+        const size_t half = both ? (region_cap / 2) & ~(size_t)255 : region_cap;
+        UF uh, ud;
+        if (P.any_h0) {
+            rc = carve_uf(region, half, P.vtot, P.vtot, uh);
+            if (rc) return rc;
+            uh.lab = lab;
+            uh.dd = dd;
+            uh.cnt = &cnt[CNT_H0];
+            uh.hcnt = hc;
         }
-        u.max_edges = max_edges;
-        if (!R.ok) return CR_ERR_WORKSPACE;
-        rc = run_h0(imgs, segs, P.segs.data(), n, P.vtot, P.ntiles, u, pb, flags, P.any_mid ? extra : nullptr,
-                    status, st);
+        if (P.any_dual) {
+            rc = carve_uf(region + (both ? half : 0), both ? region_cap - half : region_cap, P.ctot, P.vtot, ud);
+            if (rc) return rc;
+            ud.lab = labc;
+            ud.dd = ddc;
+            ud.cnt = &cnt[CNT_DUAL];
+            ud.hcnt = hc;
+        }
+        rc = run_uf(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, P.any_h0 ? &uh : nullptr,
+                    P.any_dual ? &ud : nullptr, pb, flags, P.any_mid ? extra : nullptr, status, st);
         if (rc) return rc;
     }
 
@@ -378,42 +400,6 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         B.pool = R.take<uint64_t>(B.pool_cap);
         int64_t ncols = 0;
         rc = run_h1(imgs, dd, extra, segs, P.segs.data(), n, P.vtot, P.ntiles, B, pb, flags, status, &ncols, st);
-        if (rc) return rc;
-    }
-
-    // ---- top dimension by duality ----
-    if (P.any_dual) {
-        Carver R(region, region_cap);
-        UF u;
-        u.lab = lab;
-        u.dd = ddc;
-        u.cnt = &cnt[CNT_DUAL];
-        u.hcnt = hc;
-        int64_t max_groups = P.ctot;
-        size_t gbytes = (size_t)max_groups * 45 + 8 * 256;
-        if (gbytes > region_cap / 3) max_groups = (int64_t)((region_cap / 3) / 45) - 64;
-        if (max_groups < 1) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
-        u.gkey = R.take<uint64_t>(max_groups);
-        u.minE = R.take<uint64_t>(max_groups);
-        u.groot = R.take<uint32_t>(max_groups);
-        u.gseg = R.take<uint32_t>(max_groups);
-        u.minE2 = R.take<uint64_t>(max_groups);
-        u.dkey = R.take<uint64_t>(max_groups);
-        u.hook = R.take<uint32_t>(max_groups);
-        u.gdead = R.take<uint8_t>(max_groups);
-        u.max_groups = max_groups;
-        size_t left = R.cap > R.used ? R.cap - R.used : 0;
-        int64_t max_edges = (int64_t)(left / 32) - 64;
-        if (max_edges > 3 * P.vtot + 1) max_edges = 3 * P.vtot + 1;
-        if (max_edges < 1 || !R.ok) { g_detail = SITE_UF_CARVE; return CR_ERR_WORKSPACE; }
-        for (int b = 0; b < 2; b++) {
-            u.ek[b] = R.take<uint64_t>(max_edges);
-            u.ea[b] = R.take<uint32_t>(max_edges);
-            u.eb[b] = R.take<uint32_t>(max_edges);
-        }
-        u.max_edges = max_edges;
-        if (!R.ok) return CR_ERR_WORKSPACE;
-        rc = run_dual(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, u, pb, flags, status, st);
         if (rc) return rc;
     }
 

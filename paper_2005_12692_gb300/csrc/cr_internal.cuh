@@ -282,11 +282,11 @@ struct UF {
     unsigned long long *cnt;   // device counters [0] groups, [1] edges, [2] edges after a round
     unsigned long long *hcnt;  // host mirror
 };
-int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ntiles, UF &u,
-           const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status, cudaStream_t st);
-int run_dual(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ctot,
-             int64_t ntiles, UF &u,
-             const PairBuf &pb, uint32_t flags, int *status, cudaStream_t st);
+// union-find of H0 (u0, primal graph) and of the top dimension (u1, dual
+// graph); either may be null
+int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ctot,
+           int64_t ntiles, UF *u0, UF *u1, const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status,
+           cudaStream_t st);
 
 // middle-dimension buffers (cr_h1.cu)
 struct H1Bufs {

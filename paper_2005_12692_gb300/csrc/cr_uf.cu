@@ -806,15 +806,14 @@ __global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restric
 
 // ---------------------------------------------------------------------------
 // All Boruvka rounds in one cooperative kernel: the counts stay on the
-// device, phases are separated by a grid barrier with a bounded spin.
+// device, phases are separated by a grid barrier with a bounded spin.  The
+// primal graph (H0) and the dual graph (top dimension) are independent, so one
+// launch runs both in lock step and they share every barrier.
 // ---------------------------------------------------------------------------
+constexpr int MAX_GRAPHS = 2;
 struct RoundArgs {
-    UF u;
-    const Seg *segs;
-    int mode;
-    PairBuf pb;
-    uint32_t flags;
-    uint32_t *extra_mask;
+    UF u[MAX_GRAPHS];
+    int ngraph;
     int *status;
 };
 
@@ -850,7 +849,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int &
 }
 
 // ---------------------------------------------------------------------------
-// Basins in one cooperative launch (one 1024-thread block per SM):
+// Basins in one cooperative launch (one 1024-thread block per SM), for one or
+// both graphs at once:
 //   passes of in-place pointer doubling until a pass changes nothing (every
 //   write stores an ancestor, and a pass without writes saw every node
 //   pointing at a root);
@@ -863,97 +863,121 @@ struct BasinArgs {
     const float *img;
     const Seg *segs;
     int nseg;
-    int mode;  // 0 primal vertices, 1 dual nodes (top cubes + outer nodes)
-    int64_t n;
-    uint32_t *lab;
-    unsigned long long *cnt;  // the run's counter slots
-    int64_t max_groups;
-    uint64_t *gkey;
-    uint32_t *groot, *gseg;
+    int ngraph;
+    int mode[MAX_GRAPHS];  // 0 primal vertices, 1 dual nodes (top cubes + outer nodes)
+    int64_t n[MAX_GRAPHS];
+    UF u[MAX_GRAPHS];
     int *status;
 };
 
+__device__ __forceinline__ int doubling_pass(uint32_t *lab, int64_t n, int64_t tid, int64_t nthr) {
+    int ch = 0;
+    int64_t i = tid;
+    for (; i + 3 * nthr < n; i += 4 * nthr) {
+        uint32_t a[4], b[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) a[k] = __ldcg(lab + i + k * nthr);
+#pragma unroll
+        for (int k = 0; k < 4; k++) b[k] = __ldcg(lab + a[k]);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (b[k] != a[k]) {
+                lab[i + k * nthr] = b[k];
+                ch = 1;
+            }
+    }
+    for (; i < n; i += nthr) {
+        const uint32_t a = __ldcg(lab + i), b = __ldcg(lab + a);
+        if (b != a) {
+            lab[i] = b;
+            ch = 1;
+        }
+    }
+    return ch;
+}
+
 __global__ void __launch_bounds__(BASIN_THREADS, 1) k_basins(BasinArgs A) {
     if (*(volatile int *)A.status) return;
-    unsigned int *bar = (unsigned int *)&A.cnt[UFC_BAR_BASINS];
+    unsigned int *bar = (unsigned int *)&A.u[0].cnt[UFC_BAR_BASINS];
     unsigned int target = 0;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n = A.n;
-    uint32_t *lab = A.lab;
+    bool live[MAX_GRAPHS] = {A.ngraph > 0, A.ngraph > 1};
     for (int pass = 0; pass < 64; pass++) {
-        unsigned long long *changed = &A.cnt[UFC_CHANGED + pass % 3];
-        if (tid == 0) {
-            A.cnt[UFC_CHANGED + (pass + 1) % 3] = 0;  // last read two barriers ago
-            A.cnt[UFC_PASSES] += 1ull;
-        }
-        int ch = 0;
-        int64_t i = tid;
-        for (; i + 3 * nthr < n; i += 4 * nthr) {
-            uint32_t a[4], b[4];
 #pragma unroll
-            for (int k = 0; k < 4; k++) a[k] = __ldcg(lab + i + k * nthr);
-#pragma unroll
-            for (int k = 0; k < 4; k++) b[k] = __ldcg(lab + a[k]);
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (b[k] != a[k]) {
-                    lab[i + k * nthr] = b[k];
-                    ch = 1;
-                }
-        }
-        for (; i < n; i += nthr) {
-            const uint32_t a = __ldcg(lab + i), b = __ldcg(lab + a);
-            if (b != a) {
-                lab[i] = b;
-                ch = 1;
+        for (int gi = 0; gi < MAX_GRAPHS; gi++) {
+            if (!live[gi]) continue;
+            unsigned long long *cnt = A.u[gi].cnt;
+            if (tid == 0) {
+                cnt[UFC_CHANGED + (pass + 1) % 3] = 0;  // last read two barriers ago
+                cnt[UFC_PASSES] += 1ull;
             }
+            const int ch = doubling_pass(A.u[gi].lab, A.n[gi], tid, nthr);
+            if (__syncthreads_or(ch) && threadIdx.x == 0) atomicAdd(&cnt[UFC_CHANGED + pass % 3], 1ull);
         }
-        if (__syncthreads_or(ch) && threadIdx.x == 0) atomicAdd(changed, 1ull);
         if (!grid_barrier(bar, target, A.status)) return;
-        if (__ldcg(changed) == 0) break;
+        bool any = false;
+#pragma unroll
+        for (int gi = 0; gi < MAX_GRAPHS; gi++) {
+            if (live[gi] && __ldcg(&A.u[gi].cnt[UFC_CHANGED + pass % 3]) == 0) live[gi] = false;
+            any |= live[gi];
+        }
+        if (!any) break;
         if (pass == 63) {
             set_status(A.status, CR_ERR_INTERNAL);
             return;
         }
     }
     // roots
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += nthr) {
-        const int64_t v = base + threadIdx.x;
-        const bool isroot = v < n && __ldcg(lab + v) == (uint32_t)v;
-        const int64_t g = warp_append(isroot, &A.cnt[UFC_GROUPS]);
-        if (!isroot) continue;
-        if (g >= A.max_groups) {
-            fail_ws(A.status, SITE_GROUPS);
-            lab[v] = 0x80000000u;
-            continue;
-        }
-        uint64_t key;
-        int si;
-        if (A.mode == 0) {
-            si = seg_of(A.segs, A.nseg, v);
-            const int64_t lv = v - A.segs[si].voff;
-            key = make_key(ord32(A.img[v]), (uint32_t)lv);
-        } else {
-            si = seg_of_node(A.segs, A.nseg, v);
-            const Seg S = A.segs[si];
-            const int64_t c = v - S.coff;
-            key = 0;  // outer node: oldest
-            if (c < S.ncell) {
-                const CellPos p = cell_pos(S, c);
-                key = ~top_key(A.img, S, p.x, p.y, p.z);
+#pragma unroll
+    for (int gi = 0; gi < MAX_GRAPHS; gi++) {
+        if (gi >= A.ngraph) break;
+        const UF &u = A.u[gi];
+        uint32_t *lab = u.lab;
+        const int64_t n = A.n[gi];
+        for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += nthr) {
+            const int64_t v = base + threadIdx.x;
+            const bool isroot = v < n && __ldcg(lab + v) == (uint32_t)v;
+            const int64_t g = warp_append(isroot, &u.cnt[UFC_GROUPS]);
+            if (!isroot) continue;
+            if (g >= u.max_groups) {
+                fail_ws(A.status, SITE_GROUPS);
+                lab[v] = 0x80000000u;
+                continue;
             }
+            uint64_t key;
+            int si;
+            if (A.mode[gi] == 0) {
+                si = seg_of(A.segs, A.nseg, v);
+                const int64_t lv = v - A.segs[si].voff;
+                key = make_key(ord32(A.img[v]), (uint32_t)lv);
+            } else {
+                si = seg_of_node(A.segs, A.nseg, v);
+                const Seg S = A.segs[si];
+                const int64_t c = v - S.coff;
+                key = 0;  // outer node: oldest
+                if (c < S.ncell) {
+                    const CellPos p = cell_pos(S, c);
+                    key = ~top_key(A.img, S, p.x, p.y, p.z);
+                }
+            }
+            u.gkey[g] = key;
+            u.groot[g] = (uint32_t)v;
+            u.gseg[g] = (uint32_t)si;
+            lab[v] = 0x80000000u | (uint32_t)g;
         }
-        A.gkey[g] = key;
-        A.groot[g] = (uint32_t)v;
-        A.gseg[g] = (uint32_t)si;
-        lab[v] = 0x80000000u | (uint32_t)g;
     }
     if (!grid_barrier(bar, target, A.status)) return;
     // labels -> group ids (roots are marked; every other node points at a root)
-    for (int64_t i = tid; i < n; i += nthr) {
-        const uint32_t v = __ldcg(lab + i);
-        lab[i] = (v & 0x80000000u) ? (v & 0x7FFFFFFFu) : (__ldcg(lab + v) & 0x7FFFFFFFu);
+#pragma unroll
+    for (int gi = 0; gi < MAX_GRAPHS; gi++) {
+        if (gi >= A.ngraph) break;
+        uint32_t *lab = A.u[gi].lab;
+        const int64_t n = A.n[gi];
+        for (int64_t i = tid; i < n; i += nthr) {
+            const uint32_t v = __ldcg(lab + i);
+            lab[i] = (v & 0x80000000u) ? (v & 0x7FFFFFFFu) : (__ldcg(lab + v) & 0x7FFFFFFFu);
+        }
     }
 }
 
@@ -961,17 +985,17 @@ constexpr int UF_THREADS = 1024;
 
 #ifdef CR_UF_TIMING
 // diagnostics build: block 0 records the global timer at every phase end
-__device__ unsigned long long g_uf_trace[2][1024];
-__device__ int g_uf_trace_n[2];
+__device__ unsigned long long g_uf_trace[1024];
+__device__ int g_uf_trace_n;
 #define UF_MARK(v)                                                              \
     do {                                                                        \
         if (blockIdx.x == 0 && threadIdx.x == 0) {                              \
-            int m_ = g_uf_trace_n[A.mode];                                      \
+            int m_ = g_uf_trace_n;                                              \
             if (m_ < 1024) {                                                    \
                 unsigned long long t_;                                          \
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));          \
-                g_uf_trace[A.mode][m_] = (t_ << 20) | ((unsigned long long)(v) & 0xFFFFF); \
-                g_uf_trace_n[A.mode] = m_ + 1;                                  \
+                g_uf_trace[m_] = (t_ << 20) | ((unsigned long long)(v) & 0xFFFFF); \
+                g_uf_trace_n = m_ + 1;                                          \
             }                                                                   \
         }                                                                       \
     } while (0)
@@ -980,6 +1004,16 @@ __device__ int g_uf_trace_n[2];
     do {           \
     } while (0)
 #endif
+
+// per-graph state of the rounds (identical in every thread)
+struct RoundState {
+    int cur;          // edge buffer in use
+    bool inplace;     // list kept in place (dropped edges have a == b)
+    bool compact;     // this round compacts into the other buffer
+    bool done;
+    unsigned long long live_seen;
+    int64_t ne, live, ng;
+};
 
 // Borůvka rounds under the elder rule, three phases per round:
 //   B  (edges)  the edge attaining minE[g] decides g's hook: g dies into the
@@ -995,152 +1029,189 @@ __device__ int g_uf_trace_n[2];
 // atomic and its count read on every round's critical path.
 // The first round's min edges come from a prologue phase; the deaths are
 // written out after the rounds by k_uf_emit.
+__device__ __forceinline__ void phase_B(const UF &u, const RoundState &R, int round, int64_t tid, int64_t nthr) {
+    const uint64_t *ek = R.cur ? u.ek[1] : u.ek[0];
+    const uint32_t *ea = R.cur ? u.ea[1] : u.ea[0], *eb = R.cur ? u.eb[1] : u.eb[0];
+    // the min-edge buffers alternate every round, the edge buffers only
+    // when the list is compacted
+    const uint64_t *mcur = (round & 1) ? u.minE2 : u.minE;
+    uint64_t *mnext = (round & 1) ? u.minE : u.minE2;
+    for (int64_t i = tid; i < R.ne; i += nthr) {
+        const uint64_t k = ek[i];
+        const uint32_t e0 = ea[i], e1 = eb[i];
+        if (e0 == e1) continue;  // dropped edge (in-place list)
+        const uint64_t m0 = __ldcg(mcur + e0), m1 = __ldcg(mcur + e1);
+        const uint64_t k0 = u.gkey[e0], k1 = u.gkey[e1];
+        // only the younger end can die, and only on its own min edge
+        const bool young0 = k1 < k0;
+        const uint32_t g = young0 ? e0 : e1, t = young0 ? e1 : e0;
+        if ((young0 ? m0 : m1) != k) continue;
+        u.hook[g] = t;
+        u.gdead[g] = 1;
+        u.dkey[g] = k;
+    }
+    for (int64_t g = tid; g < R.ng; g += nthr) mnext[g] = ~0ull;
+}
+
+__device__ __forceinline__ void phase_C(const UF &u, const RoundState &R, int64_t tid, int64_t nthr) {
+    for (int64_t g = tid; g < R.ng; g += nthr) {
+        uint32_t p = __ldcg(u.hook + g);
+        if (p == (uint32_t)g) continue;
+        for (int it = 0; it < (1 << 24); it++) {
+            const uint32_t pp = __ldcg(u.hook + p);
+            if (pp == p) break;
+            p = pp;
+            u.hook[g] = p;
+        }
+    }
+}
+
+__device__ __forceinline__ void phase_D(const UF &u, RoundState &R, int round, int64_t tid, int64_t nthr) {
+    uint64_t *ek = R.cur ? u.ek[1] : u.ek[0];
+    uint32_t *ea = R.cur ? u.ea[1] : u.ea[0], *eb = R.cur ? u.eb[1] : u.eb[0];
+    uint64_t *mnext = (round & 1) ? u.minE : u.minE2;
+    if (R.compact) {
+        unsigned long long *nnext = R.cur ? &u.cnt[UFC_E0] : &u.cnt[UFC_E1];
+        uint64_t *ok = R.cur ? u.ek[0] : u.ek[1];
+        uint32_t *oa = R.cur ? u.ea[0] : u.ea[1], *ob = R.cur ? u.eb[0] : u.eb[1];
+        for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < R.ne; base += nthr) {
+            const int64_t i = base + threadIdx.x;
+            bool keep = false;
+            uint32_t a = 0, b = 0;
+            uint64_t k = 0, ma = 0, mb = 0;
+            if (i < R.ne) {
+                a = __ldcg(u.hook + ea[i]);
+                b = __ldcg(u.hook + eb[i]);
+                k = ek[i];
+                keep = a != b;
+                if (keep) {
+                    ma = __ldcg(mnext + a);
+                    mb = __ldcg(mnext + b);
+                }
+            }
+            const int64_t j = block_append(keep ? 1 : 0, nnext);
+            if (keep) {
+                ok[j] = k;
+                oa[j] = a;
+                ob[j] = b;
+                if (ma > k) atomicMin((unsigned long long *)&mnext[a], k);
+                if (mb > k) atomicMin((unsigned long long *)&mnext[b], k);
+            }
+        }
+        R.cur ^= 1;
+    } else {
+        R.inplace = true;
+        int nlive = 0;
+        for (int64_t i = tid; i < R.ne; i += nthr) {
+            const uint32_t e0 = ea[i], e1 = eb[i];
+            const uint64_t k = ek[i];
+            if (e0 == e1) continue;
+            const uint32_t a = __ldcg(u.hook + e0), b = __ldcg(u.hook + e1);
+            if (a == b) {
+                ea[i] = a;
+                eb[i] = a;
+                continue;
+            }
+            const uint64_t ma = __ldcg(mnext + a), mb = __ldcg(mnext + b);
+            if (a != e0) ea[i] = a;
+            if (b != e1) eb[i] = b;
+            if (ma > k) atomicMin((unsigned long long *)&mnext[a], k);
+            if (mb > k) atomicMin((unsigned long long *)&mnext[b], k);
+            nlive++;
+        }
+        nlive = __reduce_add_sync(0xFFFFFFFFu, nlive);
+        if ((threadIdx.x & 31) == 0 && nlive) atomicAdd(&u.cnt[UFC_LIVE], (unsigned long long)nlive);
+    }
+}
+
 __global__ void __launch_bounds__(UF_THREADS, 1) k_uf_rounds(RoundArgs A) {
-    UF &u = A.u;
-    unsigned int *bar = (unsigned int *)&u.cnt[4];
-    unsigned long long *live_total = &u.cnt[7];
+    unsigned int *bar = (unsigned int *)&A.u[0].cnt[UFC_BAR_ROUNDS];
     unsigned int target = 0;
     if (*(volatile int *)A.status) return;
 #ifdef CR_UF_TIMING
-    if (blockIdx.x == 0 && threadIdx.x == 0) g_uf_trace_n[A.mode] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) g_uf_trace_n = 0;
 #endif
     UF_MARK(0);
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    int64_t ng = (int64_t)*(volatile unsigned long long *)&u.cnt[0];
-    if (ng > u.max_groups) ng = u.max_groups;
-    for (int64_t g = tid; g < ng; g += nthr) {
-        u.gdead[g] = 0;
-        u.hook[g] = (uint32_t)g;
-        u.minE[g] = ~0ull;
+    RoundState R[MAX_GRAPHS];
+#pragma unroll
+    for (int gi = 0; gi < MAX_GRAPHS; gi++) {
+        R[gi] = RoundState{0, false, false, gi >= A.ngraph, 0ull, 0, 0, 0};
+        if (R[gi].done) continue;
+        const UF &u = A.u[gi];
+        int64_t ng = (int64_t)__ldcg(&u.cnt[UFC_GROUPS]);
+        R[gi].ng = ng > u.max_groups ? u.max_groups : ng;
+        for (int64_t g = tid; g < R[gi].ng; g += nthr) {
+            u.gdead[g] = 0;
+            u.hook[g] = (uint32_t)g;
+            u.minE[g] = ~0ull;
+        }
     }
     if (!grid_barrier(bar, target, A.status)) return;
     UF_MARK(1);
-    int64_t ne = (int64_t)__ldcg(&u.cnt[1]);
-    if (ne > u.max_edges) ne = u.max_edges;
-    for (int64_t i = tid; i < ne; i += nthr) {
-        const unsigned long long k = u.ek[0][i];
-        const uint32_t a = u.ea[0][i], b = u.eb[0][i];
-        if (__ldcg(u.minE + a) > k) atomicMin((unsigned long long *)&u.minE[a], k);
-        if (__ldcg(u.minE + b) > k) atomicMin((unsigned long long *)&u.minE[b], k);
+#pragma unroll
+    for (int gi = 0; gi < MAX_GRAPHS; gi++) {
+        if (R[gi].done) continue;
+        const UF &u = A.u[gi];
+        int64_t ne = (int64_t)__ldcg(&u.cnt[UFC_E0]);
+        R[gi].ne = ne > u.max_edges ? u.max_edges : ne;
+        R[gi].live = R[gi].ne;
+        for (int64_t i = tid; i < R[gi].ne; i += nthr) {
+            const unsigned long long k = u.ek[0][i];
+            const uint32_t a = u.ea[0][i], b = u.eb[0][i];
+            if (__ldcg(u.minE + a) > k) atomicMin((unsigned long long *)&u.minE[a], k);
+            if (__ldcg(u.minE + b) > k) atomicMin((unsigned long long *)&u.minE[b], k);
+        }
     }
     if (!grid_barrier(bar, target, A.status)) return;
     UF_MARK(2);
-    int cur = 0;
-    bool inplace = false;
-    unsigned long long live_seen = 0;
-    int64_t live = ne;
     for (int round = 0; round < (1 << 20); round++) {
-        unsigned long long *nnext = cur ? &u.cnt[1] : &u.cnt[2];
-        if (round > 0) {
-            if (inplace) {
-                const unsigned long long v = __ldcg(live_total);
-                live = (int64_t)(v - live_seen);
-                live_seen = v;
-            } else {
-                ne = (int64_t)__ldcg(cur ? &u.cnt[2] : &u.cnt[1]);
-                if (ne > u.max_edges) ne = u.max_edges;
-                live = ne;
-            }
-        }
-        if (live == 0) break;
-        const bool compact = !inplace && ne > nthr;
-        if (tid == 0) {
-            if (compact) *nnext = 0;
-            u.cnt[3] += (unsigned long long)live;  // edges visited, for the algorithmic byte count
-            u.cnt[6] += 1ull;                      // rounds
-        }
-        uint64_t *ek = cur ? u.ek[1] : u.ek[0];
-        uint32_t *ea = cur ? u.ea[1] : u.ea[0], *eb = cur ? u.eb[1] : u.eb[0];
-        // the min-edge buffers alternate every round, the edge buffers only
-        // when the list is compacted
-        const uint64_t *mcur = (round & 1) ? u.minE2 : u.minE;
-        uint64_t *mnext = (round & 1) ? u.minE : u.minE2;
-        // B
-        for (int64_t i = tid; i < ne; i += nthr) {
-            const uint64_t k = ek[i];
-            const uint32_t e0 = ea[i], e1 = eb[i];
-            if (e0 == e1) continue;  // dropped edge (in-place list)
-            const uint64_t m0 = __ldcg(mcur + e0), m1 = __ldcg(mcur + e1);
-            const uint64_t k0 = u.gkey[e0], k1 = u.gkey[e1];
-            // only the younger end can die, and only on its own min edge
-            const bool young0 = k1 < k0;
-            const uint32_t g = young0 ? e0 : e1, t = young0 ? e1 : e0;
-            if ((young0 ? m0 : m1) != k) continue;
-            u.hook[g] = t;
-            u.gdead[g] = 1;
-            u.dkey[g] = k;
-        }
-        for (int64_t g = tid; g < ng; g += nthr) mnext[g] = ~0ull;
-        if (!grid_barrier(bar, target, A.status)) return;
-        UF_MARK(live);
-        // C
-        for (int64_t g = tid; g < ng; g += nthr) {
-            uint32_t p = __ldcg(u.hook + g);
-            if (p == (uint32_t)g) continue;
-            for (int it = 0; it < (1 << 24); it++) {
-                const uint32_t pp = __ldcg(u.hook + p);
-                if (pp == p) break;
-                p = pp;
-                u.hook[g] = p;
-            }
-        }
-        if (!grid_barrier(bar, target, A.status)) return;
-        UF_MARK(live);
-        // D
-        if (compact) {
-            uint64_t *ok = cur ? u.ek[0] : u.ek[1];
-            uint32_t *oa = cur ? u.ea[0] : u.ea[1], *ob = cur ? u.eb[0] : u.eb[1];
-            for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ne; base += nthr) {
-                const int64_t i = base + threadIdx.x;
-                bool keep = false;
-                uint32_t a = 0, b = 0;
-                uint64_t k = 0, ma = 0, mb = 0;
-                if (i < ne) {
-                    a = __ldcg(u.hook + ea[i]);
-                    b = __ldcg(u.hook + eb[i]);
-                    k = ek[i];
-                    keep = a != b;
-                    if (keep) {
-                        ma = __ldcg(mnext + a);
-                        mb = __ldcg(mnext + b);
-                    }
-                }
-                const int64_t j = block_append(keep ? 1 : 0, nnext);
-                if (keep) {
-                    ok[j] = k;
-                    oa[j] = a;
-                    ob[j] = b;
-                    if (ma > k) atomicMin((unsigned long long *)&mnext[a], k);
-                    if (mb > k) atomicMin((unsigned long long *)&mnext[b], k);
+        bool any = false;
+#pragma unroll
+        for (int gi = 0; gi < MAX_GRAPHS; gi++) {
+            RoundState &S = R[gi];
+            if (S.done) continue;
+            const UF &u = A.u[gi];
+            if (round > 0) {
+                if (S.inplace) {
+                    const unsigned long long v = __ldcg(&u.cnt[UFC_LIVE]);
+                    S.live = (int64_t)(v - S.live_seen);
+                    S.live_seen = v;
+                } else {
+                    const int64_t ne = (int64_t)__ldcg(S.cur ? &u.cnt[UFC_E1] : &u.cnt[UFC_E0]);
+                    S.ne = ne > u.max_edges ? u.max_edges : ne;
+                    S.live = S.ne;
                 }
             }
-            cur ^= 1;
-        } else {
-            inplace = true;
-            int nlive = 0;
-            for (int64_t i = tid; i < ne; i += nthr) {
-                const uint32_t e0 = ea[i], e1 = eb[i];
-                const uint64_t k = ek[i];
-                if (e0 == e1) continue;
-                const uint32_t a = __ldcg(u.hook + e0), b = __ldcg(u.hook + e1);
-                if (a == b) {
-                    ea[i] = a;
-                    eb[i] = a;
-                    continue;
-                }
-                const uint64_t ma = __ldcg(mnext + a), mb = __ldcg(mnext + b);
-                if (a != e0) ea[i] = a;
-                if (b != e1) eb[i] = b;
-                if (ma > k) atomicMin((unsigned long long *)&mnext[a], k);
-                if (mb > k) atomicMin((unsigned long long *)&mnext[b], k);
-                nlive++;
+            if (S.live == 0) {
+                S.done = true;
+                continue;
             }
-            nlive = __reduce_add_sync(0xFFFFFFFFu, nlive);
-            if ((threadIdx.x & 31) == 0 && nlive) atomicAdd(live_total, (unsigned long long)nlive);
+            any = true;
+            S.compact = !S.inplace && S.ne > nthr;
+            if (tid == 0) {
+                if (S.compact) *(S.cur ? &u.cnt[UFC_E0] : &u.cnt[UFC_E1]) = 0;
+                u.cnt[UFC_VISITED] += (unsigned long long)S.live;  // for the algorithmic byte count
+                u.cnt[UFC_ROUNDS] += 1ull;
+            }
         }
+        if (!any) break;
+#pragma unroll
+        for (int gi = 0; gi < MAX_GRAPHS; gi++)
+            if (!R[gi].done) phase_B(A.u[gi], R[gi], round, tid, nthr);
         if (!grid_barrier(bar, target, A.status)) return;
-        UF_MARK(live);
+        UF_MARK(R[0].live);
+#pragma unroll
+        for (int gi = 0; gi < MAX_GRAPHS; gi++)
+            if (!R[gi].done) phase_C(A.u[gi], R[gi], tid, nthr);
+        if (!grid_barrier(bar, target, A.status)) return;
+        UF_MARK(R[0].live);
+#pragma unroll
+        for (int gi = 0; gi < MAX_GRAPHS; gi++)
+            if (!R[gi].done) phase_D(A.u[gi], R[gi], round, tid, nthr);
+        if (!grid_barrier(bar, target, A.status)) return;
+        UF_MARK(R[0].live);
     }
 }
 
@@ -1202,121 +1273,132 @@ static int sm_count() {
     return sms;
 }
 
-static int rounds_coop(UF &u, int64_t work_estimate, const Seg *segs, int mode, const PairBuf &pb, uint32_t flags,
-                       uint32_t *extra_mask, int *status, cudaStream_t st) {
-    static int per_sm = 0;
-    if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uf_rounds, UF_THREADS, 0) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-    }
-    int64_t maxb = (int64_t)(per_sm < 1 ? 1 : 1) * sm_count();  // one block per SM keeps barriers short
-    int64_t want = work_estimate / (8 * UF_THREADS) + 1;
-    int blocks = (int)(want < maxb ? want : maxb);
-    if (blocks < 1) blocks = 1;
-    RoundArgs A{u, segs, mode, pb, flags, extra_mask, status};
-    void *args[] = {&A};
-    prof_begin(st, STAGE_UF_ROUND);
-    CR_NOTE_LAUNCH();
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_uf_rounds, dim3(blocks), dim3(UF_THREADS), args, 0, st);
-    prof_end(st, STAGE_UF_ROUND, 0.0);
-    return e == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+// one 1024-thread block per SM at most (short barriers), fewer for small work
+static int coop_blocks(int64_t work) {
+    const int64_t maxb = sm_count();
+    const int64_t want = work / (8 * UF_THREADS) + 1;
+    const int blocks = (int)(want < maxb ? want : maxb);
+    return blocks < 1 ? 1 : blocks;
 }
 
-static int basins_coop(const float *img, const Seg *segs, int nseg, int mode, int64_t n, UF &u, int *status,
-                       cudaStream_t st) {
-    int64_t want = n / (8 * BASIN_THREADS) + 1;
-    int64_t maxb = sm_count();  // one block per SM keeps barriers short
-    int blocks = (int)(want < maxb ? want : maxb);
-    if (blocks < 1) blocks = 1;
-    BasinArgs A{img, segs, nseg, mode, n, u.lab, u.cnt, u.max_groups, u.gkey, u.groot, u.gseg, status};
-    void *args[] = {&A};
-    prof_begin(st, STAGE_JUMP);
-    CR_NOTE_LAUNCH();
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_basins, dim3(blocks), dim3(BASIN_THREADS), args, 0, st);
-    prof_end(st, STAGE_JUMP, 8.0 * (double)n);
-    return e == cudaSuccess ? CR_OK : CR_ERR_CUDA;
-}
-
-int run_h0(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ntiles, UF &u,
-           const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status, cudaStream_t st) {
-    cudaMemsetAsync(u.cnt, 0, UF_CNT * sizeof(unsigned long long), st);
-    prof_begin(st, STAGE_H0_STENCIL);
-    CR_NOTE_LAUNCH();
-    CUtensorMap tmap;
-    const bool flat = hsegs[0].nz == 1;
-    if (nseg == 1 && make_image_map(&tmap, img, hsegs[0], TMA_BX, TMA_BY, flat ? 1 : TMA_BZ)) {
-        if (flat)
-            k_h0_stencil_tma<true><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd,
-                                                                                    status, pb, flags);
-        else
-            k_h0_stencil_tma<false><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd,
-                                                                                     status, pb, flags);
-    } else {
-        k_h0_stencil_tiled<<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(img, segs, nseg, u.lab, u.dd, status,
-                                                                              pb, flags);
+// Union-find for H0 (u0, primal) and the top dimension (u1, dual); either may
+// be null.  The stencils and cross-edge kernels run per graph; basins and
+// rounds run both graphs in one cooperative launch each.
+int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ctot,
+           int64_t ntiles, UF *u0, UF *u1, const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status,
+           cudaStream_t st) {
+    if (u0) cudaMemsetAsync(u0->cnt, 0, UF_CNT * sizeof(unsigned long long), st);
+    if (u1) cudaMemsetAsync(u1->cnt, 0, UF_CNT * sizeof(unsigned long long), st);
+    if (u0) {
+        prof_begin(st, STAGE_H0_STENCIL);
+        CR_NOTE_LAUNCH();
+        CUtensorMap tmap;
+        const bool flat = hsegs[0].nz == 1;
+        if (nseg == 1 && make_image_map(&tmap, img, hsegs[0], TMA_BX, TMA_BY, flat ? 1 : TMA_BZ)) {
+            if (flat)
+                k_h0_stencil_tma<true><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u0->lab,
+                                                                                        u0->dd, status, pb, flags);
+            else
+                k_h0_stencil_tma<false><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u0->lab,
+                                                                                         u0->dd, status, pb, flags);
+        } else {
+            k_h0_stencil_tiled<<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(img, segs, nseg, u0->lab, u0->dd,
+                                                                                  status, pb, flags);
+        }
+        prof_end(st, STAGE_H0_STENCIL, 9.0 * vtot);
     }
-    prof_end(st, STAGE_H0_STENCIL, 9.0 * vtot);
+    if (u1) {
+        prof_begin(st, STAGE_DUAL_STENCIL);
+        CR_NOTE_LAUNCH();
+        CUtensorMap tmap;
+        const int edim = hsegs[0].edim;
+        if (nseg == 1 && (edim == 2 || edim == 3) &&
+            make_image_map(&tmap, img, hsegs[0], DUAL_BX, DUAL_BY, edim == 3 ? DUAL_BZ3 : 1)) {
+            if (edim == 3)
+                k_dual_stencil_tma<3><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u1->lab,
+                                                                                       u1->dd, status, pb, flags);
+            else
+                k_dual_stencil_tma<2><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u1->lab,
+                                                                                       u1->dd, status, pb, flags);
+        } else {
+            k_dual_stencil<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u1->lab, u1->dd, pb,
+                                                                         flags);
+        }
+        prof_end(st, STAGE_DUAL_STENCIL, 4.0 * vtot + 5.0 * ctot);
+    }
+    // basins of both graphs
     {
-        int rc = basins_coop(img, segs, nseg, 0, vtot, u, status, st);
-        if (rc) return rc;
+        BasinArgs A{};
+        A.img = img;
+        A.segs = segs;
+        A.nseg = nseg;
+        A.status = status;
+        int64_t work = 0;
+        for (UF *u : {u0, u1}) {
+            if (!u) continue;
+            const int k = A.ngraph++;
+            A.u[k] = *u;
+            A.mode[k] = u == u0 ? 0 : 1;
+            A.n[k] = u == u0 ? vtot : ctot;
+            work = A.n[k] > work ? A.n[k] : work;
+        }
+        void *args[] = {&A};
+        prof_begin(st, STAGE_JUMP);
+        CR_NOTE_LAUNCH();
+        cudaError_t e = cudaLaunchCooperativeKernel((void *)k_basins, dim3(coop_blocks(work)), dim3(BASIN_THREADS),
+                                                    args, 0, st);
+        prof_end(st, STAGE_JUMP, 8.0 * (double)((u0 ? vtot : 0) + (u1 ? ctot : 0)));
+        if (e != cudaSuccess) return CR_ERR_CUDA;
     }
-    prof_begin(st, STAGE_H0_CROSS);
-    CR_NOTE_LAUNCH();
-    k_h0_cross<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, u.ek[0], u.ea[0],
-                                                             u.eb[0], &u.cnt[1], u.max_edges, &u.cnt[0], status);
-    prof_end(st, STAGE_H0_CROSS, 9.0 * vtot);
-    int rc = rounds_coop(u, vtot, segs, 0, pb, flags, extra_mask, status, st);
-    if (rc) return rc;
-    CR_NOTE_LAUNCH();
-    k_uf_emit<<<2 * sm_count(), 256, 0, st>>>(&u.cnt[0], u, 0, segs, pb, flags, extra_mask);
-    return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
-}
-
-int run_dual(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ctot,
-             int64_t ntiles, UF &u,
-             const PairBuf &pb, uint32_t flags, int *status, cudaStream_t st) {
-    cudaMemsetAsync(u.cnt, 0, UF_CNT * sizeof(unsigned long long), st);
-    prof_begin(st, STAGE_DUAL_STENCIL);
-    CR_NOTE_LAUNCH();
-    CUtensorMap tmap;
-    const int edim = hsegs[0].edim;
-    if (nseg == 1 && (edim == 2 || edim == 3) &&
-        make_image_map(&tmap, img, hsegs[0], DUAL_BX, DUAL_BY, edim == 3 ? DUAL_BZ3 : 1)) {
-        if (edim == 3)
-            k_dual_stencil_tma<3><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd, status,
-                                                                                   pb, flags);
-        else
-            k_dual_stencil_tma<2><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u.lab, u.dd, status,
-                                                                                   pb, flags);
-    } else {
-        k_dual_stencil<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, pb, flags);
+    if (u0) {
+        prof_begin(st, STAGE_H0_CROSS);
+        CR_NOTE_LAUNCH();
+        k_h0_cross<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u0->lab, u0->dd, u0->ek[0],
+                                                                 u0->ea[0], u0->eb[0], &u0->cnt[UFC_E0],
+                                                                 u0->max_edges, &u0->cnt[UFC_GROUPS], status);
+        prof_end(st, STAGE_H0_CROSS, 9.0 * vtot);
     }
-    prof_end(st, STAGE_DUAL_STENCIL, 4.0 * vtot + 5.0 * ctot);
+    if (u1) {
+        prof_begin(st, STAGE_DUAL_CROSS);
+        CR_NOTE_LAUNCH();
+        k_dual_cross<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u1->lab, u1->dd, u1->ek[0],
+                                                                   u1->ea[0], u1->eb[0], &u1->cnt[UFC_E0],
+                                                                   u1->max_edges, &u1->cnt[UFC_GROUPS], status);
+        prof_end(st, STAGE_DUAL_CROSS, 4.0 * vtot + 5.0 * ctot);
+    }
+    // rounds of both graphs
     {
-        int rc = basins_coop(img, segs, nseg, 1, ctot, u, status, st);
-        if (rc) return rc;
+        RoundArgs A{};
+        A.status = status;
+        for (UF *u : {u0, u1})
+            if (u) A.u[A.ngraph++] = *u;
+        void *args[] = {&A};
+        prof_begin(st, STAGE_UF_ROUND);
+        CR_NOTE_LAUNCH();
+        cudaError_t e = cudaLaunchCooperativeKernel((void *)k_uf_rounds, dim3(coop_blocks(vtot)), dim3(UF_THREADS),
+                                                    args, 0, st);
+        prof_end(st, STAGE_UF_ROUND, 0.0);
+        if (e != cudaSuccess) return CR_ERR_CUDA;
     }
-    prof_begin(st, STAGE_DUAL_CROSS);
-    CR_NOTE_LAUNCH();
-    k_dual_cross<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(img, segs, nseg, u.lab, u.dd, u.ek[0], u.ea[0],
-                                                               u.eb[0], &u.cnt[1], u.max_edges, &u.cnt[0], status);
-    prof_end(st, STAGE_DUAL_CROSS, 4.0 * vtot + 5.0 * ctot);
-    int rc = rounds_coop(u, vtot, segs, 1, pb, flags, nullptr, status, st);
-    if (rc) return rc;
-    CR_NOTE_LAUNCH();
-    k_uf_emit<<<2 * sm_count(), 256, 0, st>>>(&u.cnt[0], u, 1, segs, pb, flags, nullptr);
+    if (u0) {
+        CR_NOTE_LAUNCH();
+        k_uf_emit<<<2 * sm_count(), 256, 0, st>>>(&u0->cnt[UFC_GROUPS], *u0, 0, segs, pb, flags, extra_mask);
+    }
+    if (u1) {
+        CR_NOTE_LAUNCH();
+        k_uf_emit<<<2 * sm_count(), 256, 0, st>>>(&u1->cnt[UFC_GROUPS], *u1, 1, segs, pb, flags, nullptr);
+    }
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
 }  // namespace cr
 
 #ifdef CR_UF_TIMING
-extern "C" int cr_debug_uf_trace(int mode, unsigned long long *out, int cap) {
+extern "C" int cr_debug_uf_trace(unsigned long long *out, int cap) {
     int n = 0;
-    cudaMemcpyFromSymbol(&n, cr::g_uf_trace_n, sizeof(int), mode * sizeof(int));
+    cudaMemcpyFromSymbol(&n, cr::g_uf_trace_n, sizeof(int));
     if (n > cap) n = cap;
-    cudaMemcpyFromSymbol(out, cr::g_uf_trace, n * sizeof(unsigned long long), mode * 1024 * sizeof(unsigned long long));
+    cudaMemcpyFromSymbol(out, cr::g_uf_trace, n * sizeof(unsigned long long));
     return n;
 }
 #endif
