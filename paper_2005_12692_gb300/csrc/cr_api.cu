@@ -25,6 +25,7 @@ struct HostPlan {
     int64_t vtot = 0, ctot = 0, cells = 0, ntiles = 0;
     int64_t max_face_per_image = 0;
     bool any_h0 = false, any_dual = false, any_mid = false;
+    bool serial_uf = false;  // run the two union-finds one after the other (half the region)
     int nseg_bits = 0;
 };
 
@@ -137,7 +138,7 @@ static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
         for (const Seg &S : P.segs) edim = S.edim > edim ? S.edim : edim;
         uf = al((size_t)nodes * 16) + al((size_t)P.vtot * (edim == 3 && P.any_dual ? 96 : 48)) + (8 << 20);
     }
-    if (P.any_h0 && P.any_dual) uf *= 2;  // both union-finds are live at once
+    if (P.any_h0 && P.any_dual && !P.serial_uf) uf *= 2;  // both union-finds are live at once
     if (P.any_mid) {
         int64_t nw;
         int ml;
@@ -336,7 +337,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     // ---- H0 and the top dimension by duality: two independent union-finds,
     // run side by side in halves of the region ----
     if (P.any_h0 || P.any_dual) {
-        const bool both = P.any_h0 && P.any_dual;
+        const bool both = P.any_h0 && P.any_dual && !P.serial_uf;
         const size_t half = both ? (region_cap / 2) & ~(size_t)255 : region_cap;
         UF uh, ud;
         if (P.any_h0) {
@@ -347,6 +348,11 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
             uh.cnt = &cnt[CNT_H0];
             uh.hcnt = hc;
         }
+        if (P.any_h0 && !both) {
+            rc = run_uf(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, &uh, nullptr, pb, flags,
+                        P.any_mid ? extra : nullptr, status, st);
+            if (rc) return rc;
+        }
         if (P.any_dual) {
             rc = carve_uf(region + (both ? half : 0), both ? region_cap - half : region_cap, P.ctot, P.vtot, ud);
             if (rc) return rc;
@@ -355,9 +361,11 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
             ud.cnt = &cnt[CNT_DUAL];
             ud.hcnt = hc;
         }
-        rc = run_uf(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, P.any_h0 ? &uh : nullptr,
-                    P.any_dual ? &ud : nullptr, pb, flags, P.any_mid ? extra : nullptr, status, st);
-        if (rc) return rc;
+        if (both || P.any_dual) {
+            rc = run_uf(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, both ? &uh : nullptr, &ud, pb,
+                        flags, both && P.any_mid ? extra : nullptr, status, st);
+            if (rc) return rc;
+        }
     }
 
     // ---- middle dimension of volumes ----
@@ -623,6 +631,30 @@ static int plan_batched(const int32_t *shapes, int n_images, int ndim, int maxdi
     }
     return plan_images(rows.data(), n_images, ndim, maxdim, flags, P);
 }
+
+namespace cr {
+// single image with the two union-finds run one after the other, so that the
+// workspace bound is that of one of them (used by the no-alloc entry point)
+int workspace_size_serial(int ndim, const int64_t *shape, int maxdim, uint32_t flags, size_t *bytes) {
+    if (!bytes) return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_single(ndim, shape, maxdim, flags, P);
+    if (rc) return rc;
+    P.serial_uf = true;
+    *bytes = total_bytes(P, flags, true);
+    return CR_OK;
+}
+int persistence_serial(const float *img, int ndim, const int64_t *shape, int maxdim, cr_pair *pairs_out,
+                       int64_t capacity, int64_t *n_pairs, void *ws, size_t ws_bytes, cudaStream_t stream,
+                       uint32_t flags) {
+    if (!img || !n_pairs || capacity < 0 || (capacity > 0 && !pairs_out)) return CR_ERR_INVALID_ARG;
+    HostPlan P;
+    int rc = plan_single(ndim, shape, maxdim, flags, P);
+    if (rc) return rc;
+    P.serial_uf = true;
+    return pipeline(img, P, maxdim, flags, pairs_out, capacity, nullptr, n_pairs, ws, ws_bytes, stream);
+}
+}  // namespace cr
 
 extern "C" {
 

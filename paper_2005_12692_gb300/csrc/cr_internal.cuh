@@ -282,6 +282,13 @@ struct UF {
     unsigned long long *cnt;   // device counters [0] groups, [1] edges, [2] edges after a round
     unsigned long long *hcnt;  // host mirror
 };
+// single-image persistence with the two union-finds run one after the other
+// (a workspace bound of one union-find; cr_api.cu)
+int workspace_size_serial(int ndim, const int64_t *shape, int maxdim, uint32_t flags, size_t *bytes);
+int persistence_serial(const float *img, int ndim, const int64_t *shape, int maxdim, cr_pair *pairs_out,
+                       int64_t capacity, int64_t *n_pairs, void *ws, size_t ws_bytes, cudaStream_t stream,
+                       uint32_t flags);
+
 // union-find of H0 (u0, primal graph) and of the top dimension (u1, dual
 // graph); either may be null
 int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ctot,

@@ -48,13 +48,13 @@ extern "C" int cr_persistence_noalloc(const float *img, int ndim, const int64_t 
     for (int d = 0; d + 2 < ndim; d++)
         if (shape[d] > 1) return CR_ERR_INVALID_ARG;
     size_t need = 0;
-    int rc = cr_workspace_size(ndim, shape, maxdim, flags, &need);
+    int rc = cr::workspace_size_serial(ndim, shape, maxdim, flags, &need);
     if (rc) return rc;
     if (need > CR_NOALLOC_BYTES_) return CR_ERR_TOO_LARGE;
     void *ws = nullptr;
     rc = scratch_for_current_device(&ws);
     if (rc) return rc;
     // every buffer the pipeline relies on being zero is cleared by the pipeline itself
-    return cr_persistence(img, ndim, shape, maxdim, pairs_out, capacity, n_pairs, ws, (size_t)CR_NOALLOC_BYTES_,
-                          stream, flags);
+    return cr::persistence_serial(img, ndim, shape, maxdim, pairs_out, capacity, n_pairs, ws,
+                                  (size_t)CR_NOALLOC_BYTES_, (cudaStream_t)stream, flags);
 }
