@@ -212,7 +212,7 @@ __global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, uint64
 // ---------------------------------------------------------------------------
 constexpr int SC_DX = 48, SC_DY = TILE_Y + 1, SC_DZ = TILE_Z + 1;  // hook-code box (x0..x0+47)
 constexpr int SC_DD_BYTES = SC_DX * SC_DY * SC_DZ;
-constexpr int SC_CAP = 1536;  // residual columns buffered per tile (at most 3 per voxel per plane)
+constexpr int SC_WCAP = 192;  // residual columns buffered per warp (a plane adds at most 96)
 constexpr int SCAN_DYN_SMEM = TMA_BYTES + SC_DD_BYTES + 128;
 static_assert(TMA_BYTES % 128 == 0, "hook-code box must start on a 128-byte boundary");
 
@@ -229,9 +229,11 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
     uint8_t(*dds)[SC_DY][SC_DX] = reinterpret_cast<uint8_t(*)[SC_DY][SC_DX]>(dyn + TMA_BYTES);
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t ext[3][TILE_Z][TILE_Y][2];          // death-mask words of each edge row
-    __shared__ uint32_t app[3][TILE_Z + 1][TILE_Y + 1][2];  // apparent pivots, face rows from y0-1, z0-1
-    __shared__ uint64_t cbuf[SC_CAP];                       // residual columns of the tile
-    __shared__ int cn;
+    // apparent pivots, face rows from y0-1, z0-1: slots 0-2 = face types 0-2, slot 3 = type 0 marked from
+    // the -y side (so that every (slot, row) is written by one warp only, without atomics)
+    __shared__ uint32_t app[4][TILE_Z + 1][TILE_Y + 1][2];
+    __shared__ uint64_t cbuf[TILE_Y][SC_WCAP];  // residual columns, one run per warp
+    __shared__ int s_wn[TILE_Y];
     __shared__ unsigned long long cbase;
     const Seg S = segs[0];
     const int nx = S.nx, ny = S.ny, nz = S.nz;
@@ -278,9 +280,8 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         ext[ax][dz][dy][0] = w0;
         ext[ax][dz][dy][1] = w1;
     }
-    for (int i = threadIdx.x; i < 3 * (TILE_Z + 1) * (TILE_Y + 1) * 2; i += TILE_X * TILE_Y)
+    for (int i = threadIdx.x; i < 4 * (TILE_Z + 1) * (TILE_Y + 1) * 2; i += TILE_X * TILE_Y)
         (&app[0][0][0][0])[i] = 0u;
-    if (threadIdx.x == 0) cn = 0;
     __syncthreads();
     // the wait's outcome is made uniform so that no thread is left at a later barrier
     if (!__syncthreads_and(mbar_wait(&bar, 1ll << 24))) {
@@ -298,6 +299,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
     const bool keep_zero = (flags & CR_KEEP_ZERO) != 0;
     const uint32_t lo = (uint32_t)S.loff;  // only its low bits matter for positions within mask words
     const bool hx = x + 1 < nx, hy = y + 1 < ny, my = y > 0;
+    int wn = 0;  // entries in this warp's run of residual columns (the same in every lane)
     // Values of this thread's column roll through registers: f(x,y,z), f(x+1,y,z),
     // f(x,y+1,z) and the x- and y-edge values of planes z-1, z (and z+1 once read).
     // Out-of-image entries of the box are zero and never decide anything: each
@@ -387,16 +389,17 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
             const unsigned m3 = __ballot_sync(0xFFFFFFFFu, sx == 3), m4 = __ballot_sync(0xFFFFFFFFu, sx == 4);
             const unsigned m5 = __ballot_sync(0xFFFFFFFFu, sy == 1), m6 = __ballot_sync(0xFFFFFFFFu, sy == 2);
             if (lane < 6) {
-                // lane k: x-edge +z, -z (type 1), +y, -y (type 0); y-edge +z, -z (type 2)
+                // lane k: x-edge +z, -z (type 1), +y, -y (type 0, slot 3); y-edge +z, -z (type 2)
                 const unsigned msk = lane == 0 ? m1 : lane == 1 ? m2 : lane == 2 ? m3 : lane == 3 ? m4 : lane == 4 ? m5 : m6;
                 if (msk) {
                     const int m = lane < 2 ? 1 : (lane < 4 ? 0 : 2);
+                    const int slot = lane == 3 ? 3 : m;
                     const int dzf = (lane == 1 || lane == 5) ? -1 : 0, dyf = lane == 3 ? -1 : 0;
                     const uint32_t fr = (uint32_t)m * P + rowL + (uint32_t)(dzf * (int)plane + dyf * nx);
                     const int off = (int)((lo + fr) & 31u);
-                    uint32_t *w = &app[m][zz + 1 + dzf][ty + 1 + dyf][0];
-                    atomicOr(w, msk << off);
-                    if (off) atomicOr(w + 1, msk >> (32 - off));
+                    uint32_t *w = &app[slot][zz + 1 + dzf][ty + 1 + dyf][0];
+                    w[0] |= msk << off;
+                    if (off) w[1] |= msk >> (32 - off);
                 }
             }
         }
@@ -407,55 +410,75 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         exc = exn;
         eyp = eyc;
         eyc = eyn;
-        // residual columns: a warp reserves its run in the tile buffer with one
-        // shared atomic; the buffer goes out with one global reservation when
-        // the next plane could overflow it, and at the end of the tile
+        // residual columns: appended to the warp's run in shared memory (no block
+        // barrier per plane); a run that could overflow goes out with its own
+        // global reservation, the rest with one reservation per tile
         const int cnt = (int)colx + (int)coly + (int)colz;
         const unsigned b0 = __ballot_sync(0xFFFFFFFFu, cnt & 1), b1 = __ballot_sync(0xFFFFFFFFu, cnt & 2);
         const int total = __popc(b0) + 2 * __popc(b1);
         if (total) {
-            const unsigned lt = (1u << lane) - 1u;
-            int wb = 0;
-            if (lane == 0) wb = atomicAdd(&cn, total);
-            wb = __shfl_sync(0xFFFFFFFFu, wb, 0);
-            int j = wb + __popc(b0 & lt) + 2 * __popc(b1 & lt);
-            if (colx) cbuf[j++] = ~make_key(ord32(fsx), lv);
-            if (coly) cbuf[j++] = ~make_key(ord32(fsy), lv + P);
-            if (colz) cbuf[j++] = ~make_key(ord32(fsz), lv + 2u * P);
-        }
-        __syncthreads();
-        const int n = cn;
-        if (n > SC_CAP - 3 * TILE_X * TILE_Y || (zz == zend - 1 && n > 0)) {
-            if (threadIdx.x == 0) cbase = atomicAdd(ncol, (unsigned long long)n);
-            __syncthreads();
-            const int64_t b0g = (int64_t)cbase;
-            if (b0g + n > max_cols) {
-                if (threadIdx.x == 0) fail_ws(status, SITE_COLUMNS);
-            } else {
-                for (int i = threadIdx.x; i < n; i += TILE_X * TILE_Y) {
-                    colkey[b0g + i] = cbuf[i];
-                    colseg[b0g + i] = 0u;
+            if (wn + total > SC_WCAP) {
+                __syncwarp();
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(ncol, (unsigned long long)wn);
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if ((int64_t)base + wn > max_cols) {
+                    if (lane == 0) fail_ws(status, SITE_COLUMNS);
+                } else {
+                    for (int i = lane; i < wn; i += 32) {
+                        colkey[base + i] = cbuf[ty][i];
+                        colseg[base + i] = 0u;
+                    }
                 }
+                __syncwarp();
+                wn = 0;
             }
-            __syncthreads();
-            if (threadIdx.x == 0) cn = 0;
-            __syncthreads();
+            const unsigned lt = (1u << lane) - 1u;
+            int j = wn + __popc(b0 & lt) + 2 * __popc(b1 & lt);
+            if (colx) cbuf[ty][j++] = ~make_key(ord32(fsx), lv);
+            if (coly) cbuf[ty][j++] = ~make_key(ord32(fsy), lv + P);
+            if (colz) cbuf[ty][j++] = ~make_key(ord32(fsz), lv + 2u * P);
+            wn += total;
+        }
+    }
+    // the tile's remaining runs: one global reservation
+    if (lane == 0) s_wn[ty] = wn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < TILE_Y; w++) t += s_wn[w];
+        cbase = t ? atomicAdd(ncol, (unsigned long long)t) : 0ull;
+    }
+    __syncthreads();
+    {
+        int before = 0, t = 0;
+        for (int w = 0; w < TILE_Y; w++) {
+            if (w < ty) before += s_wn[w];
+            t += s_wn[w];
+        }
+        const int64_t b0g = (int64_t)cbase;
+        if (b0g + t > max_cols) {
+            if (threadIdx.x == 0 && t) fail_ws(status, SITE_COLUMNS);
+        } else {
+            for (int i = lane; i < wn; i += 32) {
+                colkey[b0g + before + i] = cbuf[ty][i];
+                colseg[b0g + before + i] = 0u;
+            }
         }
     }
     __syncthreads();
     // merge the tile's apparent pivots into the global mask, one atomic per nonzero word
     for (int i = threadIdx.x; i < 3 * (TILE_Z + 1) * (TILE_Y + 1) * 2; i += TILE_X * TILE_Y) {
-        const uint32_t w = (&app[0][0][0][0])[i];
-        if (!w) continue;
         const int half = i & 1, r = i >> 1;
         const int dy = r % (TILE_Y + 1), r2 = r / (TILE_Y + 1);
         const int dz = r2 % (TILE_Z + 1), m = r2 / (TILE_Z + 1);
+        const uint32_t w = app[m][dz][dy][half] | (m == 0 ? app[3][dz][dy][half] : 0u);
+        if (!w) continue;
         const int64_t r0 = S.loff + (int64_t)m * P + (int64_t)(z0 - 1 + dz) * plane + (int64_t)(y0 - 1 + dy) * nx + x0;
         atomicOr(&I.appmask[(r0 >> 5) + half], w);
     }
 }
 
-// ---------------------------------------------------------------------------
 // 2. lock-free reduction
 // ---------------------------------------------------------------------------
 struct RedParams {
