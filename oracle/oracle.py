@@ -26,6 +26,9 @@ Contents, each following the paper (Kaji, Sudo, Ahara, "Cubical Ripser"):
                           dL/ddeath: each is routed to the vertex that attains
                           the cell's value (maximum vertex in the filtration
                           order), summed in double.
+* ``lifetime_image``, ``persistent_histogram_image`` -- the localised-feature
+                          images of Sec. 4 (largest lifetime, or a (birth,
+                          lifetime) histogram, of the pairs located at each voxel).
 """
 from __future__ import annotations
 
@@ -398,3 +401,65 @@ def euler_characteristic(img, t: float) -> int:
         if val <= t:
             chi += (-1) ** dim
     return chi
+
+
+# ---------------------------------------------------------------------------
+# Localised features (Sec. 4, the example on localised features): images
+# built from the pairs and the locations of their cells
+# ---------------------------------------------------------------------------
+def _location_pixel(L: int, shape) -> int:
+    """Linear index of the voxel at which the cell with L-index ``L`` is
+    anchored (its (x, y, z) location; the cell type m is dropped)."""
+    nz, ny, nx = _canon(shape)
+    _, z, y, x = _decode(L, shape)
+    return (z * ny + y) * nx + x
+
+
+def lifetime_image(shape, pairs, location: str = "birth") -> np.ndarray:
+    """Lifetime channels of the lifetime enhanced image: channel d (d < ndim)
+    holds at each voxel the largest lifetime death - birth (float32
+    subtraction) of the finite pairs of dimension d located there, 0 where
+    there is none.  The location of a pair is the anchor voxel of its birth
+    cell (or of its death cell, ``location="death"``).  Essential pairs have no
+    finite lifetime and are left out."""
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    out = np.zeros((nd, int(np.prod(shape))), dtype=np.float32)
+    for k in range(len(pairs)):
+        death = np.float32(pairs["death"][k])
+        if not np.isfinite(death):
+            continue
+        d = int(pairs["dim"][k])
+        L = int(pairs["birth_L"][k] if location == "birth" else pairs["death_L"][k])
+        v = _location_pixel(L, shape)
+        life = np.float32(death - np.float32(pairs["birth"][k]))
+        if life > out[d, v]:
+            out[d, v] = life
+    return out.reshape((nd,) + shape)
+
+
+def persistent_histogram_image(shape, pairs, nb: int, b_lo: float, b_hi: float, nl: int, l_hi: float,
+                               location: str = "birth") -> np.ndarray:
+    """Persistent histogram image: for each voxel, per dimension d, the 2D
+    histogram of (birth, lifetime) of the finite pairs located at the voxel,
+    flattened into channels ((d * nb + i) * nl + j).  Bin i of birth covers
+    [b_lo + i w, b_lo + (i+1) w), w = (b_hi - b_lo) / nb, computed as
+    floor((birth - b_lo) / (b_hi - b_lo) * nb) in double; lifetime bin j is
+    floor(lifetime / l_hi * nl) with lifetime = death - birth in double.
+    Pairs outside [b_lo, b_hi) x [0, l_hi) are not counted."""
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    out = np.zeros((nd * nb * nl, int(np.prod(shape))), dtype=np.float32)
+    for k in range(len(pairs)):
+        death = float(pairs["death"][k])
+        if not np.isfinite(death):
+            continue
+        birth = float(pairs["birth"][k])
+        i = int(np.floor((birth - float(b_lo)) / (float(b_hi) - float(b_lo)) * nb))
+        j = int(np.floor((death - birth) / float(l_hi) * nl))
+        if i < 0 or i >= nb or j < 0 or j >= nl:
+            continue
+        d = int(pairs["dim"][k])
+        L = int(pairs["birth_L"][k] if location == "birth" else pairs["death_L"][k])
+        out[(d * nb + i) * nl + j, _location_pixel(L, shape)] += 1.0
+    return out.reshape((nd * nb * nl,) + shape)

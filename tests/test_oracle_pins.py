@@ -200,3 +200,62 @@ def test_uniform64_golden(oracle_mod):
     exp = sorted((d, float(np.float32(b)), float(np.float32(e)), bl, dl) for d, b, e, bl, dl in
                  read_pairs("uniform64_pairs.txt"))
     assert got == exp
+
+
+# ---------------------------------------------------------------------------
+# localised-feature images (Sec. 4, the example on localised features)
+# ---------------------------------------------------------------------------
+def test_lifetime_image_hand_1d(oracle_mod):
+    # f = [0, 2, 1, 3]: the component born at 1 (vertex 2) dies at value 2 when
+    # the edge (0,1) enters; the equal-valued edge (1,2) enters first (larger L)
+    # and kills the younger vertex 1 at zero length.
+    f = np.array([0, 2, 1, 3], np.float32)
+    p = oracle_mod.persistence(f)
+    assert np.array_equal(oracle_mod.lifetime_image(f.shape, p), [[0, 0, 1, 0]])
+    assert np.array_equal(oracle_mod.lifetime_image(f.shape, p, "death"), [[1, 0, 0, 0]])
+
+
+def test_lifetime_and_histogram_images_hand_2d(oracle_mod):
+    # a 3x4 plateau of 5 with two wells: 0 at (y=1, x=1) lives forever, 1 at
+    # (y=1, x=3) dies at 5 -> lifetime 4 located at row 1, column 3; every other
+    # class is born and killed at 5.
+    img = np.array([[5, 5, 5, 5], [5, 0, 5, 1], [5, 5, 5, 5]], np.float32)
+    p = oracle_mod.persistence(img)
+    p = p[p["death"] > p["birth"]]
+    li = oracle_mod.lifetime_image(img.shape, p)
+    exp = np.zeros((2, 3, 4), np.float32)
+    exp[0, 1, 3] = 4.0
+    assert np.array_equal(li, exp)
+    # birth bins of width 2 on [0, 8), lifetime bins of width 2 on [0, 8): the
+    # pair (1, 5) falls in birth bin 0 and lifetime bin 2 -> channel 2
+    h = oracle_mod.persistent_histogram_image(img.shape, p, 4, 0.0, 8.0, 4, 8.0)
+    assert h.shape == (2 * 4 * 4, 3, 4)
+    assert np.argwhere(h).tolist() == [[2, 1, 3]] and h[2, 1, 3] == 1.0
+
+
+def test_localised_images_invariants(oracle_mod):
+    # on random tie-heavy 2D/3D inputs: channel d's maximum is the largest finite
+    # lifetime of dimension d; a histogram spanning every pair counts each finite
+    # pair once, at the voxel of its birth cell
+    rng = np.random.default_rng(31)
+    for shape in [(7, 9), (4, 5, 6)]:
+        img = rng.integers(0, 6, size=shape).astype(np.float32)
+        p = oracle_mod.persistence(img)
+        for loc, key in (("birth", "birth_L"), ("death", "death_L")):
+            li = oracle_mod.lifetime_image(shape, p, loc)
+            for d in range(len(shape)):
+                sel = (p["dim"] == d) & np.isfinite(p["death"])
+                m = float((p["death"][sel] - p["birth"][sel]).max()) if sel.any() else 0.0
+                assert float(li[d].max()) == m
+        h = oracle_mod.persistent_histogram_image(shape, p, 3, -1.0, 7.0, 2, 8.0)
+        fin = np.isfinite(p["death"])
+        assert h.sum() == fin.sum()
+        for d in range(len(shape)):
+            per_voxel = h[d * 6:(d + 1) * 6].sum(axis=0).reshape(-1)
+            sel = fin & (p["dim"] == d)
+            cnt = np.zeros(per_voxel.size)
+            for L in p["birth_L"][sel]:
+                m, z, y, x = oracle_mod.oracle._decode(int(L), shape)
+                nz, ny, nx = oracle_mod.oracle._canon(shape)
+                cnt[(z * ny + y) * nx + x] += 1
+            assert np.array_equal(per_voxel, cnt)
