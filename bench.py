@@ -476,6 +476,36 @@ def main():
         plain = {"images_per_s": sub / (pms / 1e3), "sample": "first %d images, same loss" % sub,
                  "batched_over_plain": value / (sub / (pms / 1e3))}
 
+    # the localised-feature images (Sec. 4) from one call's pairs, timed alone
+    images = None
+    if W["kind"] == "single":
+        pr = step()
+        shp = tuple(data.shape)
+        nd = len(shp)
+        vox = int(np.prod(shp))
+        lo, hi = float(data.min()), float(data.max())
+        for _ in range(3):
+            cr.lifetime_image(shp, pr)
+            cr.persistent_histogram_image(shp, pr, 8, (lo, hi), 8, hi - lo)
+        reps = 20
+        res = {}
+        for name, fn, nbytes in (
+                ("lifetime_image", lambda: cr.lifetime_image(shp, pr), 4.0 * nd * vox + 32.0 * pr.n),
+                ("histogram_image_8x8", lambda: cr.persistent_histogram_image(shp, pr, 8, (lo, hi), 8, hi - lo),
+                 4.0 * nd * 64 * vox + 32.0 * pr.n)):
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / reps
+            res[name] = {"ms": ms, "algorithmic_bytes": nbytes, "gbs": nbytes / (ms / 1e3) / 1e9}
+        images = {"pairs": pr.n, **res,
+                  "note": "output zero-fill + one scatter per pair; inputs in HBM; not part of the timed step"}
+
     peaks = load_peaks()
     roof = roofline_from({roof_stage: timed_stages[roof_stage]} if roof_stage in timed_stages else stages, peaks)
 
@@ -493,6 +523,7 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
             "plain_path": plain,
+            "localised_images": images,
             "stages": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps}
                        for k, v in stages.items()},
             "stages_note": "separate profiled pass of %d steps (events around every stage)" % prof_steps}

@@ -155,6 +155,35 @@ int cr_backward_batched(const float *imgs, const int64_t *img_offsets, const int
                         const float *grad_birth, const float *grad_death, float *grad_imgs, void *ws,
                         size_t ws_bytes, cr_stream_t stream);
 
+/* Localised-feature images (Sec. 4, the example on localised features).
+ * The location of a pair is the anchor voxel (x, y, z) of its birth cell
+ * (location = 0) or of its death cell (location = 1), i.e. the cell's L-index
+ * with the type dropped.  Essential pairs (infinite death) are left out.
+ *
+ * cr_lifetime_image: out[d * V + v], d < ndim, V = prod(shape), is the
+ *   largest lifetime death - birth (float32 subtraction) of the pairs of
+ *   dimension d located at voxel v, 0 where there is none: the lifetime
+ *   channels of the paper's lifetime enhanced image (stacked with the image
+ *   itself by the caller).
+ * cr_persistent_histogram_image: out[((d * nb + i) * nl + j) * V + v] counts
+ *   the pairs of dimension d located at v whose birth falls in bin
+ *   i = floor((birth - b_lo) / (b_hi - b_lo) * nb) and whose lifetime falls in
+ *   bin j = floor((death - birth) / l_hi * nl), both computed in double; pairs
+ *   with i outside [0, nb) or j outside [0, nl) are not counted.
+ *
+ *   pairs   device cr_pair[n_pairs] of one image (as from cr_persistence)
+ *   shape   host int64[ndim], the image's shape (C order)
+ *   out     device float32, ndim * V (lifetime) or ndim * nb * nl * V
+ *           (histogram) values; zero-filled by the call
+ * Asynchronous on `stream`.  Errors: CR_ERR_INVALID_ARG (ndim not 1-3, an
+ * extent < 1, location not 0/1, nb or nl < 1, b_hi <= b_lo, l_hi <= 0, a null
+ * buffer that is needed), CR_ERR_CUDA. */
+int cr_lifetime_image(const cr_pair *pairs, int64_t n_pairs, int ndim, const int64_t *shape, int location,
+                      float *out, cr_stream_t stream);
+int cr_persistent_histogram_image(const cr_pair *pairs, int64_t n_pairs, int ndim, const int64_t *shape,
+                                  int location, int nb, double b_lo, double b_hi, int nl, double l_hi, float *out,
+                                  cr_stream_t stream);
+
 /* Anchor (x, y, z) and type m of the cube (dim, L) of an image of this shape
  * (the paper's cell tuple (x, y, z, m, d), Sec. 2).  Host-only. */
 int cr_cell_location(int64_t L, int dim, int ndim, const int64_t *shape, int *m, int64_t *x, int64_t *y,
@@ -190,7 +219,7 @@ int cr_persistence_noalloc(const float *img, int ndim, const int64_t *shape, int
 
 /* Diagnostics for benchmarks.  With profiling on, every stage of a call is
  * bracketed by CUDA events recorded on the caller's stream; totals per stage
- * are read with cr_profile_read (stage 0..15; name, total milliseconds,
+ * are read with cr_profile_read (stage 0..16; name, total milliseconds,
  * number of timed launches, algorithmic bytes the stage must move).  Returns
  * CR_ERR_INVALID_ARG past the last stage.  cr_profile_select restricts the
  * events to the stages whose bit is set in stage_mask (bit s = stage s;

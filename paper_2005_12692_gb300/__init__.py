@@ -83,6 +83,10 @@ def lib() -> ctypes.CDLL:
                                           vp, vp, vp, ctypes.c_size_t, vp]
         L.cr_cell_location.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, i64p,
                                        ctypes.POINTER(ctypes.c_int), i64p, i64p, i64p]
+        L.cr_lifetime_image.argtypes = [vp, ctypes.c_int64, ctypes.c_int, i64p, ctypes.c_int, vp, vp]
+        L.cr_persistent_histogram_image.argtypes = [vp, ctypes.c_int64, ctypes.c_int, i64p, ctypes.c_int,
+                                                    ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                    ctypes.c_double, vp, vp]
         L.cr_profile_enable.argtypes = [ctypes.c_int]
         L.cr_profile_enable.restype = ctypes.c_int
         L.cr_profile_select.argtypes = [ctypes.c_uint32]
@@ -100,7 +104,8 @@ def lib() -> ctypes.CDLL:
         L.cr_error_string.argtypes = [ctypes.c_int]
         for f in ("cr_workspace_size", "cr_workspace_size_typical", "cr_workspace_size_batched",
                   "cr_workspace_size_batched_typical", "cr_persistence", "cr_persistence_batched",
-                  "cr_backward_workspace_size", "cr_backward", "cr_backward_batched", "cr_cell_location"):
+                  "cr_backward_workspace_size", "cr_backward", "cr_backward_batched", "cr_cell_location",
+                  "cr_lifetime_image", "cr_persistent_histogram_image"):
             getattr(L, f).restype = ctypes.c_int
         _lib_handle = L
     return _lib_handle
@@ -385,6 +390,47 @@ def cr_backward_batched(flat: torch.Tensor, shapes, offsets, bp: BatchedPairs, g
                                  ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                  _stream_ptr(flat.device)))
     return grad
+
+
+_LOCATIONS = {"birth": 0, "death": 1}
+
+
+def lifetime_image(shape: Sequence[int], pairs: Pairs, location: str = "birth") -> torch.Tensor:
+    """Lifetime channels (ndim, *shape) of the lifetime enhanced image (Sec. 4):
+    per dimension d, the largest lifetime of the finite pairs of dimension d
+    located at each voxel (anchor of the birth or death cell), 0 elsewhere."""
+    shape = tuple(int(v) for v in shape)
+    nd = len(shape)
+    out = torch.empty((nd,) + shape, dtype=torch.float32, device=pairs.raw.device)
+    sh = (ctypes.c_int64 * nd)(*shape)
+    _check(lib().cr_lifetime_image(ctypes.c_void_p(pairs.raw.data_ptr() if pairs.n else 0), pairs.n, nd, sh,
+                                   _LOCATIONS[location], ctypes.c_void_p(out.data_ptr()),
+                                   _stream_ptr(out.device)))
+    return out
+
+
+def lifetime_enhanced_image(img: torch.Tensor, pairs: Optional[Pairs] = None, location: str = "birth"):
+    """The image stacked with its lifetime channels: (1 + ndim, *shape)."""
+    img = _require_cuda_f32(img, "img")
+    if pairs is None:
+        pairs = cr_persistence(img)
+    return torch.cat([img.unsqueeze(0), lifetime_image(img.shape, pairs, location)], dim=0)
+
+
+def persistent_histogram_image(shape: Sequence[int], pairs: Pairs, nb: int, birth_range, nl: int,
+                               max_lifetime: float, location: str = "birth") -> torch.Tensor:
+    """Persistent histogram image (Sec. 4): channel (d * nb + i) * nl + j counts,
+    per voxel, the finite pairs of dimension d located there with birth in bin i
+    of ``birth_range`` and lifetime in bin j of [0, max_lifetime)."""
+    shape = tuple(int(v) for v in shape)
+    nd = len(shape)
+    out = torch.empty((nd * nb * nl,) + shape, dtype=torch.float32, device=pairs.raw.device)
+    sh = (ctypes.c_int64 * nd)(*shape)
+    _check(lib().cr_persistent_histogram_image(ctypes.c_void_p(pairs.raw.data_ptr() if pairs.n else 0), pairs.n,
+                                               nd, sh, _LOCATIONS[location], int(nb), float(birth_range[0]),
+                                               float(birth_range[1]), int(nl), float(max_lifetime),
+                                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(out.device)))
+    return out
 
 
 class PersistentHomology(torch.autograd.Function):

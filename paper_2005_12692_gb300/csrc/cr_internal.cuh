@@ -338,7 +338,7 @@ size_t scan_temp_bytes(int64_t n);
 enum Stage {
     STAGE_H0_STENCIL, STAGE_JUMP, STAGE_ROOTS, STAGE_RELABEL, STAGE_H0_CROSS, STAGE_UF_ROUND,
     STAGE_DUAL_STENCIL, STAGE_DUAL_CROSS, STAGE_H1_SCAN, STAGE_H1_SORT, STAGE_H1_REDUCE, STAGE_H1_EMIT,
-    STAGE_OUT_SORT, STAGE_BW_CONTRIB, STAGE_BW_SORT, STAGE_BW_SUM, STAGE_COUNT
+    STAGE_OUT_SORT, STAGE_BW_CONTRIB, STAGE_BW_SORT, STAGE_BW_SUM, STAGE_IMAGES, STAGE_COUNT
 };
 extern std::atomic<long long> g_launch_count;
 void prof_begin(cudaStream_t st, int stage);

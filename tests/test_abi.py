@@ -88,3 +88,20 @@ def test_binding_refuses_cpu_tensors(cr):
     import torch
     with pytest.raises(ValueError):
         cr.cr_persistence(torch.zeros(4, 4))
+
+
+def test_image_entry_points_check_arguments_on_the_host(cr):
+    lib = cr.lib()
+    sh = (ctypes.c_int64 * 2)(4, 5)
+    bad = (ctypes.c_int64 * 2)(4, 0)
+    p = ctypes.c_void_p(256)  # never dereferenced: every call below fails its argument checks
+    assert lib.cr_lifetime_image(p, 1, 2, sh, 0, None, None) == cr.CR_ERR_INVALID_ARG        # no output
+    assert lib.cr_lifetime_image(p, 1, 2, sh, 2, p, None) == cr.CR_ERR_INVALID_ARG           # location
+    assert lib.cr_lifetime_image(p, 1, 4, sh, 0, p, None) == cr.CR_ERR_INVALID_ARG           # ndim
+    assert lib.cr_lifetime_image(p, 1, 2, bad, 0, p, None) == cr.CR_ERR_INVALID_ARG          # extent
+    assert lib.cr_lifetime_image(None, 3, 2, sh, 0, p, None) == cr.CR_ERR_INVALID_ARG        # no pairs
+    h = lib.cr_persistent_histogram_image
+    assert h(p, 1, 2, sh, 0, 0, 0.0, 1.0, 2, 1.0, p, None) == cr.CR_ERR_INVALID_ARG          # nb
+    assert h(p, 1, 2, sh, 0, 2, 1.0, 1.0, 2, 1.0, p, None) == cr.CR_ERR_INVALID_ARG          # empty birth range
+    assert h(p, 1, 2, sh, 0, 2, 0.0, 1.0, 2, 0.0, p, None) == cr.CR_ERR_INVALID_ARG          # lifetime range
+    assert h(p, 1, 2, sh, 0, 2, 0.0, 1.0, 0, 1.0, p, None) == cr.CR_ERR_INVALID_ARG          # nl
