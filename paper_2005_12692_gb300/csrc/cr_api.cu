@@ -110,6 +110,9 @@ static void red_geometry(const HostPlan &P, int64_t &nwarps, int &maxlen) {
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// pairs of a single image sorted by rank on the device (see k_out_rank)
+constexpr int SMALL_SORT = 16384;
+
 // fixed part of the workspace
 static size_t fixed_bytes(const HostPlan &P) {
     size_t b = 0;
@@ -155,6 +158,10 @@ static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
                                                        : P.vtot / 4 + 4096);
     out = al((size_t)maxpairs * (24 + 32)) + al(radix_temp_bytes(maxpairs)) + al((size_t)P.segs.size() * 4 + 64) +
           al(scan_temp_bytes((int64_t)P.segs.size() + 1)) + (1 << 20);
+    if (P.segs.size() == 1) {  // the rank sort's buffers
+        const size_t rk = al((size_t)SMALL_SORT * 4) + al((size_t)SMALL_SORT * sizeof(cr_pair)) + 1024;
+        out = out > rk ? out : rk;
+    }
     size_t r = uf;
     if (h1 > r) r = h1;
     if (out > r) r = out;
@@ -204,7 +211,6 @@ static inline unsigned nbk(int64_t n, int t = 256) { return (unsigned)((n + t - 
 // to at most one class of its dimension), so the destination of pair i is the
 // number of smaller keys.  Blocks own RK_T*RK_R pairs and one slice of the
 // keys to compare against, so a few thousand pairs still spread over the GPU.
-constexpr int SMALL_SORT = 16384;
 constexpr int RK_T = 128, RK_R = 4, RK_TILE = 1024;
 
 __device__ __forceinline__ uint64_t pair_sort_key(const cr_pair *p) {
@@ -212,13 +218,20 @@ __device__ __forceinline__ uint64_t pair_sort_key(const cr_pair *p) {
 }
 
 // rank[i] += #{j in this block's slice : key_j < key_i}; slice 0 also copies
-// the pairs to tmp
-__global__ void __launch_bounds__(RK_T) k_out_rank(const cr_pair *__restrict__ pairs, int np, int chunk,
+// the pairs to tmp.  The pair count is read on the device (at most `cap`);
+// counts above SMALL_SORT are left to the radix path (the kernels do nothing).
+__global__ void __launch_bounds__(RK_T) k_out_rank(const cr_pair *__restrict__ pairs,
+                                                   const unsigned long long *__restrict__ npp, int64_t cap,
                                                    uint32_t *__restrict__ rank, cr_pair *__restrict__ tmp) {
     __shared__ uint64_t tile[RK_TILE];
+    const int64_t npl = (int64_t)*npp < cap ? (int64_t)*npp : cap;
+    if (npl > SMALL_SORT) return;
+    const int np = (int)npl;
+    const int base = blockIdx.x * RK_T * RK_R;
+    if (base >= np) return;
+    const int chunk = (np + gridDim.y - 1) / gridDim.y;
     uint64_t mine[RK_R];
     uint32_t cnt[RK_R];
-    const int base = blockIdx.x * RK_T * RK_R;
 #pragma unroll
     for (int r = 0; r < RK_R; r++) {
         const int i = base + r * RK_T + threadIdx.x;
@@ -254,14 +267,16 @@ __global__ void __launch_bounds__(RK_T) k_out_rank(const cr_pair *__restrict__ p
     }
 }
 
-__global__ void k_out_place(const cr_pair *__restrict__ tmp, int np, const uint32_t *__restrict__ rank,
-                            cr_pair *__restrict__ pairs) {
+__global__ void k_out_place(const cr_pair *__restrict__ tmp, const unsigned long long *__restrict__ npp, int64_t cap,
+                            const uint32_t *__restrict__ rank, cr_pair *__restrict__ pairs) {
+    const int64_t npl = (int64_t)*npp < cap ? (int64_t)*npp : cap;
+    if (npl > SMALL_SORT) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
+    if (i >= (int)npl) return;
     cr_pair p = tmp[i];
     p.flags &= 0xFFu;
     const uint32_t d = rank[i];
-    if (d < (uint32_t)np) pairs[d] = p;
+    if (d < (uint32_t)npl) pairs[d] = p;
 }
 
 // Group and edge arrays of one union-find in [base, base + cap): the number of
@@ -411,6 +426,26 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         if (rc) return rc;
     }
 
+    // ---- canonical order of a single image's pairs, without reading the count:
+    // the rank sort reads it on the device and stands aside above SMALL_SORT ----
+    const bool rank_sort = n == 1 && 3 * P.vtot < ((int64_t)1 << 30);
+    if (rank_sort) {
+        Carver R(region, region_cap);
+        uint32_t *rank = R.take<uint32_t>(SMALL_SORT);
+        cr_pair *tmp = R.take<cr_pair>(SMALL_SORT);
+        if (!R.ok) { g_detail = SITE_OUT_CARVE; return CR_ERR_WORKSPACE; }
+        // blocks over pairs x slices of the keys: about two blocks per SM for ~8 k pairs
+        const unsigned slices = (unsigned)((2 * num_sms() + 15) / 16);
+        prof_begin(st, STAGE_OUT_SORT);
+        cudaMemsetAsync(rank, 0, SMALL_SORT * sizeof(uint32_t), st);
+        CR_NOTE_LAUNCH();
+        k_out_rank<<<dim3(SMALL_SORT / (RK_T * RK_R), slices), RK_T, 0, st>>>(pairs_out, pair_count, capacity, rank,
+                                                                            tmp);
+        CR_NOTE_LAUNCH();
+        k_out_place<<<SMALL_SORT / 256, 256, 0, st>>>(tmp, pair_count, capacity, rank, pairs_out);
+        prof_end(st, STAGE_OUT_SORT, 64.0 * SMALL_SORT);
+    }
+
     // ---- count, status ----
     int hstatus[16] = {0};
     unsigned long long ufc[CR_CNT_SLOTS];
@@ -445,22 +480,8 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         uint32_t *segc = R.take<uint32_t>(n + 1);
         uint32_t *part = R.take<uint32_t>(scan_temp_bytes(n + 1) / 4 + 1);
         if (!R.ok) { g_detail = SITE_OUT_CARVE; return CR_ERR_WORKSPACE; }
-        bool small = n == 1 && np <= SMALL_SORT && 3 * P.vtot < ((int64_t)1 << 30);
-        if (np > 0 && small) {
-            // blocks over pairs x slices of the keys: about two blocks per SM
-            const int nbx = (int)((np + RK_T * RK_R - 1) / (RK_T * RK_R));
-            int slices = (2 * num_sms() + nbx - 1) / nbx;
-            if (slices < 1) slices = 1;
-            if (slices > 64) slices = 64;
-            int chunk = (int)((np + slices - 1) / slices);
-            slices = (int)((np + chunk - 1) / chunk);
-            prof_begin(st, STAGE_OUT_SORT);
-            cudaMemsetAsync(v0, 0, (size_t)np * sizeof(uint32_t), st);
-            CR_NOTE_LAUNCH();
-            k_out_rank<<<dim3((unsigned)nbx, (unsigned)slices), RK_T, 0, st>>>(pairs_out, (int)np, chunk, v0, tmp);
-            CR_NOTE_LAUNCH();
-            k_out_place<<<nbk(np), 256, 0, st>>>(tmp, (int)np, v0, pairs_out);
-            prof_end(st, STAGE_OUT_SORT, 64.0 * np);
+        const bool small = rank_sort && np <= SMALL_SORT;  // already sorted on the device
+        if (small) {
         } else if (np > 0) {
             prof_begin(st, STAGE_OUT_SORT);
             if (pair_offsets) cudaMemsetAsync(segc, 0, (n + 1) * sizeof(uint32_t), st);
