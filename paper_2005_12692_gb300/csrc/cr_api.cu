@@ -9,6 +9,7 @@
 //           Rem. 2.1): dimension 1 of a 2D image, dimension 2 of a volume;
 //   output  pairs sorted by (image, dim, birth, birth cell).
 #include "cr_internal.cuh"
+#include <mutex>
 #include <vector>
 #include <cmath>
 
@@ -313,6 +314,140 @@ static int carve_uf(char *base, size_t cap, int64_t nodes, int64_t vtot, UF &u) 
 }
 
 // ---------------------------------------------------------------------------
+// CUDA graphs of the launch sequence of single 1D/2D images.  The sequence
+// depends only on the arguments below, so the second call with the same
+// arguments captures it and later calls replay it with one launch; the
+// first call runs directly (it also sets kernel attributes, which are not
+// stream operations).  Capture failures fall back to direct launches.
+// ---------------------------------------------------------------------------
+struct GraphKey {
+    const float *img;
+    int64_t vtot;
+    int nx, ny, nz, maxdim;
+    uint32_t flags;
+    cr_pair *pairs;
+    int64_t capacity;
+    void *ws;
+    size_t ws_bytes;
+    cudaStream_t st;
+    int device;
+    bool prof_on;
+    uint32_t prof_mask;
+    bool serial;
+    bool operator==(const GraphKey &o) const {
+        return img == o.img && vtot == o.vtot && nx == o.nx && ny == o.ny && nz == o.nz && maxdim == o.maxdim &&
+               flags == o.flags && pairs == o.pairs && capacity == o.capacity && ws == o.ws &&
+               ws_bytes == o.ws_bytes && st == o.st && device == o.device && prof_on == o.prof_on &&
+               prof_mask == o.prof_mask && serial == o.serial;
+    }
+};
+struct GraphEntry {
+    GraphKey key;
+    int state;  // 0 seen once, 1 capturing, 2 replayable, -1 not capturable
+    cudaGraphExec_t exec;
+    long long launches;
+    std::vector<std::pair<int, std::pair<void *, void *>>> prof_recs;
+    std::vector<double> prof_bytes;
+    uint64_t last_use;
+};
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry> g_graphs;
+static uint64_t g_graph_tick = 0;
+constexpr size_t MAX_GRAPHS_CACHED = 32;
+
+static int current_device();
+static cudaStream_t capture_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {nullptr};
+    const int d = current_device();
+    if (d < 0 || d >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[d] && cudaStreamCreateWithFlags(&streams[d], cudaStreamNonBlocking) != cudaSuccess)
+        streams[d] = nullptr;
+    return streams[d];
+}
+
+static int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+template <class Fn>
+static int run_graphed(const GraphKey &key, Fn &&launch_all, cudaStream_t st) {
+    GraphEntry *E = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (auto &e : g_graphs)
+            if (e.key == key) E = &e;
+        if (!E) {
+            if (g_graphs.size() >= MAX_GRAPHS_CACHED) {  // drop the least recently used
+                size_t victim = 0;
+                for (size_t i = 1; i < g_graphs.size(); i++)
+                    if (g_graphs[i].last_use < g_graphs[victim].last_use) victim = i;
+                if (g_graphs[victim].state == 1) return launch_all(st);  // busy: do not disturb
+                if (g_graphs[victim].exec) cudaGraphExecDestroy(g_graphs[victim].exec);
+                g_graphs.erase(g_graphs.begin() + (long)victim);
+            }
+            g_graphs.push_back(GraphEntry{key, 0, nullptr, 0, {}, {}, ++g_graph_tick});
+            E = nullptr;  // first sighting: run directly
+        } else {
+            E->last_use = ++g_graph_tick;
+            if (E->state == 2) {
+                if (cudaGraphLaunch(E->exec, st) != cudaSuccess) return CR_ERR_CUDA;
+                g_launch_count.fetch_add(E->launches, std::memory_order_relaxed);
+                prof_replay(E->prof_recs, E->prof_bytes);
+                return CR_OK;
+            }
+            if (E->state != 0) return launch_all(st);
+            E->state = 1;
+        }
+    }
+    if (!E) return launch_all(st);
+    // capture this call's launches
+    const long long l0 = g_launch_count.load();
+    std::vector<std::pair<int, std::pair<void *, void *>>> recs;
+    std::vector<double> bytes;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    // captured on a stream of our own (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the caller's
+    cudaStream_t cs = capture_stream();
+    bool ok = cs && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int rc = CR_OK;
+    if (ok) {
+        prof_capture_begin();
+        rc = launch_all(cs);
+        prof_capture_end(recs, bytes);
+        ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g && rc == CR_OK;
+        if (ok) ok = cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+    }
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    GraphEntry *G = nullptr;
+    for (auto &e : g_graphs)
+        if (e.key == key) G = &e;
+    if (!ok) {
+        cudaGetLastError();  // clear a capture error
+        g_launch_count.store(l0);
+        if (G) G->state = -1;
+        return launch_all(st);
+    }
+    if (!G) {  // evicted meanwhile: keep it anyway
+        g_graphs.push_back(GraphEntry{key, 2, x, 0, {}, {}, ++g_graph_tick});
+        G = &g_graphs.back();
+    }
+    G->state = 2;
+    G->exec = x;
+    G->launches = g_launch_count.load() - l0;
+    G->prof_recs = recs;
+    G->prof_bytes = bytes;
+    if (cudaGraphLaunch(x, st) != cudaSuccess) return CR_ERR_CUDA;
+    prof_replay(G->prof_recs, G->prof_bytes);
+    return CR_OK;
+}
+
+// ---------------------------------------------------------------------------
 // the pipeline
 // ---------------------------------------------------------------------------
 static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, cr_pair *pairs_out, int64_t capacity,
@@ -338,8 +473,6 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     unsigned long long *pair_count = &cnt[1];
 
     cudaMemcpyAsync(segs, P.segs.data(), n * sizeof(Seg), cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(cnt, 0, CR_CNT_SLOTS * sizeof(unsigned long long), st);
-    if (P.any_mid) cudaMemsetAsync(extra, 0, (size_t)mask_words * 4, st);
 
     PairBuf pb;
     pb.pairs = pairs_out;
@@ -348,6 +481,14 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
 
     unsigned long long hc[4];
     int rc = CR_OK;
+    const bool rank_sort = n == 1 && 3 * P.vtot < ((int64_t)1 << 30);
+
+    // everything up to the count readback; a fixed sequence of launches for a
+    // given image, so 1D/2D single images replay it as a CUDA graph
+    auto phase1 = [&](cudaStream_t st) -> int {
+    int rc = CR_OK;
+    cudaMemsetAsync(cnt, 0, CR_CNT_SLOTS * sizeof(unsigned long long), st);
+    if (P.any_mid) cudaMemsetAsync(extra, 0, (size_t)mask_words * 4, st);
 
     // ---- H0 and the top dimension by duality: two independent union-finds,
     // run side by side in halves of the region ----
@@ -428,7 +569,6 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
 
     // ---- canonical order of a single image's pairs, without reading the count:
     // the rank sort reads it on the device and stands aside above SMALL_SORT ----
-    const bool rank_sort = n == 1 && 3 * P.vtot < ((int64_t)1 << 30);
     if (rank_sort) {
         Carver R(region, region_cap);
         uint32_t *rank = R.take<uint32_t>(SMALL_SORT);
@@ -445,6 +585,17 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         k_out_place<<<SMALL_SORT / 256, 256, 0, st>>>(tmp, pair_count, capacity, rank, pairs_out);
         prof_end(st, STAGE_OUT_SORT, 64.0 * SMALL_SORT);
     }
+    return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+    };
+    if (n == 1 && !P.any_mid) {
+        const Seg &S0 = P.segs[0];
+        GraphKey key{imgs, P.vtot, S0.nx, S0.ny, S0.nz, maxdim, flags, pairs_out, capacity, ws, ws_bytes, st,
+                     current_device(), prof_active(), prof_mask(), P.serial_uf};
+        rc = run_graphed(key, phase1, st);
+    } else {
+        rc = phase1(st);
+    }
+    if (rc) return rc;
 
     // ---- count, status ----
     int hstatus[16] = {0};

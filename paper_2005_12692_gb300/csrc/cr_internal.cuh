@@ -11,6 +11,8 @@
 // order of Sec. 2.
 #pragma once
 #include <cstdint>
+#include <utility>
+#include <vector>
 #include <cstddef>
 #include <cstring>
 #include <atomic>
@@ -342,6 +344,11 @@ enum Stage {
 };
 extern std::atomic<long long> g_launch_count;
 void prof_begin(cudaStream_t st, int stage);
+bool prof_active();
+uint32_t prof_mask();
+void prof_capture_begin();
+void prof_capture_end(std::vector<std::pair<int, std::pair<void *, void *>>> &out, std::vector<double> &bytes);
+void prof_replay(const std::vector<std::pair<int, std::pair<void *, void *>>> &recs, const std::vector<double> &bytes);
 void prof_end(cudaStream_t st, int stage, double bytes);
 void prof_flush();
 void prof_add_bytes(int stage, double bytes);

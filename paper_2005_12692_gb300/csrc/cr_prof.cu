@@ -19,6 +19,7 @@ struct Pending {
     int stage;
     cudaEvent_t a, b;
     double bytes;
+    bool graph_owned;  // recorded by a graph node: re-used by every launch of the graph
 };
 
 static std::mutex g_mu;
@@ -27,6 +28,8 @@ static uint32_t g_mask = 0xFFFFFFFFu;  // stages that record events
 static std::vector<cudaEvent_t> g_pool;
 static std::vector<Pending> g_pending;
 static std::vector<Pending> g_open;  // begun, not ended
+static bool g_capturing = false;    // a stream capture is recording the stages
+static std::vector<Pending> g_captured;
 static double g_ms[STAGE_COUNT];
 static long long g_n[STAGE_COUNT];
 static double g_bytes[STAGE_COUNT];
@@ -45,8 +48,11 @@ static cudaEvent_t take_event() {
 void prof_begin(cudaStream_t st, int stage) {
     if (!g_on || !((g_mask >> stage) & 1u)) return;
     std::lock_guard<std::mutex> lk(g_mu);
-    Pending p{stage, take_event(), nullptr, 0.0};
-    cudaEventRecord(p.a, st);
+    Pending p{stage, take_event(), nullptr, 0.0, g_capturing};
+    if (g_capturing)
+        cudaEventRecordWithFlags(p.a, st, cudaEventRecordExternal);  // a timing node of the graph
+    else
+        cudaEventRecord(p.a, st);
     g_open.push_back(p);
 }
 
@@ -59,8 +65,13 @@ void prof_end(cudaStream_t st, int stage, double bytes) {
             g_open.erase(g_open.begin() + (long)i);
             p.b = take_event();
             p.bytes = bytes;
-            cudaEventRecord(p.b, st);
-            g_pending.push_back(p);
+            if (p.graph_owned) {
+                cudaEventRecordWithFlags(p.b, st, cudaEventRecordExternal);
+                g_captured.push_back(p);
+            } else {
+                cudaEventRecord(p.b, st);
+                g_pending.push_back(p);
+            }
             return;
         }
     }
@@ -83,10 +94,41 @@ void prof_flush() {
             g_n[p.stage] += 1;
             g_bytes[p.stage] += p.bytes;
         }
-        g_pool.push_back(p.a);
-        g_pool.push_back(p.b);
+        if (!p.graph_owned) {
+            g_pool.push_back(p.a);
+            g_pool.push_back(p.b);
+        }
     }
     g_pending.clear();
+}
+
+bool prof_active() { return g_on; }
+uint32_t prof_mask() { return g_mask; }
+
+// stages recorded while a graph is captured become event nodes of the graph;
+// their events belong to the graph and are read after every launch of it
+void prof_capture_begin() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_capturing = true;
+    g_captured.clear();
+}
+void prof_capture_end(std::vector<std::pair<int, std::pair<void *, void *>>> &out, std::vector<double> &bytes) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_capturing = false;
+    out.clear();
+    bytes.clear();
+    for (auto &p : g_captured) {
+        out.push_back({p.stage, {(void *)p.a, (void *)p.b}});
+        bytes.push_back(p.bytes);
+    }
+    g_captured.clear();
+}
+void prof_replay(const std::vector<std::pair<int, std::pair<void *, void *>>> &recs, const std::vector<double> &bytes) {
+    if (!g_on) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (size_t i = 0; i < recs.size(); i++)
+        g_pending.push_back(Pending{recs[i].first, (cudaEvent_t)recs[i].second.first,
+                                    (cudaEvent_t)recs[i].second.second, bytes[i], true});
 }
 
 }  // namespace cr

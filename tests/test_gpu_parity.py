@@ -174,3 +174,34 @@ def test_batched_volumes(cr):
     bp = cr.cr_persistence_batched(ts, keep_zero=True)
     for i, t in enumerate(ts):
         assert bp.image(i).numpy().tobytes() == cr.cr_persistence(t, keep_zero=True).numpy().tobytes()
+
+
+@pytest.mark.parametrize("shape", [(256, 192), (4096,), (64, 64)])
+def test_repeated_calls_replay_identically(cr, oracle_mod, shape):
+    # the same arguments four times through the C ABI: the first call runs the
+    # launches directly, the second captures them as a graph, the rest replay
+    # it; every call must give the oracle's pairs, and the input may change
+    # between calls (a graph holds pointers, not values)
+    import ctypes
+    from paper_2005_12692_gb300 import synth
+    L = cr.lib()
+    nd = len(shape)
+    sh = (ctypes.c_int64 * nd)(*shape)
+    sz = ctypes.c_size_t()
+    assert L.cr_workspace_size(nd, sh, nd - 1, 0, ctypes.byref(sz)) == 0
+    ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+    cap = int(np.prod(shape)) + 16
+    out = torch.empty((cap, 32), dtype=torch.uint8, device="cuda")
+    img = torch.empty(shape, dtype=torch.float32, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for k in range(4):
+        src = synth.grf(shape, 2.0, 700 + (k // 2)) if nd > 1 else np.sin(np.arange(shape[0]) * 0.05 * (k + 1)).astype(np.float32)
+        img.copy_(torch.from_numpy(np.ascontiguousarray(src, dtype=np.float32)))
+        n = ctypes.c_int64(0)
+        before = L.cr_launch_count()
+        rc = L.cr_persistence(ctypes.c_void_p(img.data_ptr()), nd, sh, nd - 1, ctypes.c_void_p(out.data_ptr()), cap,
+                              ctypes.byref(n), ctypes.c_void_p(ws.data_ptr()), ws.numel(), stream, 0)
+        assert rc == 0
+        assert L.cr_launch_count() > before
+        got = cells(cr.Pairs(out[: n.value]).numpy())
+        assert got == oracle_cells(oracle_mod, src, keep_zero=False), k
