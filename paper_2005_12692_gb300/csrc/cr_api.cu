@@ -24,6 +24,8 @@ void set_host_detail(int site) { g_detail = site; }
 struct HostPlan {
     std::vector<Seg> segs;
     int64_t vtot = 0, ctot = 0, cells = 0, ntiles = 0;
+    int64_t nstiles = 0;  // 32x32 super-tiles over all images (used when every image is 2D)
+    bool all_2d = true;
     int64_t max_face_per_image = 0;
     bool any_h0 = false, any_dual = false, any_mid = false;
     bool serial_uf = false;  // run the two union-finds one after the other (half the region)
@@ -79,7 +81,9 @@ static int plan_images(const int64_t *const *shapes_rows, int n, int ndim, int m
         S.tiles_x = (int32_t)((nx + TILE_X - 1) / TILE_X);
         S.tiles_y = (int32_t)((ny + TILE_Y - 1) / TILE_Y);
         S.tiles_z = (int32_t)((nz + TILE_Z - 1) / TILE_Z);
-        S.pad = 0;
+        S.stoff = (int32_t)P.nstiles;
+        P.nstiles += ((nx + ST_X - 1) / ST_X) * ((ny + ST_Y - 1) / ST_Y);
+        P.all_2d &= S.edim == 2 && nz == 1;
         S.toff = P.ntiles;
         P.ntiles += (int64_t)S.tiles_x * S.tiles_y * S.tiles_z;
         P.any_h0 |= want_h0 || want_mid;
@@ -93,6 +97,7 @@ static int plan_images(const int64_t *const *shapes_rows, int n, int ndim, int m
     }
     P.vtot = voff;
     P.ctot = coff;
+    if (P.nstiles >= ((int64_t)1 << 31)) P.all_2d = false;
     if (P.vtot >= ((int64_t)1 << 31) - 2 || P.ctot >= ((int64_t)1 << 31) - 2 || 3 * P.vtot >= ((int64_t)1 << 40))
         return CR_ERR_TOO_LARGE;
     int b = 0;
@@ -495,6 +500,8 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     if (P.any_h0 || P.any_dual) {
         const bool both = P.any_h0 && P.any_dual && !P.serial_uf;
         const size_t half = both ? (region_cap / 2) & ~(size_t)255 : region_cap;
+        // several 2D images: both stencils in one kernel over 32x32 super-tiles
+        const int64_t fused2d = (n > 1 && P.all_2d) ? P.nstiles : 0;
         UF uh, ud;
         if (P.any_h0) {
             rc = carve_uf(region, half, P.vtot, P.vtot, uh);
@@ -505,7 +512,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
             uh.hcnt = hc;
         }
         if (P.any_h0 && !both) {
-            rc = run_uf(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, &uh, nullptr, pb, flags,
+            rc = run_uf(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, fused2d, &uh, nullptr, pb, flags,
                         P.any_mid ? extra : nullptr, status, st);
             if (rc) return rc;
         }
@@ -518,8 +525,8 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
             ud.hcnt = hc;
         }
         if (both || P.any_dual) {
-            rc = run_uf(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, both ? &uh : nullptr, &ud, pb,
-                        flags, both && P.any_mid ? extra : nullptr, status, st);
+            rc = run_uf(imgs, segs, P.segs.data(), n, P.vtot, P.ctot, P.ntiles, fused2d, both ? &uh : nullptr, &ud,
+                        pb, flags, both && P.any_mid ? extra : nullptr, status, st);
             if (rc) return rc;
         }
     }

@@ -33,8 +33,12 @@ struct Seg {
     int32_t nx, ny, nz;
     int32_t edim;  // effective dimension (leading unit extents dropped), 0..3
     int64_t toff;  // first tile of this image in the tiled launches
-    int32_t tiles_x, tiles_y, tiles_z, pad;
+    int32_t tiles_x, tiles_y, tiles_z;
+    int32_t stoff; // first 32x32 super-tile of this image (2D batches), see k_stencil2d_batch
 };
+
+// super-tiles of the fused 2D batch stencil
+constexpr int ST_X = 32, ST_Y = 32;
 
 // tiles of the 2.5D stencil kernels: TILE_X x TILE_Y voxels marching TILE_Z planes
 constexpr int TILE_X = 32, TILE_Y = 8, TILE_Z = 16;
@@ -293,9 +297,11 @@ int persistence_serial(const float *img, int ndim, const int64_t *shape, int max
 
 // union-find of H0 (u0, primal graph) and of the top dimension (u1, dual
 // graph); either may be null
+// nstiles > 0: every image is 2D and both stencils run fused over that many
+// 32x32 super-tiles
 int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ctot,
-           int64_t ntiles, UF *u0, UF *u1, const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status,
-           cudaStream_t st);
+           int64_t ntiles, int64_t nstiles, UF *u0, UF *u1, const PairBuf &pb, uint32_t flags, uint32_t *extra_mask,
+           int *status, cudaStream_t st);
 
 // middle-dimension buffers (cr_h1.cu)
 struct H1Bufs {

@@ -540,8 +540,9 @@ __global__ void k_dual_stencil(const float *__restrict__ img, const Seg *__restr
 // largest key: the facets holding a vertex of the cube's value phi(c) all
 // have value phi(c), the others less, and among those the smallest L wins,
 // which is the first in the order -z, +z, -y, +y, -x, +x (2D: -y, +y, -x, +x).
-// The neighbour across it shares that facet, so its value is at least phi(c):
-// it is older if larger, or equal and on the - side (smaller L).
+// The neighbour across it shares that facet, so its value is max(phi(c), fo)
+// with fo the largest of its other vertices: it is older if fo > phi(c), and
+// otherwise (equal value) exactly when it lies on the - side (smaller L).
 // ---------------------------------------------------------------------------
 template <int EDIM>
 __global__ void __launch_bounds__(TILE_X *TILE_Y) k_dual_stencil_tma(const __grid_constant__ CUtensorMap tmap,
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_dual_stencil_tma(const __gri
                 const uint32_t pl = (uint32_t)cx * (uint32_t)cy;
                 other = up ? c + pl : c - pl;
             }
-            hook = fo > fc || (fo == fc && !up);
+            hook = fo > fc || !up;  // the neighbour's value is max(fo, phi(c))
             other += (uint32_t)S.coff;
         }
         const uint32_t gc = (uint32_t)S.coff + c;
@@ -795,6 +796,194 @@ __global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restric
             } else {
                 fail_ws(status, SITE_EDGES);
             }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batches of 2D images: both stencils in one kernel.  A block stages a 32x32
+// super-tile of one image with a halo (x0-1 .. x0+33, y0-1 .. y0+33) in
+// shared memory with plain coalesced loads; every pixel takes its primal hook
+// (as in k_h0_stencil_tma) and every square its dual hook (as in
+// k_dual_stencil_tma); both sets of hooks are then followed inside the
+// super-tile, so that each node leaves with its in-tile root or its first
+// ancestor outside the super-tile.
+// ---------------------------------------------------------------------------
+constexpr int SB_X = ST_X + 3, SB_Y = ST_Y + 3;
+__global__ void __launch_bounds__(256) k_stencil2d_batch(const float *__restrict__ img, const Seg *__restrict__ segs,
+                                                        int nseg, uint32_t *__restrict__ parent,
+                                                        uint8_t *__restrict__ dd, uint32_t *__restrict__ parentc,
+                                                        uint8_t *__restrict__ ddc, int *status, PairBuf pb,
+                                                        uint32_t flags) {
+    constexpr uint32_t GLOBAL = 0x80000000u;
+    __shared__ float box[SB_Y][SB_X + 1];
+    __shared__ uint32_t lp[ST_Y * ST_X], lq[ST_Y * ST_X];
+    __shared__ int s_si;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)segs[mid].stoff <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_si = lo;
+    }
+    __syncthreads();
+    const int si = s_si;
+    const Seg S = segs[si];
+    const int nx = S.nx, ny = S.ny, cx = nx - 1, cy = ny - 1;
+    const int sx = (nx + ST_X - 1) / ST_X;
+    const int t = (int)blockIdx.x - S.stoff;
+    const int x0 = (t % sx) * ST_X, y0 = (t / sx) * ST_Y;
+    const float *im = img + S.voff;
+    bool nan_seen = false;
+    for (int i = threadIdx.x; i < SB_Y * SB_X; i += 256) {
+        const int by = i / SB_X, bx = i % SB_X;
+        const int gx = x0 - 1 + bx, gy = y0 - 1 + by;
+        float v = 0.f;
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+            v = im[(int64_t)gy * nx + gx];
+            nan_seen |= isnan(v);
+        }
+        box[by][bx] = v;
+    }
+    const bool do_p = parent != nullptr, do_d = parentc != nullptr && S.ncell > 0;
+    if (do_d && t == 0 && threadIdx.x == 0) {  // the outer node
+        parentc[S.coff + S.ncell] = (uint32_t)(S.coff + S.ncell);
+        ddc[S.coff + S.ncell] = 0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 31;
+    const uint32_t P = (uint32_t)nx * (uint32_t)ny;  // one type's L-range (nz = 1)
+#pragma unroll
+    for (int k = 0; k < ST_Y / 8; k++) {
+        const int ty = (threadIdx.x >> 5) + 8 * k;
+        const int li = ty * ST_X + tx;
+        const int x = x0 + tx, y = y0 + ty;
+        const int bx = tx + 1, by = ty + 1;
+        // ---- primal: the first neighbour with phi <= phi(v) in descending edge-L order (+y, -y, +x, -x)
+        if (do_p) {
+            if (x < nx && y < ny) {
+                const float fv = box[by][bx];
+                int dir = 0;
+                float fu = 0.f;
+                if (x > 0 && box[by][bx - 1] <= fv) { dir = 1; fu = box[by][bx - 1]; }
+                if (x + 1 < nx && box[by][bx + 1] <= fv) { dir = 2; fu = box[by][bx + 1]; }
+                if (y > 0 && box[by - 1][bx] <= fv) { dir = 3; fu = box[by - 1][bx]; }
+                if (y + 1 < ny && box[by + 1][bx] <= fv) { dir = 4; fu = box[by + 1][bx]; }
+                const uint32_t lv = (uint32_t)y * nx + x;
+                if (dir && (fu < fv || !(dir & 1))) {
+                    const uint32_t stp = dir <= 2 ? 1u : (uint32_t)nx;
+                    const uint32_t lu = (dir & 1) ? lv - stp : lv + stp;
+                    const bool inside = dir == 1 ? tx > 0 : dir == 2 ? tx + 1 < ST_X : dir == 3 ? ty > 0 : ty + 1 < ST_Y;
+                    const int lstep = dir <= 2 ? 1 : ST_X;
+                    lp[li] = inside ? (uint32_t)((dir & 1) ? li - lstep : li + lstep)
+                                    : (GLOBAL | (uint32_t)(S.voff + lu));
+                    dd[S.voff + lv] = (uint8_t)dir;
+                    if (flags & CR_KEEP_ZERO) {
+                        const uint32_t la = ((dir & 1) ? lu : lv) + (dir >= 3 ? P : 0u);
+                        const float cv = unord32(ord32(fv));
+                        emit_pair(pb, (uint32_t)si, 0, cv, cv, lv, la, 0);
+                    }
+                } else {
+                    lp[li] = (uint32_t)li;
+                    dd[S.voff + lv] = 0;
+                }
+            } else {
+                lp[li] = (uint32_t)li;
+            }
+        }
+        // ---- dual: the square's first facet (-y, +y, -x, +x) holding its value
+        if (do_d) {
+            if (x < cx && y < cy) {
+                const float v00 = box[by][bx], v01 = box[by][bx + 1], v10 = box[by + 1][bx], v11 = box[by + 1][bx + 1];
+                const float ylo = fmaxf(v00, v01), yhi = fmaxf(v10, v11), xlo = fmaxf(v00, v10);
+                const float fc = fmaxf(ylo, yhi);
+                const int f = ylo == fc ? 0 : yhi == fc ? 1 : xlo == fc ? 2 : 3;
+                const int axis = 1 - (f >> 1);  // 0 x, 1 y
+                const bool up = f & 1;
+                const uint32_t c = (uint32_t)y * (uint32_t)cx + (uint32_t)x;
+                const bool outside = axis == 0 ? (up ? x + 1 >= cx : x == 0) : (up ? y + 1 >= cy : y == 0);
+                bool hook = true;
+                uint32_t other = (uint32_t)(S.coff + S.ncell);
+                bool inside = false;
+                int lother = 0;
+                if (!outside) {
+                    float fo;
+                    if (axis == 0) {
+                        const int xx = up ? bx + 2 : bx - 1;
+                        fo = fmaxf(box[by][xx], box[by + 1][xx]);
+                        other = (uint32_t)S.coff + (up ? c + 1 : c - 1);
+                        inside = up ? tx + 1 < ST_X : tx > 0;
+                        lother = up ? li + 1 : li - 1;
+                    } else {
+                        const int yy = up ? by + 2 : by - 1;
+                        fo = fmaxf(box[yy][bx], box[yy][bx + 1]);
+                        other = (uint32_t)S.coff + (up ? c + (uint32_t)cx : c - (uint32_t)cx);
+                        inside = up ? ty + 1 < ST_Y : ty > 0;
+                        lother = up ? li + ST_X : li - ST_X;
+                    }
+                    hook = fo > fc || !up;  // the neighbour's value is max(fo, phi(c))
+                }
+                const uint32_t gc = (uint32_t)S.coff + c;
+                if (hook) {
+                    lq[li] = inside ? (uint32_t)lother : (GLOBAL | other);
+                    ddc[gc] = (uint8_t)(f + 1);
+                    if (flags & CR_KEEP_ZERO) {
+                        const int m = 1 - axis;
+                        const uint32_t fl = cube_L(S, m, x + (axis == 0 && up), y + (axis == 1 && up), 0);
+                        const float cv = unord32(ord32(fc));
+                        emit_pair(pb, (uint32_t)si, 1, cv, cv, fl, cube_L(S, 0, x, y, 0), 0);
+                    }
+                } else {
+                    lq[li] = (uint32_t)li;
+                    ddc[gc] = 0;
+                }
+            } else {
+                lq[li] = (uint32_t)li;
+            }
+        }
+    }
+    if (nan_seen) set_status(status, CR_ERR_NAN);
+    __syncthreads();
+    // follow both sets of hooks inside the super-tile (every write stores an ancestor)
+    for (int it = 0; it < 64; it++) {
+        int ch = 0;
+#pragma unroll
+        for (int k = 0; k < ST_Y / 8; k++) {
+            const int li = ((threadIdx.x >> 5) + 8 * k) * ST_X + tx;
+            if (do_p) {
+                const uint32_t p = lp[li];
+                if (!(p & GLOBAL)) {
+                    const uint32_t q = lp[p];
+                    if (q != p) { lp[li] = q; ch = 1; }
+                }
+            }
+            if (do_d) {
+                const uint32_t p = lq[li];
+                if (!(p & GLOBAL)) {
+                    const uint32_t q = lq[p];
+                    if (q != p) { lq[li] = q; ch = 1; }
+                }
+            }
+        }
+        if (!__syncthreads_or(ch)) break;
+    }
+#pragma unroll
+    for (int k = 0; k < ST_Y / 8; k++) {
+        const int ty = (threadIdx.x >> 5) + 8 * k;
+        const int li = ty * ST_X + tx;
+        const int x = x0 + tx, y = y0 + ty;
+        if (do_p && x < nx && y < ny) {
+            const uint32_t p = lp[li];
+            parent[S.voff + (int64_t)y * nx + x] =
+                (p & GLOBAL) ? (p & ~GLOBAL)
+                             : (uint32_t)(S.voff + (int64_t)(y0 + (int)p / ST_X) * nx + x0 + (int)p % ST_X);
+        }
+        if (do_d && x < cx && y < cy) {
+            const uint32_t p = lq[li];
+            parentc[S.coff + (int64_t)y * cx + x] =
+                (p & GLOBAL) ? (p & ~GLOBAL)
+                             : (uint32_t)(S.coff + (int64_t)(y0 + (int)p / ST_X) * cx + x0 + (int)p % ST_X);
         }
     }
 }
@@ -1285,11 +1474,19 @@ static int coop_blocks(int64_t work) {
 // be null.  The stencils and cross-edge kernels run per graph; basins and
 // rounds run both graphs in one cooperative launch each.
 int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_t vtot, int64_t ctot,
-           int64_t ntiles, UF *u0, UF *u1, const PairBuf &pb, uint32_t flags, uint32_t *extra_mask, int *status,
-           cudaStream_t st) {
+           int64_t ntiles, int64_t nstiles, UF *u0, UF *u1, const PairBuf &pb, uint32_t flags, uint32_t *extra_mask,
+           int *status, cudaStream_t st) {
     if (u0) cudaMemsetAsync(u0->cnt, 0, UF_CNT * sizeof(unsigned long long), st);
     if (u1) cudaMemsetAsync(u1->cnt, 0, UF_CNT * sizeof(unsigned long long), st);
-    if (u0) {
+    if (nstiles > 0) {
+        prof_begin(st, STAGE_H0_STENCIL);
+        CR_NOTE_LAUNCH();
+        k_stencil2d_batch<<<(unsigned)nstiles, 256, 0, st>>>(img, segs, nseg, u0 ? u0->lab : nullptr,
+                                                             u0 ? u0->dd : nullptr, u1 ? u1->lab : nullptr,
+                                                             u1 ? u1->dd : nullptr, status, pb, flags);
+        prof_end(st, STAGE_H0_STENCIL, 4.0 * vtot + (u0 ? 5.0 * vtot : 0.0) + (u1 ? 5.0 * ctot : 0.0));
+    }
+    if (u0 && nstiles == 0) {
         prof_begin(st, STAGE_H0_STENCIL);
         CR_NOTE_LAUNCH();
         CUtensorMap tmap;
@@ -1307,7 +1504,7 @@ int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
         }
         prof_end(st, STAGE_H0_STENCIL, 9.0 * vtot);
     }
-    if (u1) {
+    if (u1 && nstiles == 0) {
         prof_begin(st, STAGE_DUAL_STENCIL);
         CR_NOTE_LAUNCH();
         CUtensorMap tmap;
