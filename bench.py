@@ -221,6 +221,16 @@ def roofline_from(stages, peaks, sustained=True):
             "limiter": LIMITER.get(best, "hbm")}
 
 
+def workload_config(args, W, data, world):
+    """The config object of the JSON line (the same for both arms)."""
+    return {"workload": args.workload,
+            "shape": list(data.shape) if W["kind"] == "single" else "4096 x U{28..256}^2",
+            "maxdim": W["maxdim"], "cells": num_cells(data.shape) if W["kind"] == "single" else None,
+            "size_override": args.size,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between steps (256 MiB write)"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -305,7 +315,7 @@ def main():
                 "ms_per_step": 1e3 * statistics.mean(dt for _, dt in vals),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "impl": "reference",
-                "config": {"workload": args.workload},
+                "config": workload_config(args, W, data, 1),
                 "cpu_baseline": {"value": value, "unit": metric.split()[0], "cores": cores, "kind": "oracle",
                                  "sample": desc},
                 "e2e": {"value": value, "unit": metric.split()[0], "h2d_bytes_per_step": 0,
@@ -512,12 +522,7 @@ def main():
     line = {"metric": metric, "value": value, "unit": metric.split()[0], "n_gpus": args.gpus * 0 + world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload,
-                       "shape": list(data.shape) if W["kind"] == "single" else "4096 x U{28..256}^2",
-                       "maxdim": W["maxdim"], "cells": num_cells(data.shape) if W["kind"] == "single" else None,
-                       "size_override": args.size,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "flushed between steps (256 MiB write)"},
+            "config": workload_config(args, W, data, world),
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": metric.split()[0], "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
