@@ -119,21 +119,6 @@ __device__ __forceinline__ uint64_t face_max_facet(const Img3 &I, const Seg &S, 
     return best;
 }
 
-// If the face with key fk is the pivot of an apparent pair, the key of its
-// edge; 0 otherwise.
-__device__ uint64_t apparent_edge(const Img3 &I, const Seg &S, uint64_t fk) {
-    int fm, c[3];
-    decode_L(S, key_L(fk), fm, c);
-    int ea, ec[3];
-    uint64_t sk = face_max_facet(I, S, fm, c, ea, ec);
-    if (h0_negative(I, S, ea, ec)) return 0;
-    uint64_t cf[4];
-    int n = edge_cofacets(I, S, ea, ec, cf);
-    uint64_t mn = ~0ull;
-    for (int i = 0; i < n; i++) mn = cf[i] < mn ? cf[i] : mn;
-    return mn == fk ? sk : 0;
-}
-
 // ---------------------------------------------------------------------------
 // 1. scan
 // ---------------------------------------------------------------------------
@@ -504,235 +489,24 @@ struct RedParams {
 
 __device__ __forceinline__ uint64_t ld_cg(const uint64_t *p) { return __ldcg((const unsigned long long *)p); }
 
-// out = A xor B (sorted, distinct), warp-cooperative; returns length or -1 if it exceeds cap
-template <bool ACG, bool BCG>
-__device__ int warp_xor(const uint64_t *A, int na, const uint64_t *B, int nb, uint64_t *out, int cap) {
-    const int lane = threadIdx.x & 31;
-    const int T = na + nb;
-    if (T <= 32) {
-        uint64_t v = ~0ull;
-        bool valid = lane < T;
-        if (lane < na) v = ACG ? ld_cg(A + lane) : A[lane];
-        else if (valid) v = BCG ? ld_cg(B + lane - na) : B[lane - na];
-        unsigned same = __match_any_sync(0xFFFFFFFFu, v);
-        bool keep = valid && __popc(same) == 1;
-        int rank = 0;
-        for (int k = 0; k < 32; k++) {
-            uint64_t w = __shfl_sync(0xFFFFFFFFu, v, k);
-            int kk = __shfl_sync(0xFFFFFFFFu, (int)keep, k);
-            rank += (kk && w < v) ? 1 : 0;
-        }
-        unsigned km = __ballot_sync(0xFFFFFFFFu, keep);
-        int n = __popc(km);
-        if (n > cap) return -1;
-        if (keep) out[rank] = v;
-        __syncwarp();
-        return n;
-    }
-    // merge path: lane takes merged positions [s, e)
-    const int per = (T + 31) / 32;
-    const int s = min(lane * per, T), e = min(s + per, T);
-    int lo = max(0, s - nb), hi = min(s, na);
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        uint64_t am = ACG ? ld_cg(A + mid) : A[mid], bm = BCG ? ld_cg(B + s - 1 - mid) : B[s - 1 - mid];
-        if (am <= bm) lo = mid + 1; else hi = mid;
-    }
-    const int i0 = lo, j0 = s - lo;
-    // predecessor of position s in the merged order
-    uint64_t prev = 0;
-    bool hasprev = false;
-    if (s > 0) {
-        uint64_t pa = i0 > 0 ? (ACG ? ld_cg(A + i0 - 1) : A[i0 - 1]) : 0, pb = j0 > 0 ? (BCG ? ld_cg(B + j0 - 1) : B[j0 - 1]) : 0;
-        prev = pa > pb ? pa : pb;
-        hasprev = true;
-    }
-    int kept = 0;
-    for (int pass = 0; pass < 2; pass++) {
-        int i = i0, j = j0;
-        uint64_t pv = prev;
-        bool hp = hasprev;
-        int wpos = 0;
-        if (pass == 1) {
-            int incl = kept;
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            wpos = incl - kept;
-            int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-            if (total > cap) return -1;
-        }
-        // current element
-        uint64_t curv = 0;
-        bool have = false;
-        auto take = [&](uint64_t &x) -> bool {
-            if (i + j >= T) return false;
-            uint64_t av = i < na ? (ACG ? ld_cg(A + i) : A[i]) : ~0ull;
-            uint64_t bv = j < nb ? (BCG ? ld_cg(B + j) : B[j]) : ~0ull;
-            if (j >= nb || (i < na && av <= bv)) { x = av; i++; }
-            else { x = bv; j++; }
-            return true;
-        };
-        int q = s;
-        if (q < e) have = take(curv);
-        while (q < e && have) {
-            uint64_t nxt = 0;
-            bool hn = take(nxt);  // may read one element past e: that is the successor
-            bool dup = (hp && pv == curv) || (hn && nxt == curv);
-            if (!dup) {
-                if (pass == 0) kept++;
-                else out[wpos++] = curv;
-            }
-            pv = curv;
-            hp = true;
-            curv = nxt;
-            have = hn;
-            q++;
-        }
-        if (pass == 1) {
-            int incl = kept;
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            __syncwarp();
-            return __shfl_sync(0xFFFFFFFFu, incl, 31);
-        }
-    }
-    return -1;  // unreachable
-}
-
-// publish column j's current state; returns false on arena overflow
-__device__ bool publish(const RedParams &R, int64_t j, const uint64_t *buf, int n) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long off = 0;
-    if (lane == 0) off = atomicAdd(R.arena_top, (unsigned long long)n);
-    off = __shfl_sync(0xFFFFFFFFu, off, 0);
-    if ((int64_t)(off + n) > R.arena_cap) return false;
-    for (int k = lane; k < n; k += 32) __stcg((unsigned long long *)&R.arena[off + k], buf[k]);
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) atomicExch(&R.cur[j], (off << 24) | (unsigned long long)n);
-    __threadfence();
-    __syncwarp();
-    return true;
-}
-
-__device__ __forceinline__ void load_version(const RedParams &R, int64_t o, unsigned long long &off, int &len) {
-    unsigned long long v = 0;
-    if ((threadIdx.x & 31) == 0) v = atomicAdd(&R.cur[o], 0ull);
-    v = __shfl_sync(0xFFFFFFFFu, v, 0);
-    __threadfence();
-    off = v >> 24;
-    len = (int)(v & 0xFFFFFFull);
-}
-
-constexpr int DMAX = 256;
+constexpr int DMAX = 256;      // entries of a published column staged in shared memory
+constexpr int FCAP = 256;      // capacity of the front
+constexpr int ICAP = 512;      // capacity of the inbox
+constexpr int TT = 256;        // merged positions per tile of a merge of sorted runs
 constexpr int RED_WARPS = 4;
 
 struct WarpSmem {
-    uint64_t d[2][DMAX];
-    uint64_t c[DMAX + 1];
-    int q[DMAX];
+    uint64_t f[2][FCAP];   // the front: sorted, distinct (double buffered)
+    uint64_t in[ICAP];     // the inbox: unsorted, repeated entries cancel in pairs
+    uint64_t c[DMAX + 1];  // a staged published column
+    uint64_t cand[128];    // candidates of a front refill
+    uint64_t ta[TT + 1];   // merge windows
+    uint64_t tb[TT + 1];
+    int q[DMAX];           // merge scratch
     int pc[DMAX + 1];
-    uint64_t win[32];    // base[wbeg .. wbeg+32): cached head of the base
-    uint64_t mwin[32];   // the same for the middle level
-    uint32_t nv[64];     // ord32 values of the 4x4x4 vertices around a face (0 = outside)
-    uint8_t ndd[64];     // their primal hook codes
-    uint32_t xm[4];      // later-round H0 death bits of the face's four edges
 };
+constexpr size_t RED_SMEM = RED_WARPS * sizeof(WarpSmem);
 
-// ---------------------------------------------------------------------------
-// Apparent-pair test of a pivot face with one parallel load: lanes fetch the
-// 4x4x4 vertices around the face (values and hook codes) and the death bits
-// of the face's four edges; everything else is computed from shared memory.
-// ---------------------------------------------------------------------------
-struct NbView {
-    const uint32_t *nv;
-    const uint8_t *ndd;
-    int c[3];  // face anchor; the box starts at c - 1
-};
-__device__ __forceinline__ uint32_t nb_val(const NbView &N, int x, int y, int z) {
-    return N.nv[(x - N.c[0] + 1) + 4 * (y - N.c[1] + 1) + 16 * (z - N.c[2] + 1)];
-}
-__device__ __forceinline__ uint8_t nb_dd(const NbView &N, int x, int y, int z) {
-    return N.ndd[(x - N.c[0] + 1) + 4 * (y - N.c[1] + 1) + 16 * (z - N.c[2] + 1)];
-}
-__device__ __forceinline__ uint64_t nb_edge_key(const NbView &N, const Seg &S, int a, const int *c) {
-    int d[3] = {c[0], c[1], c[2]};
-    d[a] += 1;
-    uint32_t u = nb_val(N, c[0], c[1], c[2]), v = nb_val(N, d[0], d[1], d[2]);
-    return make_key(u > v ? u : v, cube_L(S, a, c[0], c[1], c[2]));
-}
-__device__ __forceinline__ uint64_t nb_face_key(const NbView &N, const Seg &S, int a, int b, const int *c) {
-    uint32_t m = 0;
-    for (int i = 0; i < 2; i++)
-        for (int j = 0; j < 2; j++) {
-            int d[3] = {c[0], c[1], c[2]};
-            d[a] += i;
-            d[b] += j;
-            uint32_t o = nb_val(N, d[0], d[1], d[2]);
-            m = o > m ? o : m;
-        }
-    return make_key(m, cube_L(S, a + b - 1, c[0], c[1], c[2]));
-}
-
-// returns the apparent edge key (0 if p is not an apparent pivot); on success
-// col[0..k) holds that edge's cofacets, sorted.  The scan marked every
-// apparent pivot face, so a miss costs one load; a hit loads the 4x4x4
-// vertices around the face in one parallel step.
-__device__ uint64_t apparent_warp(const Img3 &I, const Seg &S, uint64_t fk, WarpSmem &sm, uint64_t *col, int &k) {
-    const int lane = threadIdx.x & 31;
-    int fm, c[3];
-    decode_L(S, key_L(fk), fm, c);
-    {
-        int64_t bit = S.loff + key_L(fk);
-        if (!((__ldcg(&I.appmask[bit >> 5]) >> (bit & 31)) & 1u)) return 0;
-    }
-    int a = fm == 2 ? 1 : 0, b = fm == 0 ? 1 : 2;
-    __syncwarp();
-    for (int v = lane; v < 64; v += 32) {
-        int x = c[0] - 1 + (v & 3), y = c[1] - 1 + ((v >> 2) & 3), z = c[2] - 1 + (v >> 4);
-        bool in = x >= 0 && y >= 0 && z >= 0 && x < S.nx && y < S.ny && z < S.nz;
-        int64_t gv = S.voff + ((int64_t)z * S.ny + y) * S.nx + x;
-        sm.nv[v] = in ? ord32(I.img[gv]) : 0u;
-    }
-    __syncwarp();
-    NbView N{sm.nv, sm.ndd, {c[0], c[1], c[2]}};
-    // the face's latest facet: the apparent edge
-    uint64_t best = 0;
-    int ea = 0, ec[3] = {0, 0, 0};
-    for (int q = 0; q < 4; q++) {
-        int ax = q < 2 ? a : b, other = q < 2 ? b : a;
-        int d[3] = {c[0], c[1], c[2]};
-        d[other] += (q & 1);
-        uint64_t key = nb_edge_key(N, S, ax, d);
-        if (q == 0 || key > best) {
-            best = key;
-            ea = ax;
-            ec[0] = d[0]; ec[1] = d[1]; ec[2] = d[2];
-        }
-    }
-    // its cofacets (the face itself is the earliest of them)
-    int n = 0;
-    for (int bb = 0; bb < 3; bb++) {
-        if (bb == ea) continue;
-        int lo = ea < bb ? ea : bb, hi = ea < bb ? bb : ea;
-        if (ec[bb] + 1 < ext_of(S, bb)) col[n++] = nb_face_key(N, S, lo, hi, ec);
-        if (ec[bb] >= 1) {
-            int d[3] = {ec[0], ec[1], ec[2]};
-            d[bb] -= 1;
-            col[n++] = nb_face_key(N, S, lo, hi, d);
-        }
-    }
-    sort4(col, n);
-    k = n;
-    return best;
-}
-
-// Per-lane version for the lookahead: the apparent column of face fk by
-// direct loads; false if fk is not an apparent pivot.
 __device__ bool apparent_lane(const Img3 &I, const Seg &S, uint64_t fk, uint64_t &c1, uint64_t &c2, uint64_t &c3,
                               int &k) {
     int64_t bit = S.loff + key_L(fk);
@@ -751,28 +525,32 @@ __device__ bool apparent_lane(const Img3 &I, const Seg &S, uint64_t fk, uint64_t
     return true;
 }
 
-// Lookahead cache: one entry per lane, filled for the next entries of the
-// working column in one parallel step, so that most pivots need no
-// dependent global lookup.  kind 1 = apparent pivot (column tail c1..c3),
-// kind 2 = owned by column `own` with published version `ver` (a snapshot,
-// re-validated when the column is staged).
+// Lookahead cache: one entry per lane, filled for the next 32 entries of the
+// front in one parallel step, so that a pivot needs no dependent global
+// lookup.  kind 0 = neither apparent nor owned at the time of the fill,
+// kind 1 = apparent pivot (column tail c1..c3), kind 2 = owned by column
+// `own` with published version `ver` (a snapshot); when that version has at
+// most four entries and starts with the key, k > 0 and c1..c3 hold its tail.
 struct Look {
     uint64_t key, c1, c2, c3, ver;
     int kind, k, own;
 };
 
 // ---------------------------------------------------------------------------
-// Working column of one warp.  Entries below the current pivot are always
-// cancelled (an added column shares the pivot, all its other entries are
-// larger), so the column is kept as
-//   base[start..nb)  sorted, in global memory (consumed from the front), and
-//   delta[dh..nd)    sorted, in shared memory (recent additions),
-// whose symmetric difference is the column.  A small addition is a
-// shared-memory merge into delta; base is rebuilt only when delta fills.
+// Working column of one warp.  An added column shares the pivot and has only
+// larger entries, so the pivots of one column's reduction increase and the
+// column is kept in four parts whose symmetric difference it is:
+//   front   f[fb][fh..fn)  sorted, in shared memory: every entry <= tau;
+//   inbox   in[0..ni)      unsorted, in shared memory: entries > tau;
+//   middle  mg[mown][mstart..nm)  sorted, global (long columns only);
+//   base    g[bown][start..nb)    sorted, global.
+// Every entry of inbox, middle and base is larger than tau, so the pivot is
+// the front's first entry.  An addition toggles entries up to tau in the
+// front (a short merge) and appends the rest to the inbox; entries inserted
+// far behind the pivot -- the common case in long reductions -- cost one
+// shared-memory store.  When the front runs empty it is refilled with the
+// entries of the other three parts up to a new cut.
 // ---------------------------------------------------------------------------
-// The column is base xor mid xor delta.  The middle level (global, at most
-// MIDMAX entries) is used once the base is long: delta flushes then touch
-// only the middle level, and the base is rebuilt when the middle fills.
 constexpr int MIDMAX = 8192;
 constexpr int MID_ON = 8192;
 constexpr int MIDCAP = 2 * MIDMAX + DMAX;
@@ -782,11 +560,12 @@ struct Work {
     int cap;
     int bown;
     int nb, start;
-    int sb, dh, nd;
-    int wbeg;        // start of the cached window of the base (-1: none)
     uint64_t *mg[2]; // middle level buffers (null until first needed)
-    int mown, nm, mstart, mwbeg;
+    int mown, nm, mstart;
     bool mid_on;
+    int fb, fh, fn;  // the front
+    int ni;          // entries in the inbox
+    uint64_t tau;    // ~0: nothing lies beyond the front
 };
 
 // diagnostic counters (cnt[8..15]): iterations, apparent additions, column
@@ -928,32 +707,170 @@ __device__ int insert_merge(const uint64_t *A, int na, const uint64_t *D, int nD
     return na + nD - 2 * cancelled;
 }
 
-// fold delta into base (base <- base[start..nb) xor delta[dh..nd))
+// out = A xor B for sorted, distinct runs A and B, each read from global
+// memory through L2 (AG / BG) or from shared memory.  The merged order is
+// produced in tiles of TT positions: both runs are staged in windows of TT+1
+// entries (coalesced loads; the first TT+1 merged entries lie in them), each
+// lane merges TT/32 positions found by a merge-path search in shared memory,
+// and an entry equal to its neighbour in the merged order cancels.  Returns
+// the length of out, or -1 if it would exceed cap.
+template <bool AG, bool BG>
+__device__ int tiled_xor(const uint64_t *A, int na, const uint64_t *B, int nb, uint64_t *out, int cap, WarpSmem &sm) {
+    constexpr int PER = TT / 32;
+    const int lane = threadIdx.x & 31;
+    uint64_t *ta = sm.ta, *tb = sm.tb;
+    int i = 0, j = 0, no = 0;
+    uint64_t prev = 0;
+    bool hasprev = false;
+    while (i + j < na + nb) {
+        for (int k = lane; k <= TT; k += 32) {
+            ta[k] = i + k < na ? (AG ? ld_cg(A + i + k) : A[i + k]) : ~0ull;
+            tb[k] = j + k < nb ? (BG ? ld_cg(B + j + k) : B[j + k]) : ~0ull;
+        }
+        __syncwarp();
+        const int left = na + nb - i - j;
+        const int T = min(TT, left);
+        const int wa = min(TT + 1, na - i), wb = min(TT + 1, nb - j);
+        // A entries among the first d merged positions (ties: A first)
+        auto split = [&](int d) {
+            int lo = max(0, d - wb), hi = min(d, wa);
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (ta[mid] <= tb[d - 1 - mid]) lo = mid + 1; else hi = mid;
+            }
+            return lo;
+        };
+        const int s = min(lane * PER, T), e = min(s + PER, T);
+        int ia = split(s), ib = s - ia;
+        uint64_t pv = prev;
+        bool hp = hasprev;
+        if (s > 0) {
+            const uint64_t pa = ia > 0 ? ta[ia - 1] : 0ull, pb = ib > 0 ? tb[ib - 1] : 0ull;
+            pv = pa > pb ? pa : pb;
+            hp = true;
+        }
+        auto take = [&]() {
+            if (ia < wa && (ib >= wb || ta[ia] <= tb[ib])) return ta[ia++];
+            return tb[ib++];
+        };
+        uint64_t cur = s < e ? take() : 0ull;
+        uint64_t kv[PER];
+        unsigned kf = 0;
+#pragma unroll
+        for (int t = 0; t < PER; t++) {
+            kv[t] = 0ull;
+            if (s + t < e) {
+                const bool hn = s + t + 1 < left;
+                const uint64_t nx = hn ? take() : 0ull;  // the successor (may lie past the tile)
+                const bool dup = (hp && pv == cur) || (hn && nx == cur);
+                kv[t] = cur;
+                if (!dup) kf |= 1u << t;
+                pv = cur;
+                hp = true;
+                cur = nx;
+            }
+        }
+        int total;
+        const int base = warp_excl_scan(__popc(kf), total);
+        if (no + total > cap) return -1;
+#pragma unroll
+        for (int t = 0; t < PER; t++)
+            if ((kf >> t) & 1u) out[no + base + __popc(kf & ((1u << t) - 1u))] = kv[t];
+        no += total;
+        const int ca = split(T);
+        const uint64_t la = ca > 0 ? ta[ca - 1] : 0ull, lb = T - ca > 0 ? tb[T - ca - 1] : 0ull;
+        prev = la > lb ? la : lb;
+        hasprev = true;
+        i += ca;
+        j += T - ca;
+        __syncwarp();
+    }
+    return no;
+}
+
 // base <- base[start..nb) xor mid[mstart..nm); the middle level becomes empty
-__device__ bool merge_mid(const RedParams &R, Work &W, RedStats &st) {
+__device__ bool merge_mid(const RedParams &R, Work &W, WarpSmem &sm, RedStats &st) {
     int nmid = W.nm - W.mstart;
     if (nmid == 0) return true;
     int na = W.nb - W.start;
     const uint64_t *A = W.g[W.bown] + W.start;
     if ((int64_t)na + nmid > W.cap && !grow_to(R, W, (int64_t)na + nmid)) return false;
     int x = W.bown ^ 1;
-    int n = warp_xor<true, true>(A, na, W.mg[W.mown] + W.mstart, nmid, W.g[x], W.cap);
+    int n = tiled_xor<true, true>(A, na, W.mg[W.mown] + W.mstart, nmid, W.g[x], W.cap, sm);
     __threadfence_block();
     if (n < 0) return false;
     W.bown = x;
     W.nb = n;
     W.start = 0;
-    W.wbeg = -1;
     W.nm = W.mstart = 0;
-    W.mwbeg = -1;
     st.merged += (unsigned long long)(na + nmid);
     return true;
 }
 
-// fold delta into the middle level (long columns) or into the base
-__device__ bool flush_delta(const RedParams &R, Work &W, WarpSmem &sm, RedStats &st) {
-    int nd = W.nd - W.dh;
-    if (nd == 0) return true;
+// ascending sort of a[0..n) in shared memory by the warp; n a power of two, 2 <= n <= 256
+__device__ void warp_bitonic(uint64_t *a, int n) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < (n >> 1); t += 32) {
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));  // t with a zero bit inserted at j
+                const int l = i | j;
+                const uint64_t x = a[i], y = a[l];
+                if ((x > y) == ((i & k) == 0)) {
+                    a[i] = y;
+                    a[l] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// sort the inbox and cancel repeated entries in pairs: in[0..n) becomes
+// sorted and distinct; returns n
+__device__ int sort_inbox(WarpSmem &sm, int ni) {
+    const int lane = threadIdx.x & 31;
+    if (ni == 0) return 0;
+    int n2 = 32;
+    while (n2 < ni) n2 <<= 1;
+    for (int i = ni + lane; i < n2; i += 32) sm.in[i] = ~0ull;
+    __syncwarp();
+    warp_bitonic(sm.in, n2);
+    uint64_t v[ICAP / 32];
+    bool keep[ICAP / 32];
+#pragma unroll
+    for (int t = 0; t < ICAP / 32; t++) {
+        const int i = t * 32 + lane;
+        keep[t] = false;
+        v[t] = ~0ull;
+        if (i < n2) {
+            v[t] = sm.in[i];
+            if (v[t] != ~0ull && (i == 0 || sm.in[i - 1] != v[t])) {
+                int r = 1;
+                while (i + r < n2 && sm.in[i + r] == v[t]) r++;
+                keep[t] = r & 1;
+            }
+        }
+    }
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    int n = 0;
+#pragma unroll
+    for (int t = 0; t < ICAP / 32; t++) {
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep[t]);
+        if (keep[t]) sm.in[n + __popc(m & lt)] = v[t];
+        n += __popc(m);
+    }
+    __syncwarp();
+    return n;
+}
+
+// fold the inbox into the middle level (long columns) or into the base
+__device__ bool flush_inbox(const RedParams &R, Work &W, WarpSmem &sm, RedStats &st) {
+    TMARK(tf);
+    const int n = sort_inbox(sm, W.ni);
+    W.ni = 0;
+    if (n == 0) return true;
     if (!W.mid_on && W.nb - W.start > MID_ON) {
         if (!W.mg[0]) {
             const int lane = threadIdx.x & 31;
@@ -967,167 +884,172 @@ __device__ bool flush_delta(const RedParams &R, Work &W, WarpSmem &sm, RedStats 
         W.mid_on = true;
         W.mown = 0;
         W.nm = W.mstart = 0;
-        W.mwbeg = -1;
     }
-    TMARK(tf);
     if (W.mid_on) {
-        int nmid = W.nm - W.mstart;
-        int x = W.mown ^ 1;
-        int n = insert_merge<true>(W.mg[W.mown] + W.mstart, nmid, &sm.d[W.sb][W.dh], nd, W.mg[x], sm);
+        const int nmid = W.nm - W.mstart, x = W.mown ^ 1;
+        const int m = tiled_xor<true, false>(W.mg[W.mown] + W.mstart, nmid, sm.in, n, W.mg[x], MIDCAP, sm);
         __threadfence_block();
+        if (m < 0) return false;
         W.mown = x;
-        W.nm = n;
+        W.nm = m;
         W.mstart = 0;
-        W.mwbeg = -1;
-        W.dh = W.nd = 0;
-        st.merged += (unsigned long long)(nmid + nd);
-        if (W.nm > MIDMAX && !merge_mid(R, W, st)) return false;
+        st.merged += (unsigned long long)(nmid + n);
+        if (W.nm > MIDMAX && !merge_mid(R, W, sm, st)) return false;
     } else {
-        int na = W.nb - W.start;
+        const int na = W.nb - W.start;
         const uint64_t *A = W.g[W.bown] + W.start;
-        if ((int64_t)na + nd > W.cap && !grow_to(R, W, (int64_t)na + nd)) return false;
-        int x = W.bown ^ 1;
-        int n = insert_merge<true>(A, na, &sm.d[W.sb][W.dh], nd, W.g[x], sm);
+        if ((int64_t)na + n > W.cap && !grow_to(R, W, (int64_t)na + n)) return false;
+        const int x = W.bown ^ 1;
+        const int m = tiled_xor<true, false>(A, na, sm.in, n, W.g[x], W.cap, sm);
         __threadfence_block();
+        if (m < 0) return false;
         W.bown = x;
-        W.nb = n;
+        W.nb = m;
         W.start = 0;
-        W.dh = W.nd = 0;
-        W.wbeg = -1;
-        st.merged += (unsigned long long)(na + nd);
+        st.merged += (unsigned long long)(na + n);
     }
-    TADD(st, 5, tf);
     st.flush++;
+    TADD(st, 5, tf);
     return true;
 }
 
-// heads of the levels, through 32-entry windows in shared memory
-__device__ __forceinline__ uint64_t base_head(Work &W, WarpSmem &sm) {
-    if (W.start >= W.nb) return ~0ull;
-    if (W.wbeg < 0 || W.start >= W.wbeg + 32) {
-        const int lane = threadIdx.x & 31;
-        int i = W.start + lane;
-        __syncwarp();
-        sm.win[lane] = i < W.nb ? ld_cg(W.g[W.bown] + i) : ~0ull;
-        __syncwarp();
-        W.wbeg = W.start;
-    }
-    return sm.win[W.start - W.wbeg];
-}
-__device__ __forceinline__ uint64_t mid_head(Work &W, WarpSmem &sm) {
-    if (!W.mid_on || W.mstart >= W.nm) return ~0ull;
-    if (W.mwbeg < 0 || W.mstart >= W.mwbeg + 32) {
-        const int lane = threadIdx.x & 31;
-        int i = W.mstart + lane;
-        __syncwarp();
-        sm.mwin[lane] = i < W.nm ? ld_cg(W.mg[W.mown] + i) : ~0ull;
-        __syncwarp();
-        W.mwbeg = W.mstart;
-    }
-    return sm.mwin[W.mstart - W.mwbeg];
+// append x (lane e < m holds one entry) to the inbox
+__device__ __forceinline__ bool inbox_add(const RedParams &R, Work &W, WarpSmem &sm, uint64_t x, int m,
+                                          RedStats &st) {
+    const int lane = threadIdx.x & 31;
+    if (W.ni + m > ICAP && !flush_inbox(R, W, sm, st)) return false;
+    if (lane < m) sm.in[W.ni + lane] = x;
+    W.ni += m;
+    __syncwarp();
+    return true;
 }
 
-// the pivot (earliest face) of base xor mid xor delta; src = 1 base, 2 mid, 0 delta; ~0 if empty
-__device__ uint64_t pivot_of(Work &W, WarpSmem &sm, int &src) {
-    for (;;) {
-        uint64_t hb = base_head(W, sm);
-        uint64_t hm = mid_head(W, sm);
-        uint64_t hd = W.dh < W.nd ? sm.d[W.sb][W.dh] : ~0ull;
-        uint64_t m = hb < hm ? hb : hm;
-        m = m < hd ? m : hd;
-        if (m == ~0ull) return ~0ull;
-        int cnt = (hb == m) + (hm == m) + (hd == m);
-        if (cnt == 2) {  // two copies cancel
-            if (hb == m) W.start++;
-            if (hm == m) W.mstart++;
-            if (hd == m) W.dh++;
+// move the front's entries above t to the inbox; tau becomes t
+__device__ bool lower_tau(const RedParams &R, Work &W, WarpSmem &sm, uint64_t t, RedStats &st) {
+    const int lane = threadIdx.x & 31;
+    int lo = W.fh, hi = W.fn;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sm.f[W.fb][mid] <= t) lo = mid + 1; else hi = mid;
+    }
+    for (int s = lo; s < W.fn; s += 32) {
+        const int m = min(32, W.fn - s);
+        const uint64_t x = lane < m ? sm.f[W.fb][s + lane] : 0ull;
+        if (!inbox_add(R, W, sm, x, m, st)) return false;
+    }
+    W.fn = lo;
+    W.tau = t;
+    return true;
+}
+
+// The front is empty: take every entry of inbox xor middle xor base up to a
+// cut.  The cut is the smaller of the 32nd remaining entries of base and
+// middle, so that their entries up to it are in one 32-entry window each;
+// the candidates are sorted and entries present an even number of times cancel.
+__device__ bool front_refill(const RedParams &R, Work &W, WarpSmem &sm, RedStats &st) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    while (W.tau != ~0ull) {
+        const int nbr = W.nb - W.start, nmr = W.mid_on ? W.nm - W.mstart : 0;
+        const uint64_t bv = lane < nbr ? ld_cg(W.g[W.bown] + W.start + lane) : ~0ull;
+        const uint64_t mv = lane < nmr ? ld_cg(W.mg[W.mown] + W.mstart + lane) : ~0ull;
+        const uint64_t cb = __shfl_sync(0xFFFFFFFFu, bv, 31), cm = __shfl_sync(0xFFFFFFFFu, mv, 31);
+        uint64_t cut = nbr > 32 ? cb : ~0ull;
+        if (nmr > 32 && cm < cut) cut = cm;
+        int nic = 0;
+        for (int i0 = 0; i0 < W.ni; i0 += 32) {
+            const int i = i0 + lane;
+            nic += __popc(__ballot_sync(0xFFFFFFFFu, i < W.ni && sm.in[i] <= cut));
+        }
+        if (nic > 64) {  // the inbox joins the sorted levels first
+            if (!flush_inbox(R, W, sm, st)) return false;
             continue;
         }
-        if (cnt == 3) {  // three copies: two cancel, the delta copy remains
-            W.start++;
-            W.mstart++;
+        const bool tb = lane < nbr && bv <= cut, tm = lane < nmr && mv <= cut;
+        sm.cand[lane] = tb ? bv : ~0ull;
+        sm.cand[32 + lane] = tm ? mv : ~0ull;
+        sm.cand[64 + lane] = ~0ull;
+        sm.cand[96 + lane] = ~0ull;
+        __syncwarp();
+        int nk = 0, nt = 0;
+        for (int i0 = 0; i0 < W.ni; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < W.ni;
+            const uint64_t x = valid ? sm.in[i] : ~0ull;
+            const bool take = valid && x <= cut;
+            const unsigned mt = __ballot_sync(0xFFFFFFFFu, take), mk = __ballot_sync(0xFFFFFFFFu, valid && !take);
+            if (take) sm.cand[64 + nk + __popc(mt & lt)] = x;
+            if (valid && !take) sm.in[nt + __popc(mk & lt)] = x;  // never past this chunk's own slots
+            nk += __popc(mt);
+            nt += __popc(mk);
+            __syncwarp();
         }
-        src = (hd == m) ? 0 : ((hb == m) ? 1 : 2);
-        return m;
+        W.ni = nt;
+        W.start += __popc(__ballot_sync(0xFFFFFFFFu, tb));
+        if (W.mid_on) W.mstart += __popc(__ballot_sync(0xFFFFFFFFu, tm));
+        warp_bitonic(sm.cand, 128);
+        uint64_t *out = sm.f[W.fb];
+        int ns = 0;
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int i = t * 32 + lane;
+            const uint64_t v = sm.cand[i];
+            bool keep = false;
+            if (v != ~0ull && (i == 0 || sm.cand[i - 1] != v)) {
+                int r = 1;
+                while (i + r < 128 && sm.cand[i + r] == v) r++;
+                keep = r & 1;
+            }
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+            if (keep) out[ns + __popc(m & lt)] = v;
+            ns += __popc(m);
+        }
+        __syncwarp();
+        W.fh = 0;
+        W.fn = ns;
+        W.tau = cut;
+        if (ns > 0) return true;
     }
-}
-
-__device__ __forceinline__ void remove_pivot(Work &W, int src) {
-    if (src == 1) W.start++;
-    else if (src == 2) W.mstart++;
-    else W.dh++;
-}
-
-// add the column staged in sm.c[0..m) whose first entry is the current pivot
-__device__ bool add_staged(const RedParams &R, Work &W, WarpSmem &sm, int src, int m, RedStats &st) {
-    remove_pivot(W, src);
-    int mc = m - 1;
-    if (W.nd - W.dh + mc > DMAX) {
-        if (!flush_delta(R, W, sm, st)) return false;
-    }
-    int n = insert_merge<false>(&sm.d[W.sb][W.dh], W.nd - W.dh, &sm.c[1], mc, sm.d[W.sb ^ 1], sm);
-    W.sb ^= 1;
-    W.dh = 0;
-    W.nd = n;
     return true;
 }
 
-__device__ void look_refill(const RedParams &R, const Seg &S, Work &W, WarpSmem &sm, Look &L) {
-    const int lane = threadIdx.x & 31;
-    uint64_t cand = ~0ull;
-    if (lane < 10) {
-        int i = W.start + lane;
-        if (i < W.nb) cand = ld_cg(W.g[W.bown] + i);
-    } else if (lane < 20) {
-        int i = W.mstart + lane - 10;
-        if (W.mid_on && i < W.nm) cand = ld_cg(W.mg[W.mown] + i);
-    } else {
-        int i = W.dh + lane - 20;
-        if (i < W.nd) cand = sm.d[W.sb][i];
-    }
-    L.key = ~0ull;
-    L.kind = 0;
-    if (cand == ~0ull) return;
-    uint64_t c1, c2, c3;
-    int k;
-    if (apparent_lane(R.I, S, cand, c1, c2, c3, k)) {
-        L.key = cand;
-        L.kind = 1;
-        L.c1 = c1;
-        L.c2 = c2;
-        L.c3 = c3;
-        L.k = k;
-        return;
-    }
-    int o = __ldcg(&R.P[S.loff + key_L(cand)]);
-    if (o >= 0) {
-        L.key = cand;
-        L.kind = 2;
-        L.own = o;
-        L.ver = __ldcg(&R.cur[o]);
-    }
+// the working column's pivot after a refill of an empty front; ~0 if the column is empty
+__device__ __forceinline__ bool front_ready(const RedParams &R, Work &W, WarpSmem &sm, RedStats &st) {
+    if (W.fh < W.fn) return true;
+    TMARK(tr);
+    const bool ok = front_refill(R, W, sm, st);
+    TADD(st, 0, tr);
+    return ok;
 }
 
-// add a short column x0 < x1 < x2 < x3 (k <= 4 entries, x0 = current pivot;
-// unused entries are ~0): one pass over delta, no scratch arrays.  Lane e
-// locates entry e+1 in delta; the results are broadcast by shuffles.
-__device__ bool add_small(const RedParams &R, Work &W, WarpSmem &sm, int src, uint64_t x1, uint64_t x2,
-                          uint64_t x3, int k, RedStats &st) {
+// Toggle x1 < x2 < x3 (the first m of them; all above the removed pivot).
+// Entries up to tau are merged into the front in one pass (lane e locates
+// entry e in the front; results are broadcast by shuffles), the rest go to
+// the inbox.
+__device__ bool toggle_small(const RedParams &R, Work &W, WarpSmem &sm, uint64_t x1, uint64_t x2, uint64_t x3,
+                             int m, RedStats &st) {
     const int lane = threadIdx.x & 31;
-    remove_pivot(W, src);
-    const int m = k - 1;
-    if (W.nd - W.dh + m > DMAX) {
-        if (!flush_delta(R, W, sm, st)) return false;
+    int mlo = (m > 0 && x1 <= W.tau) + (m > 1 && x2 <= W.tau) + (m > 2 && x3 <= W.tau);
+    if (mlo > 0 && W.fn - W.fh + mlo > FCAP) {
+        if (!lower_tau(R, W, sm, sm.f[W.fb][W.fh + FCAP / 2 - 1], st)) return false;
+        mlo = (m > 0 && x1 <= W.tau) + (m > 1 && x2 <= W.tau) + (m > 2 && x3 <= W.tau);
     }
-    const uint64_t *D = &sm.d[W.sb][W.dh];
-    uint64_t *out = sm.d[W.sb ^ 1];
-    const int nd = W.nd - W.dh;
-    uint64_t mine = lane == 0 ? x1 : (lane == 1 ? x2 : x3);
+    const int mhi = m - mlo;
+    if (mhi > 0) {
+        const int e = mlo + lane;
+        const uint64_t v = e == 0 ? x1 : (e == 1 ? x2 : x3);
+        if (!inbox_add(R, W, sm, v, mhi, st)) return false;
+    }
+    if (mlo == 0) return true;
+    const uint64_t *D = &sm.f[W.fb][W.fh];
+    uint64_t *out = sm.f[W.fb ^ 1];
+    const int nd = W.fn - W.fh;
+    const uint64_t mine = lane == 0 ? x1 : (lane == 1 ? x2 : x3);
     int myq = 0, myeq = 0;
-    if (lane < m) {
+    if (lane < mlo) {
         int lo = 0, hi = nd;
         while (lo < hi) {
-            int mid = (lo + hi) >> 1;
+            const int mid = (lo + hi) >> 1;
             if (D[mid] < mine) lo = mid + 1; else hi = mid;
         }
         myq = lo;
@@ -1135,93 +1057,166 @@ __device__ bool add_small(const RedParams &R, Work &W, WarpSmem &sm, int src, ui
     }
     const int eq0 = __shfl_sync(0xFFFFFFFFu, myeq, 0), eq1 = __shfl_sync(0xFFFFFFFFu, myeq, 1),
               eq2 = __shfl_sync(0xFFFFFFFFu, myeq, 2);
-    const uint64_t v0 = m > 0 ? x1 : ~0ull, v1 = m > 1 ? x2 : ~0ull, v2 = m > 2 ? x3 : ~0ull;
+    const uint64_t v0 = x1, v1 = mlo > 1 ? x2 : ~0ull, v2 = mlo > 2 ? x3 : ~0ull;
     for (int i = lane; i < nd; i += 32) {
-        uint64_t d = D[i];
+        const uint64_t d = D[i];
         int ins = 0, can = 0;
         if (v0 < d) { if (eq0) can++; else ins++; }
         if (v1 < d) { if (eq1) can++; else ins++; }
         if (v2 < d) { if (eq2) can++; else ins++; }
-        bool drop = (v0 == d) | (v1 == d) | (v2 == d);
+        const bool drop = (v0 == d) | (v1 == d) | (v2 == d);
         if (!drop) out[i + ins - can] = d;
     }
-    if (lane < m && !myeq) {
-        int before_c = (lane > 0 ? eq0 : 0) + (lane > 1 ? eq1 : 0);
-        int before_nc = lane - before_c;
-        out[myq + before_nc - before_c] = mine;
+    if (lane < mlo && !myeq) {
+        const int before_c = (lane > 0 ? eq0 : 0) + (lane > 1 ? eq1 : 0);
+        out[myq + (lane - before_c) - before_c] = mine;
     }
     __syncwarp();
-    W.sb ^= 1;
-    W.dh = 0;
-    W.nd = nd + m - 2 * (eq0 + (m > 1 ? eq1 : 0) + (m > 2 ? eq2 : 0));
+    W.fb ^= 1;
+    W.fh = 0;
+    W.fn = nd + mlo - 2 * (eq0 + (mlo > 1 ? eq1 : 0) + (mlo > 2 ? eq2 : 0));
     return true;
 }
 
-// add a published column (arena, length len, first entry = current pivot)
-__device__ bool add_arena(const RedParams &R, Work &W, WarpSmem &sm, int src, const uint64_t *C, int len,
-                          RedStats &st) {
+// Toggle the sorted, distinct entries X[0..n) (all above the removed pivot),
+// read from shared memory or, XG, from the arena.  Entries up to tau are
+// merged into the front (tau is lowered first if the front would overflow),
+// a short rest goes to the inbox, a long rest straight into middle or base.
+template <bool XG>
+__device__ bool toggle_list(const RedParams &R, Work &W, WarpSmem &sm, const uint64_t *X, int n, RedStats &st) {
     const int lane = threadIdx.x & 31;
-    if (len - 1 <= DMAX) {
-        for (int k = lane; k < len; k += 32) sm.c[k] = ld_cg(C + k);
-        __syncwarp();
-        return add_staged(R, W, sm, src, len, st);
+    auto count_le = [&](uint64_t t) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((XG ? ld_cg(X + mid) : X[mid]) <= t) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    };
+    int nlo = count_le(W.tau);
+    if (nlo > 0 && W.fn - W.fh + nlo > FCAP) {
+        uint64_t t = ~0ull;
+        if (W.fn - W.fh > FCAP / 4) t = sm.f[W.fb][W.fh + FCAP / 4 - 1];
+        if (nlo > FCAP / 4) {
+            const uint64_t u = XG ? ld_cg(X + FCAP / 4 - 1) : X[FCAP / 4 - 1];
+            t = u < t ? u : t;
+        }
+        if (!lower_tau(R, W, sm, t, st)) return false;
+        nlo = count_le(W.tau);
     }
-    // a long column: fold delta into base, then merge base with the column's tail
-    remove_pivot(W, src);
-    if (!flush_delta(R, W, sm, st)) return false;
-    if (W.mid_on && len - 1 <= MIDMAX) {
-        // long column, long working column: fold the column into the middle level
-        int nmid = W.nm - W.mstart;
-        int x = W.mown ^ 1;
-        int n = warp_xor<true, true>(W.mg[W.mown] + W.mstart, nmid, C + 1, len - 1, W.mg[x], MIDCAP);
-        __threadfence_block();
-        if (n < 0) return false;
-        W.mown = x;
-        W.nm = n;
-        W.mstart = 0;
-        W.mwbeg = -1;
-        st.merged += (unsigned long long)(nmid + len);
-        if (W.nm > MIDMAX && !merge_mid(R, W, st)) return false;
+    if (nlo > 0) {
+        const uint64_t *D = X;
+        if (XG) {
+            for (int k = lane; k < nlo; k += 32) sm.c[k] = ld_cg(X + k);
+            __syncwarp();
+            D = sm.c;
+        }
+        const int nf = insert_merge<false>(&sm.f[W.fb][W.fh], W.fn - W.fh, D, nlo, sm.f[W.fb ^ 1], sm);
+        W.fb ^= 1;
+        W.fh = 0;
+        W.fn = nf;
+    }
+    const int nhi = n - nlo;
+    if (nhi == 0) return true;
+    const uint64_t *Xh = X + nlo;
+    if (nhi <= ICAP) {
+        if (W.ni + nhi > ICAP && !flush_inbox(R, W, sm, st)) return false;
+        for (int k = lane; k < nhi; k += 32) sm.in[W.ni + k] = XG ? ld_cg(Xh + k) : Xh[k];
+        W.ni += nhi;
+        __syncwarp();
         return true;
     }
-    if (W.mid_on && !merge_mid(R, W, st)) return false;
-    int na = W.nb - W.start;
+    // a long rest
+    if (!flush_inbox(R, W, sm, st)) return false;
+    if (W.mid_on && nhi <= MIDMAX) {
+        const int nmid = W.nm - W.mstart, x = W.mown ^ 1;
+        const int r = tiled_xor<true, XG>(W.mg[W.mown] + W.mstart, nmid, Xh, nhi, W.mg[x], MIDCAP, sm);
+        __threadfence_block();
+        if (r < 0) return false;
+        W.mown = x;
+        W.nm = r;
+        W.mstart = 0;
+        st.merged += (unsigned long long)(nmid + nhi);
+        if (W.nm > MIDMAX && !merge_mid(R, W, sm, st)) return false;
+        return true;
+    }
+    if (W.mid_on && !merge_mid(R, W, sm, st)) return false;
+    const int na = W.nb - W.start;
     const uint64_t *A = W.g[W.bown] + W.start;
-    if ((int64_t)na + len - 1 > W.cap && !grow_to(R, W, (int64_t)na + len - 1)) return false;
-    int x = W.bown ^ 1;
-    int n = warp_xor<true, true>(A, na, C + 1, len - 1, W.g[x], W.cap);
+    if ((int64_t)na + nhi > W.cap && !grow_to(R, W, (int64_t)na + nhi)) return false;
+    const int x = W.bown ^ 1;
+    const int r = tiled_xor<true, XG>(A, na, Xh, nhi, W.g[x], W.cap, sm);
     __threadfence_block();
-    if (n < 0) return false;
+    if (r < 0) return false;
     W.bown = x;
-    W.nb = n;
+    W.nb = r;
     W.start = 0;
-    W.wbeg = -1;
-    st.merged += (unsigned long long)(na + len);
+    st.merged += (unsigned long long)(na + nhi);
     return true;
+}
+
+__device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, const WarpSmem &sm, Look &L) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t cand = W.fh + lane < W.fn ? sm.f[W.fb][W.fh + lane] : ~0ull;
+    L.key = cand;
+    L.kind = 0;
+    L.k = 0;
+    if (cand == ~0ull) return;
+    uint64_t c1, c2, c3;
+    int k;
+    if (apparent_lane(R.I, S, cand, c1, c2, c3, k)) {
+        L.kind = 1;
+        L.c1 = c1;
+        L.c2 = c2;
+        L.c3 = c3;
+        L.k = k;
+        return;
+    }
+    const int o = __ldcg(&R.P[S.loff + key_L(cand)]);
+    if (o < 0) return;
+    const unsigned long long v = __ldcg(&R.cur[o]);
+    L.kind = 2;
+    L.own = o;
+    L.ver = v;
+    const int len = (int)(v & 0xFFFFFFull);
+    if (len >= 1 && len <= 4) {
+        const uint64_t *C = R.arena + (v >> 24);
+        const uint64_t h = ld_cg(C);
+        const uint64_t a1 = len > 1 ? ld_cg(C + 1) : ~0ull, a2 = len > 2 ? ld_cg(C + 2) : ~0ull,
+                       a3 = len > 3 ? ld_cg(C + 3) : ~0ull;
+        if (h == cand) {
+            L.c1 = a1;
+            L.c2 = a2;
+            L.c3 = a3;
+            L.k = len;
+        }
+    }
 }
 
 // publish the working column as column j's current version
 __device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &sm, RedStats &st) {
     const int lane = threadIdx.x & 31;
-    if (W.mid_on && W.nm - W.mstart > 0) {
-        if (!flush_delta(R, W, sm, st)) return false;
-        if (!merge_mid(R, W, st)) return false;
-    } else if (W.nb - W.start > 0 && W.nd - W.dh > 0) {
-        if (!flush_delta(R, W, sm, st)) return false;
+    const bool levels = W.nb - W.start > 0 || (W.mid_on && W.nm - W.mstart > 0);
+    const uint64_t *rest;
+    int nrest;
+    if (!levels) {
+        W.ni = sort_inbox(sm, W.ni);  // still the inbox (its order is free)
+        rest = sm.in;
+        nrest = W.ni;
+    } else {
+        if (!flush_inbox(R, W, sm, st)) return false;
+        if (W.mid_on && W.nm - W.mstart > 0 && !merge_mid(R, W, sm, st)) return false;
+        rest = W.g[W.bown] + W.start;
+        nrest = W.nb - W.start;
     }
-    if (W.mid_on && W.nm - W.mstart > 0 && !merge_mid(R, W, st)) return false;
-    int nbase = W.nb - W.start, nd = W.nd - W.dh;
-    int n = nbase + nd;
+    const int nf = W.fn - W.fh, n = nf + nrest;
     unsigned long long off = 0;
     if (lane == 0) off = atomicAdd(R.arena_top, (unsigned long long)n);
     off = __shfl_sync(0xFFFFFFFFu, off, 0);
     if ((int64_t)(off + n) > R.arena_cap) return false;
-    if (nbase > 0) {
-        const uint64_t *A = W.g[W.bown] + W.start;
-        for (int k = lane; k < nbase; k += 32) __stcg((unsigned long long *)&R.arena[off + k], ld_cg(A + k));
-    } else {
-        for (int k = lane; k < nd; k += 32) __stcg((unsigned long long *)&R.arena[off + k], sm.d[W.sb][W.dh + k]);
-    }
+    for (int k = lane; k < nf; k += 32) __stcg((unsigned long long *)&R.arena[off + k], sm.f[W.fb][W.fh + k]);
+    for (int k = lane; k < nrest; k += 32)
+        __stcg((unsigned long long *)&R.arena[off + nf + k], levels ? ld_cg(rest + k) : rest[k]);
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicExch(&R.cur[j], (off << 24) | (unsigned long long)n);
@@ -1230,8 +1225,9 @@ __device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &s
     return true;
 }
 
-__global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
-    __shared__ WarpSmem smem[RED_WARPS];
+__global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
+    extern __shared__ __align__(16) unsigned char red_smem[];
+    WarpSmem *smem = reinterpret_cast<WarpSmem *>(red_smem);
     const int lane = threadIdx.x & 31;
     WarpSmem &sm = smem[threadIdx.x >> 5];
     RedStats st;
@@ -1250,30 +1246,29 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
         jj = __shfl_sync(0xFFFFFFFFu, jj, 0);
         if ((int64_t)jj >= R.ncols) { flush_stats(R, st); return; }
         int64_t j = (int64_t)jj;
-        uint64_t jkey = R.colkey[j];
+        const uint64_t jkey = R.colkey[j];
         const Seg S = R.segs[R.colseg[j]];
-        // the coboundary of edge j becomes the delta; base is empty
+        // the coboundary of edge j is the front; nothing lies beyond it
         {
             int a, c[3];
             decode_L(S, key_L(jkey), a, c);
             uint64_t cf[4];
-            int k = edge_cofacets(R.I, S, a, c, cf);
+            const int k = edge_cofacets(R.I, S, a, c, cf);
             sort4(cf, k);
-            W.sb = 0;
-            if (lane < k) sm.d[0][lane] = cf[lane];
-            W.dh = 0;
-            W.nd = k;
+            if (lane < k) sm.f[0][lane] = cf[lane];
+            W.fb = 0;
+            W.fh = 0;
+            W.fn = k;
+            W.tau = ~0ull;
+            W.ni = 0;
             W.bown = 0;
             W.nb = W.start = 0;
-            W.wbeg = -1;
             W.mid_on = false;
             W.nm = W.mstart = 0;
-            W.mwbeg = -1;
             __syncwarp();
         }
         look.key = ~0ull;
         look.kind = 0;
-        bool refilled = false;
         int64_t it = 0;
         for (;;) {
             if (++it > CAP) { if (lane == 0) set_status(R.status, CR_ERR_TIMEOUT); flush_stats(R, st); return; }
@@ -1283,73 +1278,47 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
 #ifdef CR_H1_TIMING
             if (st.lng) st.t[7]++;
 #endif
-            int src = 0;
-            TMARK(t0);
-            uint64_t p = pivot_of(W, sm, src);
-            TADD(st, 0, t0);
-            if (p == ~0ull) { if (lane == 0) set_status(R.status, CR_ERR_INTERNAL); break; }
-            int64_t gidx = S.loff + key_L(p);
+            if (!front_ready(R, W, sm, st)) {
+                if (lane == 0) fail_ws(R.status, SITE_POOL);
+                flush_stats(R, st);
+                return;
+            }
+            if (W.fh == W.fn) { if (lane == 0) set_status(R.status, CR_ERR_INTERNAL); break; }
+            const uint64_t p = sm.f[W.fb][W.fh];
+            const int64_t gidx = S.loff + key_L(p);
             TMARK(t1);
             unsigned hit = __ballot_sync(0xFFFFFFFFu, look.key == p);
-            if (!hit && !refilled) {
-                look_refill(R, S, W, sm, look);
-                refilled = true;
+            if (!hit) {
+#ifdef CR_H1_TIMING
+                if (st.lng) st.t[6]++;
+#endif
+                look_refill(R, S, W, sm, look);  // p is lane 0's entry
                 hit = __ballot_sync(0xFFFFFFFFu, look.key == p);
             }
-            int hkind = 0, hown = -1;
-            unsigned long long hver = 0;
-            if (hit) {
-                int hl = __ffs(hit) - 1;  // cache lane holding the pivot
-                hkind = __shfl_sync(0xFFFFFFFFu, look.kind, hl);
-                if (hkind == 1) {
-                    uint64_t c1 = __shfl_sync(0xFFFFFFFFu, look.c1, hl);
-                    uint64_t c2 = __shfl_sync(0xFFFFFFFFu, look.c2, hl);
-                    uint64_t c3 = __shfl_sync(0xFFFFFFFFu, look.c3, hl);
-                    int kk = __shfl_sync(0xFFFFFFFFu, look.k, hl);
-                    TADD(st, 1, t1);
-                    st.app++;
-                    TMARK(t2);
-                    bool okadd = add_small(R, W, sm, src, c1, c2, c3, kk, st);
-                    TADD(st, 2, t2);
-                    if (!okadd) {
-                        if (lane == 0) fail_ws(R.status, SITE_POOL);
-                        flush_stats(R, st);
-                        return;
-                    }
-                    refilled = false;
-                    continue;
-                }
-                hown = __shfl_sync(0xFFFFFFFFu, look.own, hl);
-                hver = __shfl_sync(0xFFFFFFFFu, look.ver, hl);
-                if (lane == hl) look.key = ~0ull;  // used once; a stale snapshot is re-read directly
-            } else {
-                uint64_t cf[4];
-                int k = 0;
-                uint64_t ak = apparent_warp(R.I, S, p, sm, cf, k);
-                if (ak) {
-                    TADD(st, 1, t1);
-                    st.app++;
-                    TMARK(t2);
-                    bool okadd = add_small(R, W, sm, src, k > 1 ? cf[1] : ~0ull, k > 2 ? cf[2] : ~0ull,
-                                           k > 3 ? cf[3] : ~0ull, k, st);
-                    TADD(st, 2, t2);
-                    if (!okadd) {
-                        if (lane == 0) fail_ws(R.status, SITE_POOL);
-                        flush_stats(R, st);
-                        return;
-                    }
-                    refilled = false;
-                    continue;
-                }
-            }
+            const int hl = hit ? __ffs(hit) - 1 : 0;
+            const int hkind = hit ? __shfl_sync(0xFFFFFFFFu, look.kind, hl) : 0;
+            const uint64_t c1 = __shfl_sync(0xFFFFFFFFu, look.c1, hl), c2 = __shfl_sync(0xFFFFFFFFu, look.c2, hl),
+                           c3 = __shfl_sync(0xFFFFFFFFu, look.c3, hl);
+            const int hk = __shfl_sync(0xFFFFFFFFu, look.k, hl), hown = __shfl_sync(0xFFFFFFFFu, look.own, hl);
+            const unsigned long long hver = __shfl_sync(0xFFFFFFFFu, look.ver, hl);
+            if (hit && lane == hl) look.key = ~0ull;  // used once
             TADD(st, 1, t1);
-            TMARK(t3);
-            int o = hkind == 2 ? hown : __ldcg(&R.P[gidx]);
+            if (hkind == 1) {
+                st.app++;
+                TMARK(t2);
+                W.fh++;
+                const bool okadd = toggle_small(R, W, sm, c1, c2, c3, hk - 1, st);
+                TADD(st, 2, t2);
+                if (!okadd) {
+                    if (lane == 0) fail_ws(R.status, SITE_POOL);
+                    flush_stats(R, st);
+                    return;
+                }
+                continue;
+            }
+            const int o = hkind == 2 ? hown : __ldcg(&R.P[gidx]);
             if (o < 0) {
-                TMARK(t6);
-                bool okpub = publish_work(R, j, W, sm, st);
-                TADD(st, 6, t6);
-                if (!okpub) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
+                if (!publish_work(R, j, W, sm, st)) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
                 int prev = 0;
                 if (lane == 0) prev = atomicCAS(&R.P[gidx], -1, (int)j);
                 prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
@@ -1359,7 +1328,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
             }
             if ((int64_t)o == j) break;
             // columns are numbered in cohomology order: a smaller index is an earlier column
-            bool takeover = (int64_t)o > j;  // o is a later column: j takes its pivot, then continues with o
+            const bool takeover = (int64_t)o > j;  // o is a later column: j takes its pivot, then continues with o
             if (takeover) {
                 if (!publish_work(R, j, W, sm, st)) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
                 int prev = 0;
@@ -1367,12 +1336,25 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
                 prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
                 if (prev != o) { st.retry++; continue; }
                 st.take++;
-                p = pivot_of(W, sm, src);  // publishing may have folded delta into base
+                look.key = ~0ull;  // snapshots taken for column j's pivots
             }
-            unsigned long long ver = (hkind == 2 && !takeover) ? hver : __ldcg(&R.cur[o]);
-            refilled = false;
-            unsigned long long off = ver >> 24;
-            int len = (int)(ver & 0xFFFFFFull);
+            TMARK(t3);
+            if (hkind == 2 && !takeover && hk > 0) {
+                // the snapshot's version is short and was read with the fill
+                st.add++;
+                W.fh++;
+                const bool okadd = toggle_small(R, W, sm, c1, c2, c3, hk - 1, st);
+                TADD(st, 3, t3);
+                if (!okadd) {
+                    if (lane == 0) fail_ws(R.status, SITE_POOL);
+                    flush_stats(R, st);
+                    return;
+                }
+                continue;
+            }
+            const unsigned long long ver = (hkind == 2 && !takeover) ? hver : __ldcg(&R.cur[o]);
+            const unsigned long long off = ver >> 24;
+            const int len = (int)(ver & 0xFFFFFFull);
             if (len == 0) continue;
             bool ok2;
             if (len - 1 <= DMAX) {
@@ -1381,16 +1363,16 @@ __global__ void __launch_bounds__(RED_WARPS * 32) k_h1_reduce(RedParams R) {
                 __syncwarp();
                 if (sm.c[0] != p) { st.retry++; continue; }
                 st.add++;
-                TADD(st, 3, t3);
                 TMARK(t4);
-                ok2 = add_staged(R, W, sm, src, len, st);
+                W.fh++;
+                ok2 = toggle_list<false>(R, W, sm, sm.c + 1, len - 1, st);
                 TADD(st, 4, t4);
             } else {
                 if (ld_cg(&R.arena[off]) != p) { st.retry++; continue; }
                 st.add++;
-                TADD(st, 3, t3);
                 TMARK(t4);
-                ok2 = add_arena(R, W, sm, src, R.arena + off, len, st);
+                W.fh++;
+                ok2 = toggle_list<true>(R, W, sm, R.arena + off + 1, len - 1, st);
                 TADD(st, 4, t4);
             }
             if (!ok2) {
@@ -1506,7 +1488,16 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     unsigned blocks = (unsigned)((warps + RED_WARPS - 1) / RED_WARPS);
     prof_begin(st, STAGE_H1_REDUCE);
     CR_NOTE_LAUNCH();
-    k_h1_reduce<<<blocks, RED_WARPS * 32, 0, st>>>(R);
+    {
+        static int red_attr_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (red_attr_dev != dev) {
+            cudaFuncSetAttribute(k_h1_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RED_SMEM);
+            red_attr_dev = dev;
+        }
+    }
+    k_h1_reduce<<<blocks, RED_WARPS * 32, RED_SMEM, st>>>(R);
     prof_end(st, STAGE_H1_REDUCE, 12.0 * ncols);
     CR_NOTE_LAUNCH();
     k_h1_emit<<<nb1(ncols), 256, 0, st>>>(B.colkey, B.colseg, ncols, segs, B.P, B.cur, B.arena, pb, flags, status);
