@@ -491,7 +491,7 @@ __device__ __forceinline__ uint64_t ld_cg(const uint64_t *p) { return __ldcg((co
 
 constexpr int DMAX = 256;      // entries of a published column staged in shared memory
 constexpr int FCAP = 256;      // capacity of the front
-constexpr int ICAP = 512;      // capacity of the inbox
+constexpr int ICAP = 1024;     // capacity of the inbox
 constexpr int TT = 256;        // merged positions per tile of a merge of sorted runs
 constexpr int RED_WARPS = 4;
 
@@ -506,24 +506,6 @@ struct WarpSmem {
     int pc[DMAX + 1];
 };
 constexpr size_t RED_SMEM = RED_WARPS * sizeof(WarpSmem);
-
-__device__ bool apparent_lane(const Img3 &I, const Seg &S, uint64_t fk, uint64_t &c1, uint64_t &c2, uint64_t &c3,
-                              int &k) {
-    int64_t bit = S.loff + key_L(fk);
-    if (!((__ldcg(&I.appmask[bit >> 5]) >> (bit & 31)) & 1u)) return false;
-    int fm, c[3];
-    decode_L(S, key_L(fk), fm, c);
-    int ea, ec[3];
-    face_max_facet(I, S, fm, c, ea, ec);
-    uint64_t cf[4];
-    int n = edge_cofacets(I, S, ea, ec, cf);
-    sort4(cf, n);
-    c1 = n > 1 ? cf[1] : ~0ull;
-    c2 = n > 2 ? cf[2] : ~0ull;
-    c3 = n > 3 ? cf[3] : ~0ull;
-    k = n;
-    return true;
-}
 
 // Lookahead cache: one entry per lane, filled for the next 32 entries of the
 // front in one parallel step, so that a pivot needs no dependent global
@@ -807,7 +789,7 @@ __device__ bool merge_mid(const RedParams &R, Work &W, WarpSmem &sm, RedStats &s
     return true;
 }
 
-// ascending sort of a[0..n) in shared memory by the warp; n a power of two, 2 <= n <= 256
+// ascending sort of a[0..n) in shared memory by the warp; n a power of two, 2 <= n <= 1024
 __device__ void warp_bitonic(uint64_t *a, int n) {
     const int lane = threadIdx.x & 31;
     for (int k = 2; k <= n; k <<= 1) {
@@ -827,7 +809,9 @@ __device__ void warp_bitonic(uint64_t *a, int n) {
 }
 
 // sort the inbox and cancel repeated entries in pairs: in[0..n) becomes
-// sorted and distinct; returns n
+// sorted and distinct; returns n.  Survivors (the first entry of a run of odd
+// length) are marked in a read-only pass, then compacted in place chunk by
+// chunk (a chunk's survivors land no further than its own slots).
 __device__ int sort_inbox(WarpSmem &sm, int ni) {
     const int lane = threadIdx.x & 31;
     if (ni == 0) return 0;
@@ -836,32 +820,27 @@ __device__ int sort_inbox(WarpSmem &sm, int ni) {
     for (int i = ni + lane; i < n2; i += 32) sm.in[i] = ~0ull;
     __syncwarp();
     warp_bitonic(sm.in, n2);
-    uint64_t v[ICAP / 32];
-    bool keep[ICAP / 32];
-#pragma unroll
-    for (int t = 0; t < ICAP / 32; t++) {
+    unsigned keep = 0;  // bit t: entry t*32 + lane survives
+    for (int t = 0; t * 32 < n2; t++) {
         const int i = t * 32 + lane;
-        keep[t] = false;
-        v[t] = ~0ull;
-        if (i < n2) {
-            v[t] = sm.in[i];
-            if (v[t] != ~0ull && (i == 0 || sm.in[i - 1] != v[t])) {
-                int r = 1;
-                while (i + r < n2 && sm.in[i + r] == v[t]) r++;
-                keep[t] = r & 1;
-            }
+        const uint64_t v = sm.in[i];
+        if (v != ~0ull && (i == 0 || sm.in[i - 1] != v)) {
+            int r = 1;
+            while (i + r < n2 && sm.in[i + r] == v) r++;
+            if (r & 1) keep |= 1u << t;
         }
     }
     __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
     int n = 0;
-#pragma unroll
-    for (int t = 0; t < ICAP / 32; t++) {
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep[t]);
-        if (keep[t]) sm.in[n + __popc(m & lt)] = v[t];
+    for (int t = 0; t * 32 < n2; t++) {
+        const bool k = (keep >> t) & 1u;
+        const uint64_t v = sm.in[t * 32 + lane];
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, k);
+        if (k) sm.in[n + __popc(m & lt)] = v;
         n += __popc(m);
+        __syncwarp();
     }
-    __syncwarp();
     return n;
 }
 
@@ -1155,6 +1134,11 @@ __device__ bool toggle_list(const RedParams &R, Work &W, WarpSmem &sm, const uin
     return true;
 }
 
+// Fill the lookahead cache for the front's next 32 entries.  The apparent
+// bit, the owner and the face's four vertices are read in one round trip; an
+// apparent face then needs its latest facet's cofacets (a second), an owned
+// face its owner's version and, when short, that version's entries (a second
+// and a third).
 __device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, const WarpSmem &sm, Look &L) {
     const int lane = threadIdx.x & 31;
     const uint64_t cand = W.fh + lane < W.fn ? sm.f[W.fb][W.fh + lane] : ~0ull;
@@ -1162,17 +1146,47 @@ __device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, con
     L.kind = 0;
     L.k = 0;
     if (cand == ~0ull) return;
-    uint64_t c1, c2, c3;
-    int k;
-    if (apparent_lane(R.I, S, cand, c1, c2, c3, k)) {
+    const uint32_t fl = key_L(cand);
+    int fm, c[3];
+    decode_L(S, fl, fm, c);
+    const int a = fm == 2 ? 1 : 0, b = fm == 0 ? 1 : 2;
+    const int64_t bit = S.loff + fl;
+    const int64_t v0 = S.voff + ((int64_t)c[2] * S.ny + c[1]) * S.nx + c[0];
+    const int64_t da = a == 0 ? 1 : (int64_t)S.nx, db = b == 1 ? (int64_t)S.nx : (int64_t)S.nx * S.ny;
+    const uint32_t am = __ldcg(&R.I.appmask[bit >> 5]);
+    const int o = __ldcg(&R.P[bit]);
+    const float g0 = R.I.img[v0], g1 = R.I.img[v0 + da], g2 = R.I.img[v0 + db], g3 = R.I.img[v0 + da + db];
+    if ((am >> (bit & 31)) & 1u) {
+        // the face's latest facet: the apparent edge
+        const uint32_t u0 = ord32(g0), u1 = ord32(g1), u2 = ord32(g2), u3 = ord32(g3);
+        int ea = a, ec[3] = {c[0], c[1], c[2]};
+        uint64_t best = make_key(u0 > u1 ? u0 : u1, cube_L(S, a, c[0], c[1], c[2]));
+        {
+            int d[3] = {c[0], c[1], c[2]};
+            d[b] += 1;
+            const uint64_t k1 = make_key(u2 > u3 ? u2 : u3, cube_L(S, a, d[0], d[1], d[2]));
+            if (k1 > best) { best = k1; ea = a; ec[0] = d[0]; ec[1] = d[1]; ec[2] = d[2]; }
+        }
+        {
+            const uint64_t k2 = make_key(u0 > u2 ? u0 : u2, cube_L(S, b, c[0], c[1], c[2]));
+            if (k2 > best) { best = k2; ea = b; ec[0] = c[0]; ec[1] = c[1]; ec[2] = c[2]; }
+        }
+        {
+            int d[3] = {c[0], c[1], c[2]};
+            d[a] += 1;
+            const uint64_t k3 = make_key(u1 > u3 ? u1 : u3, cube_L(S, b, d[0], d[1], d[2]));
+            if (k3 > best) { best = k3; ea = b; ec[0] = d[0]; ec[1] = d[1]; ec[2] = d[2]; }
+        }
+        uint64_t cf[4];
+        const int n = edge_cofacets(R.I, S, ea, ec, cf);
+        sort4(cf, n);
         L.kind = 1;
-        L.c1 = c1;
-        L.c2 = c2;
-        L.c3 = c3;
-        L.k = k;
+        L.c1 = n > 1 ? cf[1] : ~0ull;
+        L.c2 = n > 2 ? cf[2] : ~0ull;
+        L.c3 = n > 3 ? cf[3] : ~0ull;
+        L.k = n;
         return;
     }
-    const int o = __ldcg(&R.P[S.loff + key_L(cand)]);
     if (o < 0) return;
     const unsigned long long v = __ldcg(&R.cur[o]);
     L.kind = 2;
