@@ -221,6 +221,16 @@ def roofline_from(stages, peaks, sustained=True):
             "limiter": LIMITER.get(best, "hbm")}
 
 
+def tune_candidates(W, data):
+    """Knob values the autotuner tries for a workload (knobs that cannot change its launches are left out:
+    a batch or a volume always fills every SM with union-find blocks; only volumes run the reduction)."""
+    if W["kind"] == "batch":
+        return {"uf_compact": [1, 2, 4, 8]}
+    if len(data.shape) == 3 and min(data.shape) > 1:
+        return {"red_warps": [8, 16], "uf_compact": [1, 4]}
+    return {"uf_items": [2, 4, 8, 16, 32], "uf_compact": [1, 2, 4, 8]}
+
+
 def workload_config(args, W, data, world):
     """The config object of the JSON line (the same for both arms)."""
     return {"workload": args.workload,
@@ -284,6 +294,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop (profiling runs)")
+    ap.add_argument("--autotune", default="on", choices=["on", "off"],
+                    help="pick the library's launch knobs by timing candidates before the warm-up (not timed)")
     ap.add_argument("--size", type=int, default=None,
                     help="side length override of a single-image workload (same recipe; profiling on smaller cases)")
     args = ap.parse_args()
@@ -366,6 +378,18 @@ def main():
             life = torch.where(sel, p.death - p.birth, torch.zeros_like(p.birth))
             g = cr.cr_backward_batched(flat, shapes, offs, bp, -2 * life, 2 * life)
             return g
+
+    # -------- launch knobs: tuned offline, before the warm-up, outside every timed region --------
+    tuning = None
+    if args.autotune == "on":
+        from paper_2005_12692_gb300 import autotune as at
+        t0 = time.time()
+        try:
+            res = at.autotune(step, tune_candidates(W, data), warmup=2, repeats=3)
+            tuning = {"best": res.best, "seconds": round(time.time() - t0, 2), "table": res.as_dict()["table"]}
+        except cr.CRError as e:  # keep the default launch shapes
+            at.apply(at.DEFAULTS)
+            tuning = {"error": str(e)[:200], "best": at.current()}
 
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     clocks.start()
@@ -527,6 +551,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": metric.split()[0], "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
+            "tuning": tuning,
             "plain_path": plain,
             "localised_images": images,
             "stages": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps}

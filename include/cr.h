@@ -237,6 +237,30 @@ int64_t cr_launch_count(void);
  * buffer growths, most iterations spent on one column.  Host-only. */
 int cr_h1_last_stats(int64_t *out, int n);
 
+/* Launch knobs, set by the autotuner (host-side, per process).  They change
+ * how many blocks or warps a kernel is launched with, never what it computes:
+ *   CR_TUNE_UF_ITEMS   work items per thread that the cooperative union-find
+ *                      grids aim for: blocks = min(SMs, work / (items * 1024) + 1);
+ *                      1..64, default 8.  A smaller value launches more blocks
+ *                      for mid-size inputs: more parallel work, more blocks
+ *                      arriving at every grid barrier.
+ *   CR_TUNE_RED_WARPS  warps per SM working on the middle-dimension reduction
+ *                      of 3D images; 1..16, default 16 (the workspace is sized
+ *                      for 16).
+ *   CR_TUNE_UF_COMPACT the union-find rounds compact their edge list while it
+ *                      holds more than this many edges per launched thread,
+ *                      then mark dead edges in place; 1..64, default 1.
+ * cr_tune_set returns CR_ERR_INVALID_ARG for an unknown knob or a value out of
+ * range (the knob keeps its value); cr_tune_get writes the current value to
+ * *value.  A launch sequence cached as a CUDA graph is captured afresh after a
+ * knob changes.  Host-only. */
+#define CR_TUNE_UF_ITEMS 0
+#define CR_TUNE_RED_WARPS 1
+#define CR_TUNE_UF_COMPACT 2
+#define CR_TUNE_COUNT 3
+int cr_tune_set(int knob, int value);
+int cr_tune_get(int knob, int *value);
+
 /* Static description of an error code. */
 const char *cr_error_string(int code);
 

@@ -38,6 +38,11 @@ CR_ERR_INTERNAL = -8
 
 CR_KEEP_ZERO = 1
 CR_TOPDIM_ONLY = 2
+
+# launch knobs (cr_tune_set)
+CR_TUNE_UF_ITEMS = 0
+CR_TUNE_RED_WARPS = 1
+CR_TUNE_UF_COMPACT = 2
 CR_PAIR_ESSENTIAL = 1
 
 PAIR_BYTES = 32
@@ -102,6 +107,10 @@ def lib() -> ctypes.CDLL:
         L.cr_last_error_detail.argtypes = []
         L.cr_error_string.restype = ctypes.c_char_p
         L.cr_error_string.argtypes = [ctypes.c_int]
+        L.cr_tune_set.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.cr_tune_set.restype = ctypes.c_int
+        L.cr_tune_get.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.cr_tune_get.restype = ctypes.c_int
         for f in ("cr_workspace_size", "cr_workspace_size_typical", "cr_workspace_size_batched",
                   "cr_workspace_size_batched_typical", "cr_persistence", "cr_persistence_batched",
                   "cr_backward_workspace_size", "cr_backward", "cr_backward_batched", "cr_cell_location",
@@ -121,6 +130,17 @@ def _check(rc: int):
 
 def error_string(code: int) -> str:
     return lib().cr_error_string(code).decode()
+
+
+def cr_tune_set(knob: int, value: int) -> None:
+    """Set a launch knob of the library (see include/cr.h); raises on an unknown knob or a bad value."""
+    _check(lib().cr_tune_set(int(knob), int(value)))
+
+
+def cr_tune_get(knob: int) -> int:
+    v = ctypes.c_int(0)
+    _check(lib().cr_tune_get(int(knob), ctypes.byref(v)))
+    return v.value
 
 
 def cell_location(L: int, dim: int, shape: Sequence[int]):
@@ -462,5 +482,6 @@ class PersistentHomology(torch.autograd.Function):
 __all__ = [
     "build", "lib", "cr_persistence", "cr_persistence_batched", "cr_backward", "cr_backward_batched",
     "PersistentHomology", "Pairs", "BatchedPairs", "CRError", "cell_location", "error_string",
-    "CR_KEEP_ZERO", "CR_TOPDIM_ONLY",
+    "CR_KEEP_ZERO", "CR_TOPDIM_ONLY", "cr_tune_set", "cr_tune_get",
+    "CR_TUNE_UF_ITEMS", "CR_TUNE_RED_WARPS", "CR_TUNE_UF_COMPACT",
 ]

@@ -15,6 +15,16 @@
 
 namespace cr {
 
+// ---------------------------------------------------------------------------
+// Launch knobs (host-side, per process): see cr_tune_set in include/cr.h.
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_tune[CR_TUNE_COUNT] = {{8}, {16}, {1}};
+static std::atomic<uint32_t> g_tune_epoch{0};
+static const int g_tune_lo[CR_TUNE_COUNT] = {1, 1, 1}, g_tune_hi[CR_TUNE_COUNT] = {64, 16, 64};
+int tune_value(int knob) { return g_tune[knob].load(std::memory_order_relaxed); }
+uint32_t tune_epoch() { return g_tune_epoch.load(std::memory_order_relaxed); }
+
+
 static thread_local int g_detail = 0;
 void set_host_detail(int site) { g_detail = site; }
 
@@ -339,11 +349,12 @@ struct GraphKey {
     bool prof_on;
     uint32_t prof_mask;
     bool serial;
+    uint32_t tune;  // knob epoch: launch shapes were fixed at capture
     bool operator==(const GraphKey &o) const {
         return img == o.img && vtot == o.vtot && nx == o.nx && ny == o.ny && nz == o.nz && maxdim == o.maxdim &&
                flags == o.flags && pairs == o.pairs && capacity == o.capacity && ws == o.ws &&
                ws_bytes == o.ws_bytes && st == o.st && device == o.device && prof_on == o.prof_on &&
-               prof_mask == o.prof_mask && serial == o.serial;
+               prof_mask == o.prof_mask && serial == o.serial && tune == o.tune;
     }
 };
 struct GraphEntry {
@@ -597,7 +608,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     if (n == 1 && !P.any_mid) {
         const Seg &S0 = P.segs[0];
         GraphKey key{imgs, P.vtot, S0.nx, S0.ny, S0.nz, maxdim, flags, pairs_out, capacity, ws, ws_bytes, st,
-                     current_device(), prof_active(), prof_mask(), P.serial_uf};
+                     current_device(), prof_active(), prof_mask(), P.serial_uf, tune_epoch()};
         rc = run_graphed(key, phase1, st);
     } else {
         rc = phase1(st);
@@ -836,6 +847,20 @@ int persistence_serial(const float *img, int ndim, const int64_t *shape, int max
 }  // namespace cr
 
 extern "C" {
+
+int cr_tune_set(int knob, int value) {
+    if (knob < 0 || knob >= CR_TUNE_COUNT) return CR_ERR_INVALID_ARG;
+    if (value < cr::g_tune_lo[knob] || value > cr::g_tune_hi[knob]) return CR_ERR_INVALID_ARG;
+    if (cr::g_tune[knob].exchange(value) != value) cr::g_tune_epoch.fetch_add(1);
+    return CR_OK;
+}
+
+int cr_tune_get(int knob, int *value) {
+    if (knob < 0 || knob >= CR_TUNE_COUNT || !value) return CR_ERR_INVALID_ARG;
+    *value = cr::tune_value(knob);
+    return CR_OK;
+}
+
 
 int cr_workspace_size(int ndim, const int64_t *shape, int maxdim, uint32_t flags, size_t *bytes) {
     if (!bytes) return CR_ERR_INVALID_ARG;

@@ -1498,7 +1498,11 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     R.next = &B.cnt[2];
     R.stats = &B.cnt[8];
     R.status = status;
-    int64_t warps = B.nwarps < ncols ? B.nwarps : ncols;
+    // B.nwarps = 16 warps per SM (the scratch is sized for them); the knob may launch fewer
+    int64_t warps = B.nwarps / 16 * tune_value(CR_TUNE_RED_WARPS);
+    if (warps > B.nwarps) warps = B.nwarps;
+    if (warps > ncols) warps = ncols;
+    if (warps < 1) warps = 1;
     unsigned blocks = (unsigned)((warps + RED_WARPS - 1) / RED_WARPS);
     prof_begin(st, STAGE_H1_REDUCE);
     CR_NOTE_LAUNCH();

@@ -360,4 +360,8 @@ void prof_flush();
 void prof_add_bytes(int stage, double bytes);
 #define CR_NOTE_LAUNCH() (::cr::g_launch_count.fetch_add(1, std::memory_order_relaxed))
 
+// launch knobs (cr_tune_set); tune_epoch() changes whenever one does
+int tune_value(int knob);
+uint32_t tune_epoch();
+
 }  // namespace cr

@@ -1003,6 +1003,7 @@ constexpr int MAX_GRAPHS = 2;
 struct RoundArgs {
     UF u[MAX_GRAPHS];
     int ngraph;
+    int compact_mult;  // compact the edge list while it holds > compact_mult edges per thread
     int *status;
 };
 
@@ -1378,7 +1379,7 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_uf_rounds(RoundArgs A) {
                 continue;
             }
             any = true;
-            S.compact = !S.inplace && S.ne > nthr;
+            S.compact = !S.inplace && S.ne > nthr * (int64_t)A.compact_mult;
             if (tid == 0) {
                 if (S.compact) *(S.cur ? &u.cnt[UFC_E0] : &u.cnt[UFC_E1]) = 0;
                 u.cnt[UFC_VISITED] += (unsigned long long)S.live;  // for the algorithmic byte count
@@ -1465,7 +1466,7 @@ static int sm_count() {
 // one 1024-thread block per SM at most (short barriers), fewer for small work
 static int coop_blocks(int64_t work) {
     const int64_t maxb = sm_count();
-    const int64_t want = work / (8 * UF_THREADS) + 1;
+    const int64_t want = work / ((int64_t)tune_value(CR_TUNE_UF_ITEMS) * UF_THREADS) + 1;
     const int blocks = (int)(want < maxb ? want : maxb);
     return blocks < 1 ? 1 : blocks;
 }
@@ -1567,6 +1568,7 @@ int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
     {
         RoundArgs A{};
         A.status = status;
+        A.compact_mult = tune_value(CR_TUNE_UF_COMPACT);
         for (UF *u : {u0, u1})
             if (u) A.u[A.ngraph++] = *u;
         void *args[] = {&A};
