@@ -102,6 +102,43 @@ int cr_persistence(const float *img, int ndim, const int64_t *shape, int maxdim,
                    int64_t capacity, int64_t *n_pairs, void *ws, size_t ws_bytes, cr_stream_t stream,
                    uint32_t flags);
 
+/* Pairs of a float64 image: as cr_pair, with double birth and death.
+ * 40 bytes. */
+typedef struct {
+    int32_t dim;
+    uint32_t flags; /* bit 0: essential */
+    double birth;
+    double death;
+    int64_t birth_cell;
+    int64_t death_cell;
+} cr_pair64;
+
+/* Workspace for cr_persistence_f64: the float64 extras (about 48 bytes per
+ * voxel, plus 32 bytes per pair of capacity) and the float32 path's
+ * workspace (the bound if typical == 0, the typical size otherwise).
+ * Host-only. */
+int cr_workspace_size_f64(int ndim, const int64_t *shape, int maxdim, uint32_t flags, int64_t capacity,
+                          int typical, size_t *bytes);
+
+/*
+ * Persistent homology of one float64 image, the precision of the paper's
+ * timing study (its datasets were converted to double, Sec. 3).  The
+ * filtration depends on the values only through their order (cells enter by
+ * value, ties by the fixed index order, Sec. 2), so the call ranks the
+ * distinct values on the device (-0.0 = +0.0; one 64-bit radix sort), runs the
+ * float32 path on the image of ranks and maps each pair's values back: the
+ * result equals the persistence of the float64 image.
+ *   img       device float64[prod(shape)], C-order; fewer than 2^31 voxels.
+ *   pairs_out device cr_pair64[capacity], sorted by (dim, birth, birth_cell).
+ *   ws        device, 256-byte aligned, cr_workspace_size_f64 bytes for this
+ *             capacity.
+ * Other arguments, flags and errors as cr_persistence; a NaN gives
+ * CR_ERR_NAN before the float32 path runs.
+ */
+int cr_persistence_f64(const double *img, int ndim, const int64_t *shape, int maxdim, cr_pair64 *pairs_out,
+                       int64_t capacity, int64_t *n_pairs, void *ws, size_t ws_bytes, cr_stream_t stream,
+                       uint32_t flags);
+
 /* Workspace for cr_persistence_batched over these images (shapes: host
  * int32[n_images * ndim], each row the extents of one image). */
 int cr_workspace_size_batched(const int32_t *shapes, int n_images, int ndim, int maxdim, uint32_t flags,

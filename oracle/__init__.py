@@ -6,6 +6,7 @@ Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 from .oracle import (  # noqa: F401
     build,
     persistence,
+    persistence_f64,
     num_cells,
     cell_value,
     cell_vertices,

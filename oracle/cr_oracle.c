@@ -3,7 +3,8 @@
  *
  * A plain, slow, single-threaded CPU computation of the persistent homology
  * (coefficients Z/2) of the weighted cubical complex of a 1D/2D/3D float32
- * array under the V-construction.  It exists so that the CUDA path can be
+ * or float64 array under the V-construction (values are held in double; a
+ * float32 input is promoted exactly).  It exists so that the CUDA path can be
  * checked against something obviously correct; only the test suite, the
  * smoke check and the CPU-baseline leg of the benchmark may load it.  It
  * shares no code, header or table with the CUDA library.
@@ -51,7 +52,7 @@
 #define CRO_ERR_NOMEM (-4)
 
 typedef struct {
-    float value;     /* birth-time of the cube */
+    double value;    /* birth-time of the cube (float32 inputs are promoted exactly) */
     int32_t dim;     /* 0..3 */
     int32_t m;       /* type */
     int64_t x, y, z; /* anchor (minimum corner) */
@@ -98,13 +99,13 @@ static int cube_exists(int span, int64_t x, int64_t y, int64_t z, int64_t nz, in
 }
 
 /* value of a cube: maximum over its vertices */
-static float cube_value(const float *img, int span, int64_t x, int64_t y, int64_t z, int64_t ny, int64_t nx) {
-    float v = -INFINITY;
+static double cube_value(const double *img, int span, int64_t x, int64_t y, int64_t z, int64_t ny, int64_t nx) {
+    double v = -INFINITY;
     int first = 1;
     for (int dz = 0; dz <= ((span >> 2) & 1); dz++)
         for (int dy = 0; dy <= ((span >> 1) & 1); dy++)
             for (int dx = 0; dx <= (span & 1); dx++) {
-                float w = img[((z + dz) * ny + (y + dy)) * nx + (x + dx)];
+                double w = img[((z + dz) * ny + (y + dy)) * nx + (x + dx)];
                 if (first || w > v) { v = w; first = 0; }
             }
     return v;
@@ -170,7 +171,8 @@ static int cmp_i64(const void *pa, const void *pb) {
 
 /*
  * Full persistence of the V-construction complex.
- *   img      : dense C-order float32 array (x fastest)
+ *   img      : dense C-order array (x fastest), float64 here; the float32
+ *              entry point below promotes its input exactly
  *   ndim     : 1, 2 or 3; shape[ndim] extents, each >= 1
  *   twist    : 1 = reduce dimensions top-down with clearing, 0 = plain
  *              left-to-right reduction over all columns
@@ -178,9 +180,9 @@ static int cmp_i64(const void *pa, const void *pb) {
  * Output: every pair, zero-length ones included, in the order the reduction
  * finds them; essential classes have death = +inf and death_L = -1.
  */
-int cro_persistence(const float *img, int ndim, const int64_t *shape, int twist, int64_t capacity,
-                    int32_t *out_dim, float *out_birth, float *out_death, int64_t *out_birth_L,
-                    int64_t *out_death_L, int64_t *n_out) {
+static int persistence_core(const double *img, int ndim, const int64_t *shape, int twist, int64_t capacity,
+                            int32_t *out_dim, double *out_birth, double *out_death, int64_t *out_birth_L,
+                            int64_t *out_death_L, int64_t *n_out) {
     if (!img || !shape || !n_out || ndim < 1 || ndim > 3) return CRO_ERR_INVALID_ARG;
     int64_t nz, ny, nx;
     canonical_shape(ndim, shape, &nz, &ny, &nx);
@@ -188,12 +190,12 @@ int cro_persistence(const float *img, int ndim, const int64_t *shape, int twist,
     int64_t nv = nz * ny * nx;
 
     /* step 1: validate and canonicalise */
-    float *f = (float *)malloc((size_t)nv * sizeof(float));
+    double *f = (double *)malloc((size_t)nv * sizeof(double));
     if (!f) return CRO_ERR_NOMEM;
     for (int64_t i = 0; i < nv; i++) {
-        float w = img[i];
+        double w = img[i];
         if (isnan(w)) { free(f); return CRO_ERR_NAN; }
-        f[i] = (w == 0.0f) ? 0.0f : w;
+        f[i] = (w == 0.0) ? 0.0 : w;
     }
 
     /* step 2: enumerate all cubes */
@@ -318,5 +320,42 @@ done:
     for (int64_t i = 0; i < ncell; i++) free(reduced[i].v);
     free(reduced); free(cur.v); free(tmp.v); free(order);
     free(f); free(cells); free(pos); free(low_owner); free(partner); free(cleared);
+    return rc;
+}
+
+/* float64 input: the values of the paper's timing study (its datasets were
+ * converted to double, Sec. 3) */
+int cro_persistence_f64(const double *img, int ndim, const int64_t *shape, int twist, int64_t capacity,
+                        int32_t *out_dim, double *out_birth, double *out_death, int64_t *out_birth_L,
+                        int64_t *out_death_L, int64_t *n_out) {
+    return persistence_core(img, ndim, shape, twist, capacity, out_dim, out_birth, out_death, out_birth_L,
+                            out_death_L, n_out);
+}
+
+/* float32 input: promoted to double exactly, values reported back in float32
+ * (every reported value is an input value, so the conversion back is exact) */
+int cro_persistence(const float *img, int ndim, const int64_t *shape, int twist, int64_t capacity,
+                    int32_t *out_dim, float *out_birth, float *out_death, int64_t *out_birth_L,
+                    int64_t *out_death_L, int64_t *n_out) {
+    if (!img || !shape || !n_out || ndim < 1 || ndim > 3) return CRO_ERR_INVALID_ARG;
+    int64_t nz, ny, nx;
+    canonical_shape(ndim, shape, &nz, &ny, &nx);
+    if (nz < 1 || ny < 1 || nx < 1) return CRO_ERR_INVALID_ARG;
+    int64_t nv = nz * ny * nx;
+    int64_t cap = capacity > 0 ? capacity : 0;
+    double *d = (double *)malloc((size_t)nv * sizeof(double));
+    double *b = (double *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(double));
+    double *e = (double *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(double));
+    if (!d || !b || !e) { free(d); free(b); free(e); return CRO_ERR_NOMEM; }
+    for (int64_t i = 0; i < nv; i++) d[i] = (double)img[i];
+    int rc = persistence_core(d, ndim, shape, twist, capacity, out_dim, b, e, out_birth_L, out_death_L, n_out);
+    if (rc == CRO_OK || rc == CRO_ERR_CAPACITY) {
+        int64_t k = *n_out < cap ? *n_out : cap;
+        for (int64_t i = 0; i < k; i++) {
+            out_birth[i] = (float)b[i];
+            out_death[i] = (float)e[i];
+        }
+    }
+    free(d); free(b); free(e);
     return rc;
 }

@@ -45,6 +45,8 @@ _LIB = os.path.join(_HERE, "libcr_oracle.so")
 
 PAIR_DTYPE = np.dtype([("dim", np.int32), ("birth", np.float32), ("death", np.float32),
                        ("birth_L", np.int64), ("death_L", np.int64)])
+PAIR64_DTYPE = np.dtype([("dim", np.int32), ("birth", np.float64), ("death", np.float64),
+                         ("birth_L", np.int64), ("death_L", np.int64)])
 
 
 def build(force: bool = False) -> str:
@@ -66,6 +68,8 @@ def _lib():
         ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int64,
         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
         ctypes.POINTER(ctypes.c_int64)]
+    lib.cro_persistence_f64.restype = ctypes.c_int
+    lib.cro_persistence_f64.argtypes = lib.cro_persistence.argtypes
     return lib
 
 
@@ -118,6 +122,38 @@ def persistence(img: np.ndarray, maxdim: int | None = None, twist: bool = True) 
     return out
 
 
+def persistence_f64(img: np.ndarray, maxdim: int | None = None, twist: bool = True) -> np.ndarray:
+    """``persistence`` for a float64 image, computed in double (the precision
+    of the paper's timing study, whose datasets were converted to double,
+    Sec. 3); births and deaths are float64."""
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    if img.ndim < 1 or img.ndim > 3:
+        raise ValueError("ndim must be 1, 2 or 3")
+    shape = (ctypes.c_int64 * img.ndim)(*img.shape)
+    cap = max(1, num_cells(img.shape))
+    out = np.zeros(cap, dtype=PAIR64_DTYPE)
+    dim = np.zeros(cap, np.int32)
+    birth = np.zeros(cap, np.float64)
+    death = np.zeros(cap, np.float64)
+    bl = np.zeros(cap, np.int64)
+    dl = np.zeros(cap, np.int64)
+    n = ctypes.c_int64(0)
+    rc = _lib().cro_persistence_f64(img.ctypes.data, img.ndim, shape, int(bool(twist)), cap,
+                                    dim.ctypes.data, birth.ctypes.data, death.ctypes.data,
+                                    bl.ctypes.data, dl.ctypes.data, ctypes.byref(n))
+    if rc == -2:
+        raise ValueError("NaN in input")
+    if rc != 0:
+        raise RuntimeError("oracle failed with code %d" % rc)
+    k = n.value
+    out = out[:k]
+    out["dim"], out["birth"], out["death"] = dim[:k], birth[:k], death[:k]
+    out["birth_L"], out["death_L"] = bl[:k], dl[:k]
+    if maxdim is not None:
+        out = out[out["dim"] <= maxdim]
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Python cell enumeration (independent of the C code above)
 # ---------------------------------------------------------------------------
@@ -148,8 +184,8 @@ def cell_vertices(dim: int, L: int, shape):
     return out
 
 
-def _canon_values(img):
-    f = np.ascontiguousarray(img, dtype=np.float32).reshape(-1).copy()
+def _canon_values(img, dtype=np.float32):
+    f = np.ascontiguousarray(img, dtype=dtype).reshape(-1).copy()
     f[f == 0] = 0.0  # -0.0 -> +0.0
     return f
 
@@ -181,11 +217,11 @@ def gradient(img, pairs, grad_birth, grad_death) -> np.ndarray:
     return g.reshape(img.shape)
 
 
-def filtration(img):
+def filtration(img, dtype=np.float32):
     """All cubes as (value, dim, L, facets) sorted by (value, dim, -L); facets
-    are the (dim-1, L) of the 2*dim facets."""
+    are the (dim-1, L) of the 2*dim facets.  Values are taken in ``dtype``."""
     nz, ny, nx = _canon(img.shape)
-    f = _canon_values(img)
+    f = _canon_values(img, dtype)
     cells = []
     ext = (nx, ny, nz)
     for (dim, m), span in _SPAN.items():
@@ -224,13 +260,13 @@ def _xor_rank_insert(basis: dict, v: int) -> bool:
     return False
 
 
-def brute_force_pairs(img):
+def brute_force_pairs(img, dtype=np.float32):
     """Cell pairs from the rank function of the cell-by-cell filtration.
 
     Returns a set of (dim, birth_L, death_L) with death_L = -1 for essential
     classes, zero-length pairs included.  Cost grows like n^3 in the number of
-    cubes n: inputs of at most ~120 cubes."""
-    cells = filtration(img)
+    cubes n: inputs of at most ~120 cubes.  Values are taken in ``dtype``."""
+    cells = filtration(img, dtype)
     n = len(cells)
     posmap = {(c[1], c[2]): i for i, c in enumerate(cells)}
     bnd = []
@@ -292,11 +328,12 @@ def brute_force_pairs(img):
     return result
 
 
-def brute_force_rank_diagram(img):
+def brute_force_rank_diagram(img, dtype=np.float32):
     """Diagram values (dim, birth, death) with multiplicity, from ranks of the
     maps between sublevel complexes at the distinct values; zero-length bars
-    do not appear.  Returns a sorted list of (dim, birth, death)."""
-    cells = filtration(img)
+    do not appear.  Returns a sorted list of (dim, birth, death).  Values are
+    taken in ``dtype``."""
+    cells = filtration(img, dtype)
     vals = sorted(set(c[0] for c in cells))
     T = len(vals)
     n = len(cells)

@@ -8,6 +8,7 @@ raises.
 
 Public API (names as in the C ABI):
   cr_persistence(img, maxdim, keep_zero, topdim_only) -> Pairs
+  cr_persistence_f64(img, maxdim, ...)               -> Pairs64 (float64 images)
   cr_persistence_batched(images, maxdim, ...)        -> BatchedPairs
   cr_backward(img, pairs, grad_birth, grad_death)    -> grad image
   cr_backward_batched(...)
@@ -46,6 +47,7 @@ CR_TUNE_UF_COMPACT = 2
 CR_PAIR_ESSENTIAL = 1
 
 PAIR_BYTES = 32
+PAIR64_BYTES = 40
 
 
 class CRError(RuntimeError):
@@ -107,6 +109,12 @@ def lib() -> ctypes.CDLL:
         L.cr_last_error_detail.argtypes = []
         L.cr_error_string.restype = ctypes.c_char_p
         L.cr_error_string.argtypes = [ctypes.c_int]
+        L.cr_workspace_size_f64.argtypes = [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_uint32, ctypes.c_int64,
+                                            ctypes.c_int, szp]
+        L.cr_workspace_size_f64.restype = ctypes.c_int
+        L.cr_persistence_f64.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, vp, ctypes.c_int64, i64p, vp,
+                                         ctypes.c_size_t, vp, ctypes.c_uint32]
+        L.cr_persistence_f64.restype = ctypes.c_int
         L.cr_tune_set.argtypes = [ctypes.c_int, ctypes.c_int]
         L.cr_tune_set.restype = ctypes.c_int
         L.cr_tune_get.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
@@ -196,6 +204,53 @@ class Pairs:
     def numpy(self):
         import numpy as np
         dt = np.dtype([("dim", np.int32), ("birth", np.float32), ("death", np.float32), ("flags", np.uint32),
+                       ("birth_cell", np.int64), ("death_cell", np.int64)])
+        b = self.raw.detach().cpu().numpy().tobytes()
+        return np.frombuffer(b, dtype=dt).copy()
+
+
+@dataclass
+class Pairs64:
+    """Pairs of a float64 image (cr_pair64), in the same canonical order as
+    ``Pairs``.  ``raw`` is the (n, 40) byte view."""
+    raw: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.raw.shape[0])
+
+    def _f(self, dtype, lo, hi):
+        if not self.n:
+            return torch.empty(0, dtype=dtype, device=self.raw.device)
+        return self.raw[:, lo:hi].contiguous().view(dtype).reshape(-1)
+
+    @property
+    def dim(self):
+        return self._f(torch.int32, 0, 4)
+
+    @property
+    def flags(self):
+        return self._f(torch.int32, 4, 8)
+
+    @property
+    def birth(self):
+        return self._f(torch.float64, 8, 16)
+
+    @property
+    def death(self):
+        return self._f(torch.float64, 16, 24)
+
+    @property
+    def birth_cell(self):
+        return self._f(torch.int64, 24, 32)
+
+    @property
+    def death_cell(self):
+        return self._f(torch.int64, 32, 40)
+
+    def numpy(self):
+        import numpy as np
+        dt = np.dtype([("dim", np.int32), ("flags", np.uint32), ("birth", np.float64), ("death", np.float64),
                        ("birth_cell", np.int64), ("death_cell", np.int64)])
         b = self.raw.detach().cpu().numpy().tobytes()
         return np.frombuffer(b, dtype=dt).copy()
@@ -292,6 +347,51 @@ def cr_persistence(img: torch.Tensor, maxdim: Optional[int] = None, keep_zero: b
             continue
         _check(rc)
         return Pairs(out[: n.value])
+    _check(rc)
+    raise AssertionError("unreachable")
+
+
+def cr_persistence_f64(img: torch.Tensor, maxdim: Optional[int] = None, keep_zero: bool = False,
+                       topdim_only: bool = False, capacity: Optional[int] = None) -> Pairs64:
+    """Persistence pairs of one 1D/2D/3D float64 CUDA image, with float64
+    births and deaths (the library ranks the values on the device and runs
+    the float32 path on the ranks; include/cr.h, cr_persistence_f64)."""
+    if not isinstance(img, torch.Tensor) or not img.is_cuda:
+        raise ValueError("img must be a CUDA tensor (the library has no CPU path)")
+    if img.dtype != torch.float64:
+        raise ValueError("img must be float64")
+    img = img.contiguous()
+    nd = img.dim()
+    if nd < 1 or nd > 3:
+        raise ValueError("img must be 1D, 2D or 3D")
+    if maxdim is None:
+        maxdim = nd - 1
+    flags = _flags(keep_zero, topdim_only)
+    shape = (ctypes.c_int64 * nd)(*img.shape)
+    L = lib()
+    if capacity is None:
+        capacity = _num_cells(img.shape) // 2 + 2 if keep_zero else max(4096, img.numel() // 4 + 16)
+    n = ctypes.c_int64(0)
+    worst, scale = False, 1
+    for _attempt in range(6):
+        sz = ctypes.c_size_t()
+        _check(L.cr_workspace_size_f64(nd, shape, int(maxdim), flags, int(capacity), 0 if worst else 1,
+                                       ctypes.byref(sz)))
+        out = torch.empty((int(capacity), PAIR64_BYTES), dtype=torch.uint8, device=img.device)
+        ws = _WS.get(sz.value * scale, img.device)
+        rc = L.cr_persistence_f64(ctypes.c_void_p(img.data_ptr()), nd, shape, int(maxdim),
+                                  ctypes.c_void_p(out.data_ptr()), int(capacity), ctypes.byref(n),
+                                  ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(img.device), flags)
+        if rc == CR_ERR_CAPACITY:
+            capacity = int(n.value) + 16
+            continue
+        if rc == CR_ERR_WORKSPACE:
+            if worst:
+                scale *= 2
+            worst = True
+            continue
+        _check(rc)
+        return Pairs64(out[: n.value])
     _check(rc)
     raise AssertionError("unreachable")
 
@@ -482,6 +582,6 @@ class PersistentHomology(torch.autograd.Function):
 __all__ = [
     "build", "lib", "cr_persistence", "cr_persistence_batched", "cr_backward", "cr_backward_batched",
     "PersistentHomology", "Pairs", "BatchedPairs", "CRError", "cell_location", "error_string",
-    "CR_KEEP_ZERO", "CR_TOPDIM_ONLY", "cr_tune_set", "cr_tune_get",
+    "CR_KEEP_ZERO", "CR_TOPDIM_ONLY", "cr_tune_set", "cr_tune_get", "cr_persistence_f64", "Pairs64",
     "CR_TUNE_UF_ITEMS", "CR_TUNE_RED_WARPS", "CR_TUNE_UF_COMPACT",
 ]

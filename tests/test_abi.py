@@ -105,3 +105,35 @@ def test_image_entry_points_check_arguments_on_the_host(cr):
     assert h(p, 1, 2, sh, 0, 2, 1.0, 1.0, 2, 1.0, p, None) == cr.CR_ERR_INVALID_ARG          # empty birth range
     assert h(p, 1, 2, sh, 0, 2, 0.0, 1.0, 2, 0.0, p, None) == cr.CR_ERR_INVALID_ARG          # lifetime range
     assert h(p, 1, 2, sh, 0, 2, 0.0, 1.0, 0, 1.0, p, None) == cr.CR_ERR_INVALID_ARG          # nl
+
+
+def test_f64_entry_points_check_arguments_on_the_host(cr):
+    import torch
+    lib = cr.lib()
+    sz = ctypes.c_size_t()
+    for shape, cap in [((1,), 1), ((64, 64), 5000), ((16, 16, 16), 10000)]:
+        sh = (ctypes.c_int64 * len(shape))(*shape)
+        assert lib.cr_workspace_size_f64(len(shape), sh, len(shape) - 1, 0, cap, 1, ctypes.byref(sz)) == 0
+        typ = sz.value
+        assert lib.cr_workspace_size_f64(len(shape), sh, len(shape) - 1, 0, cap, 0, ctypes.byref(sz)) == 0
+        worst = sz.value
+        f32 = ctypes.c_size_t()
+        assert lib.cr_workspace_size(len(shape), sh, len(shape) - 1, 0, ctypes.byref(f32)) == 0
+        # the float64 extras: rank image, value table, two key and two index buffers, run starts, 32 B per pair
+        nv = int(np.prod(shape))
+        assert worst - f32.value >= nv * (4 + 8 + 16 + 8 + 4) + 32 * cap
+        assert 0 < typ <= worst
+    sh = (ctypes.c_int64 * 2)(0, 4)
+    assert lib.cr_workspace_size_f64(2, sh, 1, 0, 10, 1, ctypes.byref(sz)) == cr.CR_ERR_INVALID_ARG
+    sh = (ctypes.c_int64 * 2)(4, 4)
+    assert lib.cr_workspace_size_f64(2, sh, 1, 0, -1, 1, ctypes.byref(sz)) == cr.CR_ERR_INVALID_ARG
+    sh = (ctypes.c_int64 * 3)(2048, 2048, 1024)
+    assert lib.cr_workspace_size_f64(3, sh, 2, 0, 10, 1, ctypes.byref(sz)) == cr.CR_ERR_TOO_LARGE
+    n = ctypes.c_int64(0)
+    sh = (ctypes.c_int64 * 2)(4, 4)
+    assert lib.cr_persistence_f64(None, 2, sh, 1, None, 0, ctypes.byref(n), None, 0, None, 0) == \
+        cr.CR_ERR_INVALID_ARG
+    assert lib.cr_persistence_f64(ctypes.c_void_p(16), 4, sh, 1, ctypes.c_void_p(16), 4, ctypes.byref(n),
+                                  ctypes.c_void_p(256), 1 << 20, None, 0) == cr.CR_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        cr.cr_persistence_f64(torch.zeros(4, 4, dtype=torch.float64))

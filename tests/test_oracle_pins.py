@@ -259,3 +259,48 @@ def test_localised_images_invariants(oracle_mod):
                 nz, ny, nx = oracle_mod.oracle._canon(shape)
                 cnt[(z * ny + y) * nx + x] += 1
             assert np.array_equal(per_voxel, cnt)
+
+
+def _near_tied_f64(rng, shape):
+    """float64 images whose values differ below float32 resolution: small
+    integer levels plus multiples of 2^-40, so that casting to float32 ties
+    values the float64 filtration orders."""
+    base = rng.integers(0, 3, shape).astype(np.float64)
+    return base + rng.integers(0, 4, shape) * 2.0 ** -40
+
+
+@pytest.mark.parametrize("kind", ["1d", "2d", "3d"])
+def test_f64_cell_pairs_equal_rank_function(oracle_mod, kind):
+    # the float64 oracle against the rank function of the float64 cell-by-cell filtration
+    rng = np.random.default_rng({"1d": 21, "2d": 22, "3d": 23}[kind])
+    shapes = {"1d": [(3,), (6,), (9,)], "2d": [(2, 3), (3, 3), (3, 4)], "3d": [(2, 2, 2), (2, 2, 3)]}[kind]
+    differs = 0
+    for _ in range({"1d": 25, "2d": 25, "3d": 8}[kind]):
+        img = _near_tied_f64(rng, shapes[rng.integers(len(shapes))])
+        p = oracle_mod.persistence_f64(img)
+        assert p["birth"].dtype == np.float64
+        assert cellset(p) == oracle_mod.brute_force_pairs(img, np.float64), img.tolist()
+        differs += cellset(p) != cellset(oracle_mod.persistence(img))  # the float32 cast ties values
+    assert differs > 0
+
+
+def test_f64_diagram_equals_rank_diagram(oracle_mod):
+    rng = np.random.default_rng(24)
+    for _ in range(40):
+        img = _near_tied_f64(rng, (3, 3))
+        got = nonzero(oracle_mod.persistence_f64(img))
+        assert got == oracle_mod.brute_force_rank_diagram(img, np.float64)
+        # values are the image's own float64 values, not float32 roundings
+        assert all(b in set(img.ravel().tolist()) for _, b, _ in got)
+
+
+def test_f64_promotes_float32_inputs_exactly(oracle_mod):
+    from paper_2005_12692_gb300 import synth
+    for img in [synth.grf((17, 23), 2.0, 25), synth.quantised(synth.grf((5, 6, 7), 2.0, 26), 4)]:
+        a = oracle_mod.persistence(img)
+        b = oracle_mod.persistence_f64(img.astype(np.float64))
+        assert cellset(a) == cellset(b)
+        assert np.array_equal(a["birth"].astype(np.float64), b["birth"])
+        assert np.array_equal(a["death"].astype(np.float64), b["death"])
+    with pytest.raises(ValueError):
+        oracle_mod.persistence_f64(np.array([0.0, np.nan]))
