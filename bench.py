@@ -540,6 +540,31 @@ def main():
         images = {"pairs": pr.n, **res,
                   "note": "output zero-fill + one scatter per pair; inputs in HBM; not part of the timed step"}
 
+    # the float64 input path on the same field (Sec. 3's precision), timed alone after everything else
+    f64 = None
+    if W["kind"] == "single" and not args.no_e2e:
+        try:
+            img64 = torch.from_numpy(data.astype(np.float64)).to(dev)
+            reps = max(3, min(args.steps, 20)) if len(data.shape) < 3 else 2
+            for _ in range(3):
+                cr.cr_persistence_f64(img64, maxdim=W["maxdim"])
+            f64_ms = []
+            for _ in range(reps):
+                flush.fill_(1)
+                torch.cuda.synchronize(dev)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                cr.cr_persistence_f64(img64, maxdim=W["maxdim"])
+                b.record(stream)
+                b.synchronize()
+                f64_ms.append(a.elapsed_time(b))
+            ms64 = statistics.mean(f64_ms)
+            f64 = {"value": units / (ms64 / 1e3), "unit": metric.split()[0], "ms_per_call": ms64, "calls": reps,
+                   "note": "cr_persistence_f64 on the same field cast to float64, device-resident, L2 flushed"}
+        except Exception as e:  # reported, never fatal to the headline numbers
+            f64 = {"error": str(e)[:200]}
+
     peaks = load_peaks()
     roof = roofline_from({roof_stage: timed_stages[roof_stage]} if roof_stage in timed_stages else stages, peaks)
 
@@ -554,6 +579,7 @@ def main():
             "tuning": tuning,
             "plain_path": plain,
             "localised_images": images,
+            "f64_path": f64,
             "stages": {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps}
                        for k, v in stages.items()},
             "stages_note": "separate profiled pass of %d steps (events around every stage)" % prof_steps}
