@@ -221,6 +221,22 @@ def roofline_from(stages, peaks, sustained=True):
             "limiter": LIMITER.get(best, "hbm")}
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over all ranks: a replicated job's time is its slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processes units_per_rank per step (weak scaling)."""
+    return units_per_rank * world / (ms_per_step / 1e3)
+
+
 def tune_candidates(W, data):
     """Knob values the autotuner tries for a workload (knobs that cannot change its launches are left out:
     a batch or a volume always fills every SM with union-find blocks; only volumes run the reduction)."""
@@ -437,14 +453,9 @@ def main():
     L.cr_profile_select(0xFFFFFFFF)
     launches = int(L.cr_launch_count()) - launches0
     timed_stages = read_profile(cr)
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    value = units * world / (ms_per_step / 1e3)
+    value = job_value(units, world, ms_per_step)
 
     # -------- end to end through host buffers --------
     e2e_ms = []
@@ -483,7 +494,7 @@ def main():
             if i >= args.warmup:
                 e2e_ms.append((time.perf_counter() - t0) * 1e3)
             d2h = gh.numel() * 4
-    e2e_value = units * world / (statistics.mean(e2e_ms) / 1e3) if e2e_ms else None
+    e2e_value = job_value(units, world, max_over_ranks(statistics.mean(e2e_ms), world, dev)) if e2e_ms else None
 
     # the plain per-image path on the same GPU (a subset, scaled to images/s)
     plain = None
