@@ -304,3 +304,86 @@ def test_f64_promotes_float32_inputs_exactly(oracle_mod):
         assert np.array_equal(a["death"].astype(np.float64), b["death"])
     with pytest.raises(ValueError):
         oracle_mod.persistence_f64(np.array([0.0, np.nan]))
+
+
+def _uf_find(par, x):
+    while par[x] != x:
+        par[x] = par[par[x]]
+        x = par[x]
+    return x
+
+
+def _h0_by_union_find(cells):
+    """H0 cell pairs by the elder rule (Sec. 2, union-find on vertices): edges in
+    filtration order; a merge kills the component whose oldest vertex entered
+    later."""
+    pos = {(c[1], c[2]): i for i, c in enumerate(cells)}
+    par = {}
+    pairs = set()
+    for i, (val, dim, L, facets) in enumerate(cells):
+        if dim == 0:
+            par[L] = L
+        elif dim == 1:
+            a, b = (_uf_find(par, fL) for _, fL in facets)
+            if a == b:
+                continue
+            young, old = (a, b) if pos[(0, a)] > pos[(0, b)] else (b, a)
+            par[young] = old  # the root is the oldest vertex of its component
+            pairs.add((0, young, L))
+    roots = {_uf_find(par, v) for v in list(par)}
+    assert len(roots) == 1
+    pairs.add((0, roots.pop(), -1))
+    return pairs
+
+
+def _top_by_dual_union_find(cells, shape):
+    """Top-dimensional cell pairs by duality (Rem. 2.1): the top cubes plus one
+    outer node are the vertices of the dual graph, the (top-1)-cubes its edges
+    (a boundary cube joins its one top cube to the outer node).  Edges are taken
+    in reverse filtration order; a merge kills the component whose oldest
+    member in that order (its latest top cube in the filtration) comes later in
+    it, and pairs the edge with that cube."""
+    D = len(shape)  # dimension of the top cubes (every extent > 1)
+    pos = {(c[1], c[2]): i for i, c in enumerate(cells)}
+    cof = {}
+    for val, dim, L, facets in cells:
+        if dim == D:
+            for f in facets:
+                cof.setdefault(f, []).append(L)
+    OUT = -1
+    par = {OUT: OUT}
+    age = {OUT: float("inf")}  # the outer node is older than everything
+    pairs = set()
+    for val, dim, L, facets in reversed(cells):
+        if dim == D:
+            par[L] = L
+            age[L] = pos[(D, L)]
+        elif dim == D - 1:
+            ends = cof.get((dim, L), [])
+            assert 1 <= len(ends) <= 2
+            ends = ends + [OUT] * (2 - len(ends))
+            a, b = (_uf_find(par, e) for e in ends)
+            if a == b:
+                continue
+            young, old = (a, b) if age[a] < age[b] else (b, a)
+            par[young] = old
+            pairs.add((D - 1, L, young))
+    return pairs
+
+
+@pytest.mark.parametrize("kind", ["2d", "3d"])
+def test_h0_and_top_dimension_by_union_find_and_duality(oracle_mod, kind):
+    # the reduction's pairs in dimension 0 equal the elder-rule union-find, and in
+    # the top dimension the union-find on the dual graph in reverse order
+    rng = np.random.default_rng({"2d": 41, "3d": 42}[kind])
+    shapes = {"2d": [(2, 2), (3, 5), (6, 4), (9, 11), (14, 13)],
+              "3d": [(2, 2, 2), (2, 3, 4), (4, 4, 3), (5, 6, 5)]}[kind]
+    for _ in range({"2d": 40, "3d": 20}[kind]):
+        sh = shapes[rng.integers(len(shapes))]
+        img = (rng.integers(0, 4, sh) if rng.random() < 0.7 else rng.random(sh)).astype(np.float32)
+        cells = oracle_mod.filtration(img)
+        p = oracle_mod.persistence(img)
+        got = cellset(p)
+        assert {c for c in got if c[0] == 0} == _h0_by_union_find(cells), img.tolist()
+        top = len(sh) - 1
+        assert {c for c in got if c[0] == top} == _top_by_dual_union_find(cells, sh), img.tolist()
