@@ -33,6 +33,7 @@ def test_f64_matches_oracle(cr, oracle_mod):
     from paper_2005_12692_gb300 import synth
     rng = np.random.default_rng(31)
     imgs = [fine_structure(rng, (37, 41)), fine_structure(rng, (9, 10, 11)), fine_structure(rng, (300,)),
+            fine_structure(rng, (300, 310)),  # the rank sort and scan over many blocks
             synth.grf((65, 70), 3.0, 32).astype(np.float64) * (1 + 1e-12) + rng.random((65, 70)) * 1e-11,
             synth.quantised(synth.grf((12, 13, 14), 2.0, 33), 5).astype(np.float64) + 2.0 ** -45]
     for img in imgs:
