@@ -387,3 +387,20 @@ def test_h0_and_top_dimension_by_union_find_and_duality(oracle_mod, kind):
         assert {c for c in got if c[0] == 0} == _h0_by_union_find(cells), img.tolist()
         top = len(sh) - 1
         assert {c for c in got if c[0] == top} == _top_by_dual_union_find(cells, sh), img.tolist()
+
+
+def test_tie_order_by_hand(oracle_mod):
+    # Sec. 2 orders cells by (-value, type, z, y, x) in cohomology; the filtration is
+    # its reverse, so among equal values larger L enters first, vertices before edges.
+    # [0, 0, 0]: vertices enter as v2, v1, v0; then edges e1 = (v1, v2), e0 = (v0, v1).
+    # e1 joins {v2} and {v1}: v1 entered later and dies, pair (v1, e1); e0 joins
+    # {v2, v1} and {v0}: v0 dies, pair (v0, e0); v2 is essential.
+    p = oracle_mod.persistence(np.zeros(3, np.float32))
+    assert cellset(p) == {(0, 1, 1), (0, 0, 0), (0, 2, -1)}
+    # 2x2 all equal: vertices L 3, 2, 1, 0; x-edges (type 0) L 2, 0 and y-edges (type 1)
+    # L 4 + 1, 4 + 0 (L = (m*Ny + y)*Nx + x); edges enter by descending L: y-edge at x=1
+    # (L 5, joins v1 and v3), y-edge at x=0 (L 4, joins v0 and v2), x-edge at y=1
+    # (L 2, joins v2 and v3), x-edge at y=0 (L 0, joins v0 and v1, closing the loop);
+    # the square (L 0) kills that loop.
+    p = oracle_mod.persistence(np.zeros((2, 2), np.float32))
+    assert cellset(p) == {(0, 1, 5), (0, 0, 4), (0, 2, 2), (0, 3, -1), (1, 0, 0)}
