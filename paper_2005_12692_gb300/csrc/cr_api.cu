@@ -39,6 +39,7 @@ struct HostPlan {
     int64_t max_face_per_image = 0;
     bool any_h0 = false, any_dual = false, any_mid = false;
     bool serial_uf = false;  // run the two union-finds one after the other (half the region)
+    bool graphs = true;      // single 1D/2D images may replay their launches as a CUDA graph
     int nseg_bits = 0;
 };
 
@@ -605,7 +606,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     }
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
     };
-    if (n == 1 && !P.any_mid) {
+    if (n == 1 && !P.any_mid && P.graphs) {
         const Seg &S0 = P.segs[0];
         GraphKey key{imgs, P.vtot, S0.nx, S0.ny, S0.nz, maxdim, flags, pairs_out, capacity, ws, ws_bytes, st,
                      current_device(), prof_active(), prof_mask(), P.serial_uf, tune_epoch()};
@@ -842,6 +843,9 @@ int persistence_serial(const float *img, int ndim, const int64_t *shape, int max
     int rc = plan_single(ndim, shape, maxdim, flags, P);
     if (rc) return rc;
     P.serial_uf = true;
+    // no graph capture here: instantiating a graph (and creating the capture
+    // stream) may allocate, which the no-alloc entry point must not do
+    P.graphs = false;
     return pipeline(img, P, maxdim, flags, pairs_out, capacity, nullptr, n_pairs, ws, ws_bytes, stream);
 }
 }  // namespace cr

@@ -404,3 +404,58 @@ def test_tie_order_by_hand(oracle_mod):
     # the square (L 0) kills that loop.
     p = oracle_mod.persistence(np.zeros((2, 2), np.float32))
     assert cellset(p) == {(0, 1, 5), (0, 0, 4), (0, 2, 2), (0, 3, -1), (1, 0, 0)}
+
+
+def test_argmax_vertex_on_ties_by_hand(oracle_mod):
+    # A cube's value is the value of its vertex that enters the filtration last
+    # (V-construction, Sec. 2).  Among equal values larger L enters first (the
+    # reverse of the (-value, m, z, y, x) order), so among tied vertices the one
+    # with the smallest linear index enters last and carries the value.
+    av = oracle_mod.argmax_vertex
+    one = np.array([1.0, 1.0], np.float32)
+    assert av(one, 1, 0) == 0  # edge {0, 1}: vertex 1 enters before vertex 0
+    assert av(one, 0, 1) == 1  # a vertex is its own argmax
+    # 2x2 image (index y*2 + x): [[1, 1], [0, 1]]
+    img = np.array([[1.0, 1.0], [0.0, 1.0]], np.float32)
+    assert av(img, 2, 0) == 0  # square: vertices 0, 1, 3 tie at 1, vertex 0 is last
+    assert av(img, 1, 0) == 0  # x-edge at y=0 (L 0): vertices 0, 1 tie
+    assert av(img, 1, 2) == 3  # x-edge at y=1 (L 2): vertex 3 (value 1) over vertex 2 (value 0)
+    assert av(img, 1, 5) == 1  # y-edge at x=1 (L (1*2+0)*2+1): vertices 1, 3 tie
+    assert av(img, 1, 4) == 0  # y-edge at x=0 (L 4): vertex 0 (value 1) over vertex 2 (value 0)
+    # 2x2x2 cube of equal values: the cube's value is carried by vertex 0
+    assert av(np.ones((2, 2, 2), np.float32), 3, 0) == 0
+    # -0.0 and +0.0 are one value, so they tie as well
+    assert av(np.array([0.0, -0.0], np.float32), 1, 0) == 0
+
+
+def test_gradient_on_ties_by_hand(oracle_mod):
+    # [1, 1]: vertices enter as v1, v0 (both value 1), then edge e0 joins them;
+    # v0 entered later and dies: pair (v0, e0) of length 0; v1 is essential.
+    img = np.array([1.0, 1.0], np.float32)
+    p = oracle_mod.persistence(img)
+    assert cellset(p) == {(0, 0, 0), (0, 1, -1)}
+    rows = {(int(d), int(b), int(e)): k for k, (d, b, e) in enumerate(zip(p["dim"], p["birth_L"], p["death_L"]))}
+    gb = np.zeros(len(p), np.float32)
+    gd = np.zeros(len(p), np.float32)
+    gb[rows[(0, 0, 0)]], gd[rows[(0, 0, 0)]] = 3.0, 5.0
+    gb[rows[(0, 1, -1)]], gd[rows[(0, 1, -1)]] = 7.0, 11.0  # an essential death contributes nothing
+    # dL/dbirth of (v0, e0) goes to v0; dL/ddeath to the edge's last vertex, v0 again
+    assert oracle_mod.gradient(img, p, gb, gd).tolist() == [8.0, 7.0]
+    # 2x2 all equal: pairs (v1, e5), (v0, e4), (v2, e2), v3 essential and (e0, square 0)
+    # (hand-derived in test_tie_order_by_hand).  Every edge and the square is carried
+    # by its smallest vertex: e5 = {1, 3} -> 1, e4 = {0, 2} -> 0, e2 = {2, 3} -> 2,
+    # e0 = {0, 1} -> 0, the square -> 0.
+    img = np.zeros((2, 2), np.float32)
+    p = oracle_mod.persistence(img)
+    gb = np.zeros(len(p), np.float32)
+    gd = np.zeros(len(p), np.float32)
+    want = np.zeros(4)
+    births = {(0, 1): 1, (0, 0): 0, (0, 2): 2, (0, 3): 3, (1, 0): 0}
+    deaths = {(0, 5): 1, (0, 4): 0, (0, 2): 2, (1, 0): 0}
+    for k in range(len(p)):
+        d, bl, dl = int(p["dim"][k]), int(p["birth_L"][k]), int(p["death_L"][k])
+        gb[k], gd[k] = 2.0 ** k, 2.0 ** (k + 8)
+        want[births[(d, bl)]] += gb[k]
+        if dl >= 0:
+            want[deaths[(d, dl)]] += gd[k]
+    assert oracle_mod.gradient(img, p, gb, gd).reshape(-1).tolist() == want.tolist()
