@@ -55,6 +55,14 @@ typedef struct CUstream_st *cr_stream_t; /* same object as cudaStream_t */
 /* ---- flags ---- */
 #define CR_KEEP_ZERO 1u   /* also emit pairs with death == birth */
 #define CR_TOPDIM_ONLY 2u /* only the (ndim-1)-dimensional pairs, by duality (Sec. 2, Rem. 2.1) */
+/* Report the death cell as each pair's location instead of the birth cell
+ * (the location option of Sec. 4, Ex. 4.1 / Ex. 4.6; the paper notes the
+ * representative is one choice among several).  Pairs keep both cells; the
+ * flag sets CR_PAIR_LOC_DEATH in every pair's flags, and the location-based
+ * calls (cr_pair_table, the localised images) called with
+ * location = CR_LOC_FROM_PAIRS follow it.  An essential pair has no death
+ * cell: its location stays its birth cell. */
+#define CR_LOC_DEATH 4u
 
 /* A persistence pair [birth, death) of dimension `dim` (Sec. 1: a d-cycle
  * born at `birth`, killed at `death`).  birth_cell is the L index of the
@@ -72,6 +80,13 @@ typedef struct {
 } cr_pair;
 
 #define CR_PAIR_ESSENTIAL 1u
+#define CR_PAIR_LOC_DEATH 2u /* set by the CR_LOC_DEATH flag: the pair is located at its death cell */
+
+/* `location` argument of the location-based calls: the birth cell (0), the
+ * death cell (1), or what each pair records (CR_PAIR_LOC_DEATH). */
+#define CR_LOC_BIRTH_CELL 0
+#define CR_LOC_DEATH_CELL 1
+#define CR_LOC_FROM_PAIRS (-1)
 
 /* Device workspace (bytes) for cr_persistence on one image of this shape,
  * maxdim and flags.  Host-only; no GPU work.
@@ -96,7 +111,7 @@ int cr_workspace_size_typical(int ndim, const int64_t *shape, int maxdim, uint32
  *   pairs_out device cr_pair[capacity]; on success sorted by
  *             (dim, birth, birth_cell).
  *   n_pairs   host; number of pairs written (or needed, on CR_ERR_CAPACITY).
- *   flags     CR_KEEP_ZERO | CR_TOPDIM_ONLY.
+ *   flags     CR_KEEP_ZERO | CR_TOPDIM_ONLY | CR_LOC_DEATH.
  */
 int cr_persistence(const float *img, int ndim, const int64_t *shape, int maxdim, cr_pair *pairs_out,
                    int64_t capacity, int64_t *n_pairs, void *ws, size_t ws_bytes, cr_stream_t stream,
@@ -194,8 +209,10 @@ int cr_backward_batched(const float *imgs, const int64_t *img_offsets, const int
 
 /* Localised-feature images (Sec. 4, the example on localised features).
  * The location of a pair is the anchor voxel (x, y, z) of its birth cell
- * (location = 0) or of its death cell (location = 1), i.e. the cell's L-index
- * with the type dropped.  Essential pairs (infinite death) are left out.
+ * (location = CR_LOC_BIRTH_CELL), of its death cell (CR_LOC_DEATH_CELL), or
+ * of the cell the pair records (CR_LOC_FROM_PAIRS: the death cell where
+ * CR_PAIR_LOC_DEATH is set), i.e. the cell's L-index with the type dropped.
+ * Essential pairs (infinite death) are left out.
  *
  * cr_lifetime_image: out[d * V + v], d < ndim, V = prod(shape), is the
  *   largest lifetime death - birth (float32 subtraction) of the pairs of
@@ -220,6 +237,21 @@ int cr_lifetime_image(const cr_pair *pairs, int64_t n_pairs, int ndim, const int
 int cr_persistent_histogram_image(const cr_pair *pairs, int64_t n_pairs, int ndim, const int64_t *shape,
                                   int location, int nb, double b_lo, double b_hi, int nl, double l_hi, float *out,
                                   cr_stream_t stream);
+
+/* The pairs as the paper's table (Sec. 4, Ex. 4.1: computePH returns one
+ * row (dim, birth, death, x, y, z) per pair, located at the birth cell or,
+ * with the location option, the death cell).
+ *   pairs     device cr_pair[n_pairs] of one image
+ *   shape     host int64[ndim], the image's shape; (x, y, z) is the anchor of
+ *             the located cube as cr_cell_location gives it (x the fastest
+ *             array index; y = 0 in 1D, z = 0 in 1D/2D)
+ *   location  CR_LOC_BIRTH_CELL, CR_LOC_DEATH_CELL or CR_LOC_FROM_PAIRS; an
+ *             essential pair is always located at its birth cell
+ *   out       device double[n_pairs * 6], row-major; essential deaths +inf
+ * Asynchronous on `stream`.  Errors: CR_ERR_INVALID_ARG (ndim not 1-3, an
+ * extent < 1, a bad location, a null buffer that is needed), CR_ERR_CUDA. */
+int cr_pair_table(const cr_pair *pairs, int64_t n_pairs, int ndim, const int64_t *shape, int location,
+                  double *out, cr_stream_t stream);
 
 /* Anchor (x, y, z) and type m of the cube (dim, L) of an image of this shape
  * (the paper's cell tuple (x, y, z, m, d), Sec. 2).  Host-only. */

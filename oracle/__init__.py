@@ -17,6 +17,7 @@ from .oracle import (  # noqa: F401
     brute_force_rank_diagram,
     h0_1d_brute_force,
     euler_characteristic,
+    pair_table,
     lifetime_image,
     persistent_histogram_image,
 )

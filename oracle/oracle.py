@@ -26,6 +26,8 @@ Contents, each following the paper (Kaji, Sudo, Ahara, "Cubical Ripser"):
                           dL/ddeath: each is routed to the vertex that attains
                           the cell's value (maximum vertex in the filtration
                           order), summed in double.
+* ``pair_table``       -- the pairs as rows (dim, birth, death, x, y, z), located
+                          at the birth or the death cell (Sec. 4, Ex. 4.1).
 * ``lifetime_image``, ``persistent_histogram_image`` -- the localised-feature
                           images of Sec. 4 (largest lifetime, or a (birth,
                           lifetime) histogram, of the pairs located at each voxel).
@@ -450,6 +452,22 @@ def _location_pixel(L: int, shape) -> int:
     nz, ny, nx = _canon(shape)
     _, z, y, x = _decode(L, shape)
     return (z * ny + y) * nx + x
+
+
+def pair_table(shape, pairs, location: str = "birth") -> np.ndarray:
+    """One row (dim, birth, death, x, y, z) per pair, the layout of the table
+    the paper's ``computePH`` returns (Sec. 4, Ex. 4.1): (x, y, z) is the anchor
+    of the birth cell, or of the death cell with ``location="death"``; an
+    essential pair has no death cell and is located at its birth cell.  x is
+    the fastest array index; unused axes are 0."""
+    out = np.zeros((len(pairs), 6), dtype=np.float64)
+    for k in range(len(pairs)):
+        L = int(pairs["birth_L"][k])
+        if location == "death" and int(pairs["death_L"][k]) >= 0:
+            L = int(pairs["death_L"][k])
+        _, z, y, x = _decode(L, shape)
+        out[k] = (int(pairs["dim"][k]), float(pairs["birth"][k]), float(pairs["death"][k]), x, y, z)
+    return out
 
 
 def lifetime_image(shape, pairs, location: str = "birth") -> np.ndarray:

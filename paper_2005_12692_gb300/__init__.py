@@ -39,6 +39,8 @@ CR_ERR_INTERNAL = -8
 
 CR_KEEP_ZERO = 1
 CR_TOPDIM_ONLY = 2
+CR_LOC_DEATH = 4
+CR_PAIR_LOC_DEATH = 2
 
 # launch knobs (cr_tune_set)
 CR_TUNE_UF_ITEMS = 0
@@ -88,6 +90,7 @@ def lib() -> ctypes.CDLL:
         L.cr_backward.argtypes = [vp, ctypes.c_int, i64p, vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.cr_backward_batched.argtypes = [vp, i64p, i32p, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int64, vp,
                                           vp, vp, vp, ctypes.c_size_t, vp]
+        L.cr_pair_table.argtypes = [vp, ctypes.c_int64, ctypes.c_int, i64p, ctypes.c_int, vp, vp]
         L.cr_cell_location.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, i64p,
                                        ctypes.POINTER(ctypes.c_int), i64p, i64p, i64p]
         L.cr_lifetime_image.argtypes = [vp, ctypes.c_int64, ctypes.c_int, i64p, ctypes.c_int, vp, vp]
@@ -122,7 +125,7 @@ def lib() -> ctypes.CDLL:
         for f in ("cr_workspace_size", "cr_workspace_size_typical", "cr_workspace_size_batched",
                   "cr_workspace_size_batched_typical", "cr_persistence", "cr_persistence_batched",
                   "cr_backward_workspace_size", "cr_backward", "cr_backward_batched", "cr_cell_location",
-                  "cr_lifetime_image", "cr_persistent_histogram_image"):
+                  "cr_lifetime_image", "cr_persistent_histogram_image", "cr_pair_table"):
             getattr(L, f).restype = ctypes.c_int
         _lib_handle = L
     return _lib_handle
@@ -289,8 +292,11 @@ def _stream_ptr(device) -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
-def _flags(keep_zero: bool, topdim_only: bool) -> int:
-    return (CR_KEEP_ZERO if keep_zero else 0) | (CR_TOPDIM_ONLY if topdim_only else 0)
+def _flags(keep_zero: bool, topdim_only: bool, location: str = "birth") -> int:
+    if location not in ("birth", "death"):
+        raise ValueError("location must be 'birth' or 'death'")
+    return ((CR_KEEP_ZERO if keep_zero else 0) | (CR_TOPDIM_ONLY if topdim_only else 0) |
+            (CR_LOC_DEATH if location == "death" else 0))
 
 
 def _require_cuda_f32(t: torch.Tensor, name: str) -> torch.Tensor:
@@ -309,10 +315,12 @@ def _num_cells(shape) -> int:
 
 
 def cr_persistence(img: torch.Tensor, maxdim: Optional[int] = None, keep_zero: bool = False,
-                   topdim_only: bool = False, capacity: Optional[int] = None) -> Pairs:
+                   topdim_only: bool = False, capacity: Optional[int] = None, location: str = "birth") -> Pairs:
     """Persistence pairs of one 1D/2D/3D float32 CUDA image (Sec. 2 of the paper).
 
-    ``maxdim`` defaults to ndim-1 (all dimensions).  Returns pairs on the
+    ``maxdim`` defaults to ndim-1 (all dimensions).  ``location="death"``
+    records the death cell as each pair's location (CR_LOC_DEATH), which
+    ``pair_table`` and the localised images then follow.  Returns pairs on the
     image's device."""
     img = _require_cuda_f32(img, "img")
     nd = img.dim()
@@ -320,7 +328,7 @@ def cr_persistence(img: torch.Tensor, maxdim: Optional[int] = None, keep_zero: b
         raise ValueError("img must be 1D, 2D or 3D")
     if maxdim is None:
         maxdim = nd - 1
-    flags = _flags(keep_zero, topdim_only)
+    flags = _flags(keep_zero, topdim_only, location)
     shape = (ctypes.c_int64 * nd)(*img.shape)
     L = lib()
     sz = ctypes.c_size_t()
@@ -352,7 +360,8 @@ def cr_persistence(img: torch.Tensor, maxdim: Optional[int] = None, keep_zero: b
 
 
 def cr_persistence_f64(img: torch.Tensor, maxdim: Optional[int] = None, keep_zero: bool = False,
-                       topdim_only: bool = False, capacity: Optional[int] = None) -> Pairs64:
+                       topdim_only: bool = False, capacity: Optional[int] = None,
+                       location: str = "birth") -> Pairs64:
     """Persistence pairs of one 1D/2D/3D float64 CUDA image, with float64
     births and deaths (the library ranks the values on the device and runs
     the float32 path on the ranks; include/cr.h, cr_persistence_f64)."""
@@ -366,7 +375,7 @@ def cr_persistence_f64(img: torch.Tensor, maxdim: Optional[int] = None, keep_zer
         raise ValueError("img must be 1D, 2D or 3D")
     if maxdim is None:
         maxdim = nd - 1
-    flags = _flags(keep_zero, topdim_only)
+    flags = _flags(keep_zero, topdim_only, location)
     shape = (ctypes.c_int64 * nd)(*img.shape)
     L = lib()
     if capacity is None:
@@ -414,7 +423,7 @@ def _pack(images: Sequence[torch.Tensor]):
 
 def cr_persistence_batched(images, maxdim: Optional[int] = None, keep_zero: bool = False,
                            topdim_only: bool = False, shapes=None, offsets=None,
-                           capacity: Optional[int] = None) -> BatchedPairs:
+                           capacity: Optional[int] = None, location: str = "birth") -> BatchedPairs:
     """Persistence of many images in one pass.  ``images`` is a list of CUDA
     float32 tensors (same ndim, any shapes), or a packed 1D tensor together
     with ``shapes`` (list of tuples) and ``offsets`` (list of n+1 ints)."""
@@ -435,7 +444,7 @@ def cr_persistence_batched(images, maxdim: Optional[int] = None, keep_zero: bool
     nimg = len(shapes)
     if maxdim is None:
         maxdim = nd - 1
-    flags = _flags(keep_zero, topdim_only)
+    flags = _flags(keep_zero, topdim_only, location)
     sh = (ctypes.c_int32 * (nimg * nd))(*[v for s in shapes for v in s])
     of = (ctypes.c_int64 * (nimg + 1))(*offs)
     L = lib()
@@ -512,13 +521,28 @@ def cr_backward_batched(flat: torch.Tensor, shapes, offsets, bp: BatchedPairs, g
     return grad
 
 
-_LOCATIONS = {"birth": 0, "death": 1}
+_LOCATIONS = {None: -1, "pairs": -1, "birth": 0, "death": 1}
 
 
-def lifetime_image(shape: Sequence[int], pairs: Pairs, location: str = "birth") -> torch.Tensor:
+def pair_table(shape: Sequence[int], pairs: Pairs, location: Optional[str] = None) -> torch.Tensor:
+    """The pairs as the paper's (n, 6) float64 table (dim, birth, death, x, y, z)
+    (Sec. 4, Ex. 4.1), located at the birth or death cell; ``None`` follows what
+    each pair records (the ``location`` given to ``cr_persistence``)."""
+    shape = tuple(int(v) for v in shape)
+    nd = len(shape)
+    out = torch.empty((pairs.n, 6), dtype=torch.float64, device=pairs.raw.device)
+    sh = (ctypes.c_int64 * nd)(*shape)
+    _check(lib().cr_pair_table(ctypes.c_void_p(pairs.raw.data_ptr() if pairs.n else 0), pairs.n, nd, sh,
+                               _LOCATIONS[location], ctypes.c_void_p(out.data_ptr() if pairs.n else 0),
+                               _stream_ptr(out.device)))
+    return out
+
+
+def lifetime_image(shape: Sequence[int], pairs: Pairs, location: Optional[str] = None) -> torch.Tensor:
     """Lifetime channels (ndim, *shape) of the lifetime enhanced image (Sec. 4):
     per dimension d, the largest lifetime of the finite pairs of dimension d
-    located at each voxel (anchor of the birth or death cell), 0 elsewhere."""
+    located at each voxel (anchor of the birth or death cell; ``None`` follows
+    what each pair records), 0 elsewhere."""
     shape = tuple(int(v) for v in shape)
     nd = len(shape)
     out = torch.empty((nd,) + shape, dtype=torch.float32, device=pairs.raw.device)
@@ -529,16 +553,16 @@ def lifetime_image(shape: Sequence[int], pairs: Pairs, location: str = "birth") 
     return out
 
 
-def lifetime_enhanced_image(img: torch.Tensor, pairs: Optional[Pairs] = None, location: str = "birth"):
+def lifetime_enhanced_image(img: torch.Tensor, pairs: Optional[Pairs] = None, location: Optional[str] = None):
     """The image stacked with its lifetime channels: (1 + ndim, *shape)."""
     img = _require_cuda_f32(img, "img")
     if pairs is None:
-        pairs = cr_persistence(img)
+        pairs = cr_persistence(img, location=location or "birth")
     return torch.cat([img.unsqueeze(0), lifetime_image(img.shape, pairs, location)], dim=0)
 
 
 def persistent_histogram_image(shape: Sequence[int], pairs: Pairs, nb: int, birth_range, nl: int,
-                               max_lifetime: float, location: str = "birth") -> torch.Tensor:
+                               max_lifetime: float, location: Optional[str] = None) -> torch.Tensor:
     """Persistent histogram image (Sec. 4): channel (d * nb + i) * nl + j counts,
     per voxel, the finite pairs of dimension d located there with birth in bin i
     of ``birth_range`` and lifetime in bin j of [0, max_lifetime)."""
@@ -582,6 +606,6 @@ class PersistentHomology(torch.autograd.Function):
 __all__ = [
     "build", "lib", "cr_persistence", "cr_persistence_batched", "cr_backward", "cr_backward_batched",
     "PersistentHomology", "Pairs", "BatchedPairs", "CRError", "cell_location", "error_string",
-    "CR_KEEP_ZERO", "CR_TOPDIM_ONLY", "cr_tune_set", "cr_tune_get", "cr_persistence_f64", "Pairs64",
+    "CR_KEEP_ZERO", "CR_TOPDIM_ONLY", "CR_LOC_DEATH", "pair_table", "cr_tune_set", "cr_tune_get", "cr_persistence_f64", "Pairs64",
     "CR_TUNE_UF_ITEMS", "CR_TUNE_RED_WARPS", "CR_TUNE_UF_COMPACT",
 ]

@@ -60,7 +60,7 @@ static int64_t cube_count(int64_t nz, int64_t ny, int64_t nx) {
 
 static int plan_images(const int64_t *const *shapes_rows, int n, int ndim, int maxdim, uint32_t flags, HostPlan &P) {
     if (n < 1 || ndim < 1 || ndim > 3 || maxdim < 0) return CR_ERR_INVALID_ARG;
-    if (flags & ~(CR_KEEP_ZERO | CR_TOPDIM_ONLY)) return CR_ERR_INVALID_ARG;
+    if (flags & ~(CR_KEEP_ZERO | CR_TOPDIM_ONLY | CR_LOC_DEATH)) return CR_ERR_INVALID_ARG;
     P.segs.resize(n);
     int64_t voff = 0, coff = 0;
     for (int i = 0; i < n; i++) {
@@ -209,11 +209,13 @@ __global__ void k_out_rekey(const cr_pair *pairs, int64_t np, const uint32_t *va
     const cr_pair &p = pairs[vals[i]];
     keys[i] = what == 0 ? (uint64_t)p.dim : (uint64_t)(p.flags >> 8);
 }
-__global__ void k_out_gather(const cr_pair *src, int64_t np, const uint32_t *vals, cr_pair *dst) {
+// the final copy clears the image index (bits 8..31) and sets `setbits`
+// (CR_PAIR_LOC_DEATH when the caller asked for death locations)
+__global__ void k_out_gather(const cr_pair *src, int64_t np, const uint32_t *vals, cr_pair *dst, uint32_t setbits) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     cr_pair p = src[vals[i]];
-    p.flags &= 0xFFu;
+    p.flags = (p.flags & 0xFFu) | setbits;
     dst[i] = p;
 }
 __global__ void k_out_offsets(const uint32_t *scanned, int n, int64_t np, int64_t *offs) {
@@ -285,13 +287,13 @@ __global__ void __launch_bounds__(RK_T) k_out_rank(const cr_pair *__restrict__ p
 }
 
 __global__ void k_out_place(const cr_pair *__restrict__ tmp, const unsigned long long *__restrict__ npp, int64_t cap,
-                            const uint32_t *__restrict__ rank, cr_pair *__restrict__ pairs) {
+                            const uint32_t *__restrict__ rank, cr_pair *__restrict__ pairs, uint32_t setbits) {
     const int64_t npl = (int64_t)*npp < cap ? (int64_t)*npp : cap;
     if (npl > SMALL_SORT) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int)npl) return;
     cr_pair p = tmp[i];
-    p.flags &= 0xFFu;
+    p.flags = (p.flags & 0xFFu) | setbits;
     const uint32_t d = rank[i];
     if (d < (uint32_t)npl) pairs[d] = p;
 }
@@ -499,6 +501,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     unsigned long long hc[4];
     int rc = CR_OK;
     const bool rank_sort = n == 1 && 3 * P.vtot < ((int64_t)1 << 30);
+    const uint32_t locbits = (flags & CR_LOC_DEATH) ? CR_PAIR_LOC_DEATH : 0u;
 
     // everything up to the count readback; a fixed sequence of launches for a
     // given image, so 1D/2D single images replay it as a CUDA graph
@@ -601,7 +604,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         k_out_rank<<<dim3(SMALL_SORT / (RK_T * RK_R), slices), RK_T, 0, st>>>(pairs_out, pair_count, capacity, rank,
                                                                             tmp);
         CR_NOTE_LAUNCH();
-        k_out_place<<<SMALL_SORT / 256, 256, 0, st>>>(tmp, pair_count, capacity, rank, pairs_out);
+        k_out_place<<<SMALL_SORT / 256, 256, 0, st>>>(tmp, pair_count, capacity, rank, pairs_out, locbits);
         prof_end(st, STAGE_OUT_SORT, 64.0 * SMALL_SORT);
     }
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
@@ -669,7 +672,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
             }
             cudaMemcpyAsync(tmp, pairs_out, (size_t)np * sizeof(cr_pair), cudaMemcpyDeviceToDevice, st);
             CR_NOTE_LAUNCH();
-            k_out_gather<<<nbk(np), 256, 0, st>>>(tmp, np, v0, pairs_out);
+            k_out_gather<<<nbk(np), 256, 0, st>>>(tmp, np, v0, pairs_out, locbits);
             prof_end(st, STAGE_OUT_SORT, 3.0 * 24.0 * np + 64.0 * np);
         }
         if (pair_offsets) {

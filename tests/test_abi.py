@@ -66,6 +66,7 @@ def test_workspace_sizes(cr):
         assert rc == 0 and 0 < typ <= worst
     assert _ws(cr, (0, 5))[0] == cr.CR_ERR_INVALID_ARG
     assert _ws(cr, (5, 5), flags=64)[0] == cr.CR_ERR_INVALID_ARG
+    assert _ws(cr, (5, 5), flags=cr.CR_LOC_DEATH | cr.CR_KEEP_ZERO)[0] == 0
     assert _ws(cr, (2048, 2048, 2048))[0] == cr.CR_ERR_TOO_LARGE
     lib = cr.lib()
     shapes = (ctypes.c_int32 * 6)(28, 30, 256, 31, 40, 40)
@@ -105,6 +106,13 @@ def test_image_entry_points_check_arguments_on_the_host(cr):
     assert h(p, 1, 2, sh, 0, 2, 1.0, 1.0, 2, 1.0, p, None) == cr.CR_ERR_INVALID_ARG          # empty birth range
     assert h(p, 1, 2, sh, 0, 2, 0.0, 1.0, 2, 0.0, p, None) == cr.CR_ERR_INVALID_ARG          # lifetime range
     assert h(p, 1, 2, sh, 0, 2, 0.0, 1.0, 0, 1.0, p, None) == cr.CR_ERR_INVALID_ARG          # nl
+    t = lib.cr_pair_table
+    assert t(p, 1, 2, sh, 0, None, None) == cr.CR_ERR_INVALID_ARG                          # no output
+    assert t(p, 1, 2, sh, 2, p, None) == cr.CR_ERR_INVALID_ARG                             # location
+    assert t(p, 1, 2, sh, -2, p, None) == cr.CR_ERR_INVALID_ARG                            # location
+    assert t(p, 1, 0, sh, 0, p, None) == cr.CR_ERR_INVALID_ARG                             # ndim
+    assert t(p, 1, 2, bad, 0, p, None) == cr.CR_ERR_INVALID_ARG                            # extent
+    assert t(None, 0, 2, sh, -1, None, None) == 0                                          # nothing to do
 
 
 def test_f64_entry_points_check_arguments_on_the_host(cr):

@@ -64,3 +64,27 @@ def test_images_of_no_pairs_are_zero(cr):
     p = cr.cr_persistence(t)  # a constant image: only the essential class
     assert not cr.lifetime_image(t.shape, p).any()
     assert not cr.persistent_histogram_image(t.shape, p, 2, (0.0, 1.0), 2, 1.0).any()
+
+
+def test_death_location_flag(cr, oracle_mod):
+    # CR_LOC_DEATH (the location option of Sec. 4): every pair records the death
+    # cell as its location; the pair table and the localised images follow it
+    for img in _cases():
+        t = torch.from_numpy(img).cuda()
+        ref = _oracle_pairs(oracle_mod, img)
+        pd = cr.cr_persistence(t, location="death")
+        assert bool(((pd.flags & cr.CR_PAIR_LOC_DEATH) != 0).all())
+        pb = cr.cr_persistence(t)
+        assert not bool(((pb.flags & cr.CR_PAIR_LOC_DEATH) != 0).any())
+        assert torch.equal(pd.raw.view(torch.int64)[:, 2:], pb.raw.view(torch.int64)[:, 2:])  # same cells
+        for pairs, loc in ((pd, "death"), (pb, "birth")):
+            got = cr.lifetime_image(img.shape, pairs).cpu().numpy()
+            assert np.array_equal(got, oracle_mod.lifetime_image(img.shape, ref, loc))
+            rows = sorted(map(tuple, cr.pair_table(img.shape, pairs).cpu().numpy().tolist()))
+            exp = sorted(map(tuple, oracle_mod.pair_table(img.shape, ref, loc).tolist()))
+            assert rows == exp
+        # an explicit location overrides what the pairs record
+        got = cr.lifetime_image(img.shape, pd, "birth").cpu().numpy()
+        assert np.array_equal(got, oracle_mod.lifetime_image(img.shape, ref, "birth"))
+        rows = sorted(map(tuple, cr.pair_table(img.shape, pb, "death").cpu().numpy().tolist()))
+        assert rows == sorted(map(tuple, oracle_mod.pair_table(img.shape, ref, "death").tolist()))

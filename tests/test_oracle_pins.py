@@ -459,3 +459,28 @@ def test_gradient_on_ties_by_hand(oracle_mod):
         if dl >= 0:
             want[deaths[(d, dl)]] += gd[k]
     assert oracle_mod.gradient(img, p, gb, gd).reshape(-1).tolist() == want.tolist()
+
+
+def test_pair_table_by_hand(oracle_mod):
+    # 1D [0, 2, 1, 3]: the component born at vertex 2 (value 1) dies at the edge
+    # (0, 1) of value 2 (the equal-valued edge (1, 2) enters first and kills the
+    # younger vertex 1 at zero length); vertex 0 is essential.
+    p = oracle_mod.persistence(np.array([0, 2, 1, 3], np.float32))
+    p = p[p["birth"] != p["death"]]
+    rows = sorted(map(tuple, oracle_mod.pair_table((4,), p).tolist()))
+    assert rows == [(0.0, 0.0, float("inf"), 0.0, 0.0, 0.0), (0.0, 1.0, 2.0, 2.0, 0.0, 0.0)]
+    rows = sorted(map(tuple, oracle_mod.pair_table((4,), p, "death").tolist()))
+    assert rows == [(0.0, 0.0, float("inf"), 0.0, 0.0, 0.0), (0.0, 1.0, 2.0, 0.0, 0.0, 0.0)]
+    # 2D [[0, 5, 1], [5, 5, 5]] (rows y, columns x).  At value 5 the vertices
+    # enter (L 5, 4, 3, 1), then the edges by descending L: y-edges 8, 7, 6 and
+    # x-edges 4, 3, 1, 0 (L = (m*Ny + y)*Nx + x).  Edge 3, the x-edge anchored
+    # at (x 0, y 1), joins the component of vertex 0 (born 0) with the one of
+    # vertex 2 (born 1): [1, 5) is born at (x 2, y 0) and dies at (x 0, y 1).
+    img = np.array([[0, 5, 1], [5, 5, 5]], np.float32)
+    p = oracle_mod.persistence(img)
+    assert (0, 2, 3) in cellset(p)
+    p = p[p["birth"] != p["death"]]
+    rows = sorted(map(tuple, oracle_mod.pair_table(img.shape, p).tolist()))
+    assert rows == [(0.0, 0.0, float("inf"), 0.0, 0.0, 0.0), (0.0, 1.0, 5.0, 2.0, 0.0, 0.0)]
+    rows = sorted(map(tuple, oracle_mod.pair_table(img.shape, p, "death").tolist()))
+    assert rows == [(0.0, 0.0, float("inf"), 0.0, 0.0, 0.0), (0.0, 1.0, 5.0, 0.0, 1.0, 0.0)]
