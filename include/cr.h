@@ -330,6 +330,33 @@ int cr_h1_last_stats(int64_t *out, int n);
 int cr_tune_set(int knob, int value);
 int cr_tune_get(int knob, int *value);
 
+/* Limits of the bounded device-side waits, for tests of the error paths.
+ * Every wait in the library gives up after a limit and makes the call return
+ * CR_ERR_TIMEOUT (the status is read by the host; no kernel traps, and the
+ * CUDA context stays usable).  This call lowers the limits so that a test can
+ * make a wait run out:
+ *   barrier_polls          polls of one grid-barrier wait of the union-find
+ *                          kernels (0 = the default, 2^24);
+ *   reduce_iters           iterations one column of the 3D middle-dimension
+ *                          reduction may take (0 = the default, 2^24);
+ *   barrier_unsatisfiable  1: the grid barriers wait for one block more than
+ *                          the grid has (a flag that nothing sets), so every
+ *                          barrier wait runs out after barrier_polls polls;
+ *                          0: normal barriers.
+ * Host-side and per process; launch sequences cached as CUDA graphs are
+ * captured afresh.  Returns CR_ERR_INVALID_ARG for a negative limit or a flag
+ * other than 0/1.
+ *
+ * Host-side fault injection: with CR_FAULT=<site> in the environment (read at
+ * each call), cr_persistence, cr_persistence_batched, cr_persistence_f64 and
+ * cr_persistence_noalloc fail as that fault would, leaving no GPU state
+ * behind: "shape" -> CR_ERR_INVALID_ARG and "nan" -> CR_ERR_NAN before any
+ * GPU work, "workspace" -> CR_ERR_WORKSPACE (cr_last_error_detail names the
+ * injection) before any GPU work, "capacity" -> the call runs with no room
+ * for pairs and returns CR_ERR_CAPACITY with *n_pairs = the pairs needed.
+ * Any other value is ignored. */
+int cr_debug_limits(int64_t barrier_polls, int64_t reduce_iters, int barrier_unsatisfiable);
+
 /* Static description of an error code. */
 const char *cr_error_string(int code);
 

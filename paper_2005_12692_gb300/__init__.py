@@ -118,6 +118,8 @@ def lib() -> ctypes.CDLL:
         L.cr_persistence_f64.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, vp, ctypes.c_int64, i64p, vp,
                                          ctypes.c_size_t, vp, ctypes.c_uint32]
         L.cr_persistence_f64.restype = ctypes.c_int
+        L.cr_debug_limits.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+        L.cr_debug_limits.restype = ctypes.c_int
         L.cr_tune_set.argtypes = [ctypes.c_int, ctypes.c_int]
         L.cr_tune_set.restype = ctypes.c_int
         L.cr_tune_get.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
@@ -146,6 +148,13 @@ def error_string(code: int) -> str:
 def cr_tune_set(knob: int, value: int) -> None:
     """Set a launch knob of the library (see include/cr.h); raises on an unknown knob or a bad value."""
     _check(lib().cr_tune_set(int(knob), int(value)))
+
+
+def debug_limits(barrier_polls: int = 0, reduce_iters: int = 0, barrier_unsatisfiable: bool = False) -> None:
+    """Lower the limits of the library's bounded device waits (tests of the
+    error paths; include/cr.h, cr_debug_limits).  No arguments restores the
+    defaults."""
+    _check(lib().cr_debug_limits(int(barrier_polls), int(reduce_iters), int(bool(barrier_unsatisfiable))))
 
 
 def cr_tune_get(knob: int) -> int:
@@ -607,5 +616,5 @@ __all__ = [
     "build", "lib", "cr_persistence", "cr_persistence_batched", "cr_backward", "cr_backward_batched",
     "PersistentHomology", "Pairs", "BatchedPairs", "CRError", "cell_location", "error_string",
     "CR_KEEP_ZERO", "CR_TOPDIM_ONLY", "CR_LOC_DEATH", "pair_table", "cr_tune_set", "cr_tune_get", "cr_persistence_f64", "Pairs64",
-    "CR_TUNE_UF_ITEMS", "CR_TUNE_RED_WARPS", "CR_TUNE_UF_COMPACT",
+    "CR_TUNE_UF_ITEMS", "CR_TUNE_RED_WARPS", "CR_TUNE_UF_COMPACT", "debug_limits",
 ]

@@ -12,6 +12,7 @@
 #include <mutex>
 #include <vector>
 #include <cmath>
+#include <cstdlib>
 
 namespace cr {
 
@@ -24,9 +25,42 @@ static const int g_tune_lo[CR_TUNE_COUNT] = {1, 1, 1}, g_tune_hi[CR_TUNE_COUNT] 
 int tune_value(int knob) { return g_tune[knob].load(std::memory_order_relaxed); }
 uint32_t tune_epoch() { return g_tune_epoch.load(std::memory_order_relaxed); }
 
-
 static thread_local int g_detail = 0;
 void set_host_detail(int site) { g_detail = site; }
+
+// limits of the bounded device waits (cr_debug_limits)
+static std::atomic<long long> g_dbg_polls{DEFAULT_BARRIER_POLLS}, g_dbg_iters{DEFAULT_REDUCE_ITERS};
+static std::atomic<unsigned int> g_dbg_extra{0};
+DebugLimits debug_limits() {
+    return DebugLimits{g_dbg_polls.load(std::memory_order_relaxed), g_dbg_iters.load(std::memory_order_relaxed),
+                       g_dbg_extra.load(std::memory_order_relaxed)};
+}
+
+// Host-side fault injection (CR_FAULT=<site> in the environment, read at each
+// call): the forward entry points fail as the named fault would, before any
+// GPU work ("shape", "nan", "workspace") or, for "capacity", by running with
+// no room for pairs, so that every error return can be exercised without a
+// faulty input or a GPU fault.
+enum Fault { FAULT_NONE = 0, FAULT_SHAPE, FAULT_NAN, FAULT_WORKSPACE, FAULT_CAPACITY };
+static int injected_fault() {
+    const char *e = getenv("CR_FAULT");
+    if (!e || !*e) return FAULT_NONE;
+    if (!strcmp(e, "shape")) return FAULT_SHAPE;
+    if (!strcmp(e, "nan")) return FAULT_NAN;
+    if (!strcmp(e, "workspace")) return FAULT_WORKSPACE;
+    if (!strcmp(e, "capacity")) return FAULT_CAPACITY;
+    return FAULT_NONE;
+}
+int injected_error_before_gpu() {
+    switch (injected_fault()) {
+    case FAULT_SHAPE: return CR_ERR_INVALID_ARG;
+    case FAULT_NAN: return CR_ERR_NAN;
+    case FAULT_WORKSPACE: g_detail = SITE_INJECTED; return CR_ERR_WORKSPACE;
+    default: return CR_OK;
+    }
+}
+
+
 
 // ---------------------------------------------------------------------------
 // planning
@@ -474,6 +508,8 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     (void)maxdim;
     const int n = (int)P.segs.size();
     g_detail = 0;
+    if (int e = injected_error_before_gpu()) return e;
+    if (injected_fault() == FAULT_CAPACITY) capacity = 0;
     size_t need_min = fixed_bytes(P) + 1024;
     if (!ws || ws_bytes < need_min) { g_detail = SITE_FIXED; return CR_ERR_WORKSPACE; }
     Carver C(ws, ws_bytes);
@@ -862,6 +898,16 @@ int cr_tune_set(int knob, int value) {
     return CR_OK;
 }
 
+int cr_debug_limits(int64_t barrier_polls, int64_t reduce_iters, int barrier_unsatisfiable) {
+    if (barrier_polls < 0 || reduce_iters < 0 || barrier_unsatisfiable < 0 || barrier_unsatisfiable > 1)
+        return CR_ERR_INVALID_ARG;
+    cr::g_dbg_polls.store(barrier_polls ? (long long)barrier_polls : cr::DEFAULT_BARRIER_POLLS);
+    cr::g_dbg_iters.store(reduce_iters ? (long long)reduce_iters : cr::DEFAULT_REDUCE_ITERS);
+    cr::g_dbg_extra.store((unsigned int)barrier_unsatisfiable);
+    cr::g_tune_epoch.fetch_add(1);  // launch sequences cached as graphs hold the old limits
+    return CR_OK;
+}
+
 int cr_tune_get(int knob, int *value) {
     if (knob < 0 || knob >= CR_TUNE_COUNT || !value) return CR_ERR_INVALID_ARG;
     *value = cr::tune_value(knob);
@@ -1003,6 +1049,7 @@ const char *cr_last_error_detail(void) {
     case cr::SITE_H1_CARVE: return "reduction region";
     case cr::SITE_OUT_CARVE: return "output sort region";
     case cr::SITE_FIXED: return "fixed part of the workspace";
+    case cr::SITE_INJECTED: return "injected by CR_FAULT=workspace";
     default: return "unknown";
     }
 }

@@ -149,6 +149,7 @@ int cr_persistence_f64(const double *img, int ndim, const int64_t *shape, int ma
                        uint32_t flags) {
     using namespace cr;
     if (!img || !pairs_out || !n_pairs || !ws || capacity < 0) return CR_ERR_INVALID_ARG;
+    if (int e = injected_error_before_gpu()) return e;
     int64_t nv = 0;
     int rc = f64_voxels(ndim, shape, nv);
     if (rc) return rc;

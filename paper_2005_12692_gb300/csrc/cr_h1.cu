@@ -485,6 +485,7 @@ struct RedParams {
     unsigned long long *next; // work counter
     unsigned long long *stats;
     int *status;
+    int64_t cap;              // iterations one column may take before CR_ERR_TIMEOUT
 };
 
 __device__ __forceinline__ uint64_t ld_cg(const uint64_t *p) { return __ldcg((const unsigned long long *)p); }
@@ -1253,7 +1254,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
     W.cap = R.maxlen;
     W.mg[0] = W.mg[1] = nullptr;
     W.mid_on = false;
-    const int64_t CAP = (int64_t)1 << 24;
+    const int64_t CAP = R.cap;
     for (;;) {
         unsigned long long jj = 0;
         if (lane == 0) jj = atomicAdd(R.next, 1ull);
@@ -1462,8 +1463,12 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     }
     prof_end(st, STAGE_H1_SCAN, 5.0 * vtot);
     unsigned long long hc = 0;
+    int hstatus = 0;
     cudaMemcpyAsync(&hc, &B.cnt[0], sizeof(hc), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
+    // an earlier stage failed (its status is returned by the caller): no reduction on its output
+    if (hstatus) return CR_OK;
     int64_t ncols = (int64_t)hc;
     *ncols_out = ncols;
     if (ncols > B.max_cols) { set_host_detail(SITE_COLUMNS); return CR_ERR_WORKSPACE; }
@@ -1498,6 +1503,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     R.next = &B.cnt[2];
     R.stats = &B.cnt[8];
     R.status = status;
+    R.cap = debug_limits().reduce_iters;
     // B.nwarps = 16 warps per SM (the scratch is sized for them); the knob may launch fewer
     int64_t warps = B.nwarps / 16 * tune_value(CR_TUNE_RED_WARPS);
     if (warps > B.nwarps) warps = B.nwarps;

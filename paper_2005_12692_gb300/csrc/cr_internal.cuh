@@ -208,7 +208,7 @@ __host__ __device__ __forceinline__ uint32_t cube_L(const Seg &s, int m, int x, 
 // ---------------------------------------------------------------------------
 enum Site {
     SITE_NONE = 0, SITE_GROUPS = 1, SITE_EDGES = 2, SITE_COLUMNS = 3, SITE_ARENA = 4, SITE_POOL = 5,
-    SITE_UF_CARVE = 6, SITE_H1_CARVE = 7, SITE_OUT_CARVE = 8, SITE_FIXED = 9
+    SITE_UF_CARVE = 6, SITE_H1_CARVE = 7, SITE_OUT_CARVE = 8, SITE_FIXED = 9, SITE_INJECTED = 10
 };
 __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
 __device__ __forceinline__ void fail_ws(int *status, int site) {
@@ -363,5 +363,18 @@ void prof_add_bytes(int stage, double bytes);
 // launch knobs (cr_tune_set); tune_epoch() changes whenever one does
 int tune_value(int knob);
 uint32_t tune_epoch();
+
+// limits of the bounded device waits (cr_debug_limits): the defaults, or the
+// lowered values the error-path tests set
+struct DebugLimits {
+    long long barrier_polls;    // polls of one grid-barrier wait
+    long long reduce_iters;     // iterations of one column of the middle-dimension reduction
+    unsigned int barrier_extra; // arrivals a barrier expects beyond the grid (1 = never satisfied)
+};
+DebugLimits debug_limits();
+// the error a CR_FAULT injection makes a forward call return before any GPU work (CR_OK: none)
+int injected_error_before_gpu();
+constexpr long long DEFAULT_BARRIER_POLLS = 1ll << 24;
+constexpr long long DEFAULT_REDUCE_ITERS = 1ll << 24;
 
 }  // namespace cr

@@ -1005,14 +1005,17 @@ struct RoundArgs {
     int ngraph;
     int compact_mult;  // compact the edge list while it holds > compact_mult edges per thread
     int *status;
+    long long polls;   // poll limit of each barrier wait
+    unsigned int extra;  // arrivals the barriers expect beyond the grid (0; error-path tests only)
 };
 
 // Grid barrier on a monotonic arrival counter: thread 0 of every block adds 1
 // with release semantics and polls with acquire loads until all blocks of
 // barrier number n have arrived (counter >= n * blocks).  Returns false when
-// another block reported an error or the wait gave up (CR_ERR_TIMEOUT).
-constexpr long long BARRIER_POLLS = 1ll << 24;
-__device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int &target, int *status) {
+// another block reported an error or the wait gave up after `limit` polls
+// (CR_ERR_TIMEOUT).
+__device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int &target, int *status,
+                                             long long limit) {
     __shared__ int s_ok;
     target += gridDim.x;
     __syncthreads();
@@ -1025,7 +1028,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int &
             if ((int)(v - target) >= 0) break;
             if ((polls & 63) == 0) {
                 if (*(volatile int *)status) { ok = 0; break; }
-                if (polls > BARRIER_POLLS) {
+                if (polls > limit) {
                     set_status(status, CR_ERR_TIMEOUT);
                     ok = 0;
                     break;
@@ -1058,6 +1061,8 @@ struct BasinArgs {
     int64_t n[MAX_GRAPHS];
     UF u[MAX_GRAPHS];
     int *status;
+    long long polls;     // poll limit of each barrier wait
+    unsigned int extra;  // arrivals the barriers expect beyond the grid (0; error-path tests only)
 };
 
 __device__ __forceinline__ int doubling_pass(uint32_t *lab, int64_t n, int64_t tid, int64_t nthr) {
@@ -1089,7 +1094,7 @@ __device__ __forceinline__ int doubling_pass(uint32_t *lab, int64_t n, int64_t t
 __global__ void __launch_bounds__(BASIN_THREADS, 1) k_basins(BasinArgs A) {
     if (*(volatile int *)A.status) return;
     unsigned int *bar = (unsigned int *)&A.u[0].cnt[UFC_BAR_BASINS];
-    unsigned int target = 0;
+    unsigned int target = A.extra;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     bool live[MAX_GRAPHS] = {A.ngraph > 0, A.ngraph > 1};
@@ -1105,7 +1110,7 @@ __global__ void __launch_bounds__(BASIN_THREADS, 1) k_basins(BasinArgs A) {
             const int ch = doubling_pass(A.u[gi].lab, A.n[gi], tid, nthr);
             if (__syncthreads_or(ch) && threadIdx.x == 0) atomicAdd(&cnt[UFC_CHANGED + pass % 3], 1ull);
         }
-        if (!grid_barrier(bar, target, A.status)) return;
+        if (!grid_barrier(bar, target, A.status, A.polls)) return;
         bool any = false;
 #pragma unroll
         for (int gi = 0; gi < MAX_GRAPHS; gi++) {
@@ -1157,7 +1162,7 @@ __global__ void __launch_bounds__(BASIN_THREADS, 1) k_basins(BasinArgs A) {
             lab[v] = 0x80000000u | (uint32_t)g;
         }
     }
-    if (!grid_barrier(bar, target, A.status)) return;
+    if (!grid_barrier(bar, target, A.status, A.polls)) return;
     // labels -> group ids (roots are marked; every other node points at a root)
 #pragma unroll
     for (int gi = 0; gi < MAX_GRAPHS; gi++) {
@@ -1316,7 +1321,7 @@ __device__ __forceinline__ void phase_D(const UF &u, RoundState &R, int round, i
 
 __global__ void __launch_bounds__(UF_THREADS, 1) k_uf_rounds(RoundArgs A) {
     unsigned int *bar = (unsigned int *)&A.u[0].cnt[UFC_BAR_ROUNDS];
-    unsigned int target = 0;
+    unsigned int target = A.extra;
     if (*(volatile int *)A.status) return;
 #ifdef CR_UF_TIMING
     if (blockIdx.x == 0 && threadIdx.x == 0) g_uf_trace_n = 0;
@@ -1338,7 +1343,7 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_uf_rounds(RoundArgs A) {
             u.minE[g] = ~0ull;
         }
     }
-    if (!grid_barrier(bar, target, A.status)) return;
+    if (!grid_barrier(bar, target, A.status, A.polls)) return;
     UF_MARK(1);
 #pragma unroll
     for (int gi = 0; gi < MAX_GRAPHS; gi++) {
@@ -1354,7 +1359,7 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_uf_rounds(RoundArgs A) {
             if (__ldcg(u.minE + b) > k) atomicMin((unsigned long long *)&u.minE[b], k);
         }
     }
-    if (!grid_barrier(bar, target, A.status)) return;
+    if (!grid_barrier(bar, target, A.status, A.polls)) return;
     UF_MARK(2);
     for (int round = 0; round < (1 << 20); round++) {
         bool any = false;
@@ -1390,17 +1395,17 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_uf_rounds(RoundArgs A) {
 #pragma unroll
         for (int gi = 0; gi < MAX_GRAPHS; gi++)
             if (!R[gi].done) phase_B(A.u[gi], R[gi], round, tid, nthr);
-        if (!grid_barrier(bar, target, A.status)) return;
+        if (!grid_barrier(bar, target, A.status, A.polls)) return;
         UF_MARK(R[0].live);
 #pragma unroll
         for (int gi = 0; gi < MAX_GRAPHS; gi++)
             if (!R[gi].done) phase_C(A.u[gi], R[gi], tid, nthr);
-        if (!grid_barrier(bar, target, A.status)) return;
+        if (!grid_barrier(bar, target, A.status, A.polls)) return;
         UF_MARK(R[0].live);
 #pragma unroll
         for (int gi = 0; gi < MAX_GRAPHS; gi++)
             if (!R[gi].done) phase_D(A.u[gi], R[gi], round, tid, nthr);
-        if (!grid_barrier(bar, target, A.status)) return;
+        if (!grid_barrier(bar, target, A.status, A.polls)) return;
         UF_MARK(R[0].live);
     }
 }
@@ -1531,6 +1536,8 @@ int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
         A.segs = segs;
         A.nseg = nseg;
         A.status = status;
+        A.polls = debug_limits().barrier_polls;
+        A.extra = debug_limits().barrier_extra;
         int64_t work = 0;
         for (UF *u : {u0, u1}) {
             if (!u) continue;
@@ -1568,6 +1575,8 @@ int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
     {
         RoundArgs A{};
         A.status = status;
+        A.polls = debug_limits().barrier_polls;
+        A.extra = debug_limits().barrier_extra;
         A.compact_mult = tune_value(CR_TUNE_UF_COMPACT);
         for (UF *u : {u0, u1})
             if (u) A.u[A.ngraph++] = *u;
