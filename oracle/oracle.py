@@ -192,18 +192,24 @@ def _canon_values(img, dtype=np.float32):
     return f
 
 
+def _vertex_values(img, vs):
+    """Canonical float32 values of the listed vertices (only those are read)."""
+    return _canon_values(np.asarray(img).reshape(-1)[np.asarray(vs, dtype=np.int64)])
+
+
 def cell_value(img, dim: int, L: int) -> float:
-    f = _canon_values(img)
-    return float(max(f[v] for v in cell_vertices(dim, L, img.shape)))
+    vs = cell_vertices(dim, L, img.shape)
+    return float(max(_vertex_values(img, vs)))
 
 
 def argmax_vertex(img, dim: int, L: int) -> int:
     """The vertex that attains the cube's value: the latest vertex of the cube
     in the filtration (largest value; among equal values the smallest linear
     index, since larger indices enter first)."""
-    f = _canon_values(img)
     vs = cell_vertices(dim, L, img.shape)
-    return max(vs, key=lambda v: (float(f[v]), -v))
+    f = _vertex_values(img, vs)
+    best = max(range(len(vs)), key=lambda i: (float(f[i]), -vs[i]))
+    return vs[best]
 
 
 def gradient(img, pairs, grad_birth, grad_death) -> np.ndarray:

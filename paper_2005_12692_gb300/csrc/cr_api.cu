@@ -521,7 +521,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     uint8_t *ddc = C.take<uint8_t>(P.ctot);
     int64_t mask_words = (3 * P.vtot + 31) / 32;
     uint32_t *extra = C.take<uint32_t>(mask_words);
-    if (!C.ok) return CR_ERR_WORKSPACE;
+    if (!C.ok) { g_detail = SITE_FIXED; return CR_ERR_WORKSPACE; }
     char *region = (char *)ws + ((C.used + 255) & ~(size_t)255);
     size_t region_cap = ws_bytes - ((C.used + 255) & ~(size_t)255);
     int *status = (int *)&cnt[0];
@@ -596,7 +596,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         B.appmask = R.take<uint32_t>((3 * P.vtot + 31) / 32);
         B.scratch = R.take<uint64_t>((size_t)nw * 2 * ml);
         B.cnt = &cnt[CNT_H1];
-        if (!R.ok) return CR_ERR_WORKSPACE;
+        if (!R.ok) { g_detail = SITE_H1_CARVE; return CR_ERR_WORKSPACE; }
         size_t left = R.cap - R.used;
         // columns (32 B each + sort temp) get up to half of what is left, the arena the rest
         int64_t max_cols = (int64_t)((left / 2) / 40) - 1024;
@@ -610,7 +610,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         B.sort_temp_bytes = radix_temp_bytes(max_cols);
         B.sort_temp = R.take<char>(B.sort_temp_bytes);
         B.max_cols = max_cols;
-        if (!R.ok) return CR_ERR_WORKSPACE;
+        if (!R.ok) { g_detail = SITE_H1_CARVE; return CR_ERR_WORKSPACE; }
         left = R.cap - R.used;
         // the rest: 60% arena of published columns, 40% pool for long columns
         B.arena_cap = (int64_t)((left / 8) * 3 / 5) - 64;
@@ -807,7 +807,7 @@ static int backward_impl(const float *imgs, HostPlan &P, const cr_pair *pairs, c
     const int n = (int)P.segs.size();
     if (np < 0 || (np > 0 && (!pairs || !gb || !gd)) || !grad) return CR_ERR_INVALID_ARG;
     if (np >= ((int64_t)1 << 30)) return CR_ERR_TOO_LARGE;
-    if (!ws || ws_bytes < backward_bytes(np, n)) return CR_ERR_WORKSPACE;
+    if (!ws || ws_bytes < backward_bytes(np, n)) { g_detail = SITE_FIXED; return CR_ERR_WORKSPACE; }
     Carver C(ws, ws_bytes);
     Seg *segs = C.take<Seg>(n);
     int64_t nc = 2 * np;
@@ -815,7 +815,7 @@ static int backward_impl(const float *imgs, HostPlan &P, const cr_pair *pairs, c
     uint32_t *v0 = C.take<uint32_t>(nc + 1), *v1 = C.take<uint32_t>(nc + 1);
     size_t rt = radix_temp_bytes(nc + 1);
     void *rtemp = C.take<char>(rt);
-    if (!C.ok) return CR_ERR_WORKSPACE;
+    if (!C.ok) { g_detail = SITE_FIXED; return CR_ERR_WORKSPACE; }
     cudaMemcpyAsync(segs, P.segs.data(), n * sizeof(Seg), cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(grad, 0, (size_t)P.vtot * sizeof(float), st);
     if (np > 0) {

@@ -154,7 +154,10 @@ int cr_persistence_f64(const double *img, int ndim, const int64_t *shape, int ma
     int rc = f64_voxels(ndim, shape, nv);
     if (rc) return rc;
     const F64Layout L = f64_layout(nv, capacity);
-    if (((uintptr_t)ws & 255u) != 0 || ws_bytes <= L.total) return CR_ERR_WORKSPACE;
+    if (((uintptr_t)ws & 255u) != 0 || ws_bytes <= L.total) {
+        set_host_detail(SITE_FIXED);
+        return CR_ERR_WORKSPACE;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     char *base = (char *)ws;
     float *rank_img = (float *)(base + L.rank);

@@ -1461,7 +1461,10 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
         k_h1_scan<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(I, segs, nseg, B.colkey, B.colseg, &B.cnt[0],
                                                                 B.max_cols, pb, flags, status);
     }
-    prof_end(st, STAGE_H1_SCAN, 5.0 * vtot);
+    // algorithmic bytes: value and hook code read (5 B), death-mask bits read and
+    // apparent-pivot bits written (3/8 B each) per voxel; 12 B per residual
+    // column written (added below once the count is known)
+    prof_end(st, STAGE_H1_SCAN, 5.75 * vtot);
     unsigned long long hc = 0;
     int hstatus = 0;
     cudaMemcpyAsync(&hc, &B.cnt[0], sizeof(hc), cudaMemcpyDeviceToHost, st);
@@ -1470,6 +1473,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     // an earlier stage failed (its status is returned by the caller): no reduction on its output
     if (hstatus) return CR_OK;
     int64_t ncols = (int64_t)hc;
+    prof_add_bytes(STAGE_H1_SCAN, 12.0 * (double)(ncols < B.max_cols ? ncols : B.max_cols));
     *ncols_out = ncols;
     if (ncols > B.max_cols) { set_host_detail(SITE_COLUMNS); return CR_ERR_WORKSPACE; }
     if (ncols == 0) return CR_OK;
