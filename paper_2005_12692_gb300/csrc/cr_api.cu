@@ -200,7 +200,7 @@ static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
         int64_t cols = worst ? 3 * P.vtot : (3 * P.vtot) / 8 + 4096;
         int64_t arena = worst ? 12 * P.vtot : 2 * P.vtot + (1 << 20);
         int64_t pool = worst ? 8 * P.vtot : 2 * P.vtot + (1 << 22);
-        h1 = al((size_t)cols * 32) + al(radix_temp_bytes(cols)) + al((size_t)(3 * P.vtot) * 4) +
+        h1 = al((size_t)cols * 32) + al(radix_temp_bytes(cols)) + al((size_t)(3 * P.vtot) * 8) +
              al((size_t)((3 * P.vtot + 31) / 32) * 4) +
              al((size_t)arena * 8) + al((size_t)pool * 8) + al((size_t)nw * 2 * ml * 8) + (1 << 20);
     }
@@ -592,7 +592,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         B.nwarps = nw;
         B.maxlen = ml;
         B.P_len = 3 * P.vtot;
-        B.P = R.take<int>(B.P_len);
+        B.P = R.take<unsigned long long>(B.P_len);
         B.appmask = R.take<uint32_t>((3 * P.vtot + 31) / 32);
         B.scratch = R.take<uint64_t>((size_t)nw * 2 * ml);
         B.cnt = &cnt[CNT_H1];

@@ -472,7 +472,8 @@ struct RedParams {
     const uint64_t *colkey;   // edge key of column j, columns in cohomology order
     const uint32_t *colseg;
     int64_t ncols;
-    int *P;                   // face (global L-space index) -> owning column, -1 none
+    unsigned long long *P;    // face (global L-space index) -> owner << 33 | arena offset of the owner's version
+                              // whose head is that face (PIV_FREE: none), see piv_make
     unsigned long long *cur;  // published version of column j: offset << 24 | length (0 = none)
     uint64_t *arena;
     unsigned long long *arena_top;
@@ -489,6 +490,26 @@ struct RedParams {
 };
 
 __device__ __forceinline__ uint64_t ld_cg(const uint64_t *p) { return __ldcg((const unsigned long long *)p); }
+
+// A pivot-table entry names the owning column and the arena offset of the
+// owner's version that was published with that face as its pivot.  Published
+// versions never change, so one load gives an owner together with a column to
+// add: no second lookup of the owner's current version.  A version in the
+// arena is a header word (its length n) followed by its n entries, the first
+// of which is the pivot.
+constexpr unsigned long long PIV_FREE = ~0ull;
+constexpr int PIV_OFF_BITS = 33;
+constexpr unsigned long long PIV_OFF_MASK = (1ull << PIV_OFF_BITS) - 1;
+__device__ __forceinline__ unsigned long long piv_make(int64_t owner, unsigned long long off) {
+    return ((unsigned long long)owner << PIV_OFF_BITS) | off;
+}
+__device__ __forceinline__ int piv_owner(unsigned long long e) {
+    return e == PIV_FREE ? -1 : (int)(e >> PIV_OFF_BITS);
+}
+__device__ __forceinline__ unsigned long long piv_off(unsigned long long e) { return e & PIV_OFF_MASK; }
+// versions are read speculatively past their end (a header and four entries,
+// or a header and 31 entries): the arena keeps this much slack
+constexpr int ARENA_SLACK = 32;
 
 constexpr int DMAX = 256;      // entries of a published column staged in shared memory
 constexpr int FCAP = 256;      // capacity of the front
@@ -512,8 +533,9 @@ constexpr size_t RED_SMEM = RED_WARPS * sizeof(WarpSmem);
 // front in one parallel step, so that a pivot needs no dependent global
 // lookup.  kind 0 = neither apparent nor owned at the time of the fill,
 // kind 1 = apparent pivot (column tail c1..c3), kind 2 = owned by column
-// `own` with published version `ver` (a snapshot); when that version has at
-// most four entries and starts with the key, k > 0 and c1..c3 hold its tail.
+// `own`, `ver` the pivot-table entry read (owner and the arena offset of a
+// version with this pivot); when that version has at most four entries,
+// k > 0 and c1..c3 hold its tail.
 struct Look {
     uint64_t key, c1, c2, c3, ver;
     int kind, k, own;
@@ -554,9 +576,12 @@ struct Work {
 // diagnostic counters (cnt[8..15]): iterations, apparent additions, column
 // additions, merged entries, takeovers, stale or lost races, base rebuilds,
 // max iterations spent on one column
+constexpr int NT = 10;
 struct RedStats {
     unsigned long long it = 0, app = 0, add = 0, merged = 0, take = 0, retry = 0, flush = 0, maxit = 0;
-    unsigned long long t[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // cycles per phase (diagnostic builds)
+    // cycles per phase (diagnostic builds): refill, lookup, apparent, cached, staged, inbox
+    // flushes, misses, long iterations, whole iterations, pivot-table reads
+    unsigned long long t[NT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     bool lng = false;
 };
 #ifdef CR_H1_TIMING
@@ -564,9 +589,20 @@ struct RedStats {
 __device__ bool g_long_iter_dummy;
 #define TMARK(v) long long v = clock64()
 #define TADD(st, i, v) ((st).lng ? (void)((st).t[i] += (unsigned long long)(clock64() - (v))) : (void)0)
+// cycles of a whole iteration of a long column, on every way out of it
+struct IterTimer {
+    RedStats &s;
+    long long t0;
+    __device__ explicit IterTimer(RedStats &st) : s(st), t0(clock64()) {}
+    __device__ ~IterTimer() {
+        if (s.lng) s.t[8] += (unsigned long long)(clock64() - t0);
+    }
+};
+#define TITER(st) IterTimer iter_timer_(st)
 #else
 #define TMARK(v)
 #define TADD(st, i, v)
+#define TITER(st)
 #endif
 __device__ void flush_stats(const RedParams &R, const RedStats &s) {
     if ((threadIdx.x & 31) != 0) return;
@@ -579,7 +615,7 @@ __device__ void flush_stats(const RedParams &R, const RedStats &s) {
     atomicAdd(&c[5], s.retry);
     atomicAdd(&c[6], s.flush);
     atomicMax(&c[7], s.maxit);
-    for (int i = 0; i < 8; i++) atomicAdd(&c[8 + i], s.t[i]);
+    for (int i = 0; i < NT; i++) atomicAdd(&c[8 + i], s.t[i]);
 }
 
 // new buffer pair of at least `need` entries from the shared pool (the old
@@ -1155,7 +1191,7 @@ __device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, con
     const int64_t v0 = S.voff + ((int64_t)c[2] * S.ny + c[1]) * S.nx + c[0];
     const int64_t da = a == 0 ? 1 : (int64_t)S.nx, db = b == 1 ? (int64_t)S.nx : (int64_t)S.nx * S.ny;
     const uint32_t am = __ldcg(&R.I.appmask[bit >> 5]);
-    const int o = __ldcg(&R.P[bit]);
+    const unsigned long long pe = __ldcg(&R.P[bit]);
     const float g0 = R.I.img[v0], g1 = R.I.img[v0 + da], g2 = R.I.img[v0 + db], g3 = R.I.img[v0 + da + db];
     if ((am >> (bit & 31)) & 1u) {
         // the face's latest facet: the apparent edge
@@ -1188,28 +1224,26 @@ __device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, con
         L.k = n;
         return;
     }
-    if (o < 0) return;
-    const unsigned long long v = __ldcg(&R.cur[o]);
+    if (pe == PIV_FREE) return;
     L.kind = 2;
-    L.own = o;
-    L.ver = v;
-    const int len = (int)(v & 0xFFFFFFull);
-    if (len >= 1 && len <= 4) {
-        const uint64_t *C = R.arena + (v >> 24);
-        const uint64_t h = ld_cg(C);
-        const uint64_t a1 = len > 1 ? ld_cg(C + 1) : ~0ull, a2 = len > 2 ? ld_cg(C + 2) : ~0ull,
-                       a3 = len > 3 ? ld_cg(C + 3) : ~0ull;
-        if (h == cand) {
-            L.c1 = a1;
-            L.c2 = a2;
-            L.c3 = a3;
-            L.k = len;
-        }
+    L.own = piv_owner(pe);
+    L.ver = pe;
+    // the version's header and first four entries in one round trip (the
+    // arena keeps ARENA_SLACK words of slack past its last version)
+    const uint64_t *C = R.arena + piv_off(pe);
+    const uint64_t n = ld_cg(C), h = ld_cg(C + 1), a1 = ld_cg(C + 2), a2 = ld_cg(C + 3), a3 = ld_cg(C + 4);
+    if (n >= 1 && n <= 4 && h == cand) {
+        L.c1 = n > 1 ? a1 : ~0ull;
+        L.c2 = n > 2 ? a2 : ~0ull;
+        L.c3 = n > 3 ? a3 : ~0ull;
+        L.k = (int)n;
     }
 }
 
-// publish the working column as column j's current version
-__device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &sm, RedStats &st) {
+// publish the working column as column j's current version; *voff is the
+// arena offset of its header (for the pivot-table entry)
+__device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &sm, RedStats &st,
+                             unsigned long long *voff) {
     const int lane = threadIdx.x & 31;
     const bool levels = W.nb - W.start > 0 || (W.mid_on && W.nm - W.mstart > 0);
     const uint64_t *rest;
@@ -1226,17 +1260,19 @@ __device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &s
     }
     const int nf = W.fn - W.fh, n = nf + nrest;
     unsigned long long off = 0;
-    if (lane == 0) off = atomicAdd(R.arena_top, (unsigned long long)n);
+    if (lane == 0) off = atomicAdd(R.arena_top, (unsigned long long)(n + 1));
     off = __shfl_sync(0xFFFFFFFFu, off, 0);
-    if ((int64_t)(off + n) > R.arena_cap) return false;
-    for (int k = lane; k < nf; k += 32) __stcg((unsigned long long *)&R.arena[off + k], sm.f[W.fb][W.fh + k]);
+    if ((int64_t)(off + n + 1) > R.arena_cap || off > PIV_OFF_MASK) return false;
+    if (lane == 0) __stcg((unsigned long long *)&R.arena[off], (unsigned long long)n);
+    for (int k = lane; k < nf; k += 32) __stcg((unsigned long long *)&R.arena[off + 1 + k], sm.f[W.fb][W.fh + k]);
     for (int k = lane; k < nrest; k += 32)
-        __stcg((unsigned long long *)&R.arena[off + nf + k], levels ? ld_cg(rest + k) : rest[k]);
+        __stcg((unsigned long long *)&R.arena[off + 1 + nf + k], levels ? ld_cg(rest + k) : rest[k]);
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicExch(&R.cur[j], (off << 24) | (unsigned long long)n);
     __threadfence();
     __syncwarp();
+    *voff = off;
     return true;
 }
 
@@ -1290,6 +1326,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
             st.it++;
             if ((unsigned long long)it > st.maxit) st.maxit = (unsigned long long)it;
             st.lng = it > 16384;
+            TITER(st);
 #ifdef CR_H1_TIMING
             if (st.lng) st.t[7]++;
 #endif
@@ -1331,13 +1368,20 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
                 }
                 continue;
             }
-            const int o = hkind == 2 ? hown : __ldcg(&R.P[gidx]);
+            TMARK(t9);
+            const unsigned long long pe = hkind == 2 ? hver : __ldcg(&R.P[gidx]);
+            const int o = hkind == 2 ? hown : piv_owner(pe);
+#ifdef CR_H1_TIMING
+            if (hkind != 2) (void)__shfl_sync(0xFFFFFFFFu, (int)pe, 0);  // make the read complete here
+#endif
+            TADD(st, 9, t9);
             if (o < 0) {
-                if (!publish_work(R, j, W, sm, st)) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
-                int prev = 0;
-                if (lane == 0) prev = atomicCAS(&R.P[gidx], -1, (int)j);
+                unsigned long long voff = 0;
+                if (!publish_work(R, j, W, sm, st, &voff)) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
+                unsigned long long prev = 0;
+                if (lane == 0) prev = atomicCAS(&R.P[gidx], PIV_FREE, piv_make(j, voff));
                 prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
-                if (prev == -1) break;  // j settled
+                if (prev == PIV_FREE) break;  // j settled
                 st.retry++;
                 continue;
             }
@@ -1345,11 +1389,12 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
             // columns are numbered in cohomology order: a smaller index is an earlier column
             const bool takeover = (int64_t)o > j;  // o is a later column: j takes its pivot, then continues with o
             if (takeover) {
-                if (!publish_work(R, j, W, sm, st)) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
-                int prev = 0;
-                if (lane == 0) prev = atomicCAS(&R.P[gidx], o, (int)j);
+                unsigned long long voff = 0;
+                if (!publish_work(R, j, W, sm, st, &voff)) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
+                unsigned long long prev = 0;
+                if (lane == 0) prev = atomicCAS(&R.P[gidx], pe, piv_make(j, voff));
                 prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
-                if (prev != o) { st.retry++; continue; }
+                if (prev != pe) { st.retry++; continue; }
                 st.take++;
                 look.key = ~0ull;  // snapshots taken for column j's pivots
             }
@@ -1367,14 +1412,16 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
                 }
                 continue;
             }
-            const unsigned long long ver = (hkind == 2 && !takeover) ? hver : __ldcg(&R.cur[o]);
-            const unsigned long long off = ver >> 24;
-            const int len = (int)(ver & 0xFFFFFFull);
+            // the version of o with pivot p that the pivot-table entry names:
+            // its header and first 31 entries in one round trip
+            const uint64_t *V = R.arena + piv_off(pe);
+            const uint64_t w = ld_cg(V + lane);
+            const int len = (int)__shfl_sync(0xFFFFFFFFu, w, 0);
             if (len == 0) continue;
             bool ok2;
             if (len - 1 <= DMAX) {
-                // stage the column; a stale snapshot (head != pivot) leaves the state untouched
-                for (int q2 = lane; q2 < len; q2 += 32) sm.c[q2] = ld_cg(R.arena + off + q2);
+                if (lane >= 1 && lane <= len) sm.c[lane - 1] = w;
+                for (int q2 = 31 + lane; q2 < len; q2 += 32) sm.c[q2] = ld_cg(V + 1 + q2);
                 __syncwarp();
                 if (sm.c[0] != p) { st.retry++; continue; }
                 st.add++;
@@ -1383,11 +1430,11 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
                 ok2 = toggle_list<false>(R, W, sm, sm.c + 1, len - 1, st);
                 TADD(st, 4, t4);
             } else {
-                if (ld_cg(&R.arena[off]) != p) { st.retry++; continue; }
+                if (__shfl_sync(0xFFFFFFFFu, w, 1) != p) { st.retry++; continue; }
                 st.add++;
                 TMARK(t4);
                 W.fh++;
-                ok2 = toggle_list<true>(R, W, sm, R.arena + off + 1, len - 1, st);
+                ok2 = toggle_list<true>(R, W, sm, V + 2, len - 1, st);
                 TADD(st, 4, t4);
             }
             if (!ok2) {
@@ -1401,7 +1448,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
 }
 
 __global__ void k_h1_emit(const uint64_t *__restrict__ colkey, const uint32_t *__restrict__ colseg, int64_t ncols,
-                          const Seg *__restrict__ segs, const int *__restrict__ P,
+                          const Seg *__restrict__ segs, const unsigned long long *__restrict__ P,
                           const unsigned long long *__restrict__ cur, const uint64_t *__restrict__ arena, PairBuf pb,
                           uint32_t flags, int *status) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1409,9 +1456,10 @@ __global__ void k_h1_emit(const uint64_t *__restrict__ colkey, const uint32_t *_
     unsigned long long v = cur[j];
     int len = (int)(v & 0xFFFFFFull);
     if (len == 0) { set_status(status, CR_ERR_INTERNAL); return; }
-    uint64_t p = arena[v >> 24];
+    uint64_t p = arena[(v >> 24) + 1];  // the entry after the version's header
     const Seg S = segs[colseg[j]];
-    if (P[S.loff + key_L(p)] != (int)j) { set_status(status, CR_ERR_INTERNAL); return; }
+    const unsigned long long e = P[S.loff + key_L(p)];
+    if (e == PIV_FREE || (int64_t)(e >> PIV_OFF_BITS) != j) { set_status(status, CR_ERR_INTERNAL); return; }
     uint64_t sk = colkey[j];
     float b = key_value(sk), d = key_value(p);
     if ((flags & CR_KEEP_ZERO) || b != d) emit_pair(pb, colseg[j], 1, b, d, key_L(sk), key_L(p), 0);
@@ -1428,11 +1476,11 @@ __global__ void k_not_keys(uint64_t *k, int64_t n) {
 
 static inline unsigned nb1(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-static unsigned long long g_h1_stats[16];
+static unsigned long long g_h1_stats[24];
 static int64_t g_h1_stats_cols = 0;
 int h1_stats(int64_t *out, int n) {
     out[0] = g_h1_stats_cols;
-    for (int i = 0; i < 16 && i + 1 < n; i++) out[i + 1] = (int64_t)g_h1_stats[i];
+    for (int i = 0; i < 24 && i + 1 < n; i++) out[i + 1] = (int64_t)g_h1_stats[i];
     return CR_OK;
 }
 
@@ -1441,7 +1489,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
            int64_t *ncols_out, cudaStream_t st) {
     Img3 I{img, dd, extra, B.appmask};
     cudaMemsetAsync(B.appmask, 0, (size_t)((3 * vtot + 31) / 32) * sizeof(uint32_t), st);
-    cudaMemsetAsync(B.cnt, 0, 24 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(B.cnt, 0, 32 * sizeof(unsigned long long), st);  // counters and statistics (CNT_H1 .. CNT_H1 + 32)
     prof_begin(st, STAGE_H1_SCAN);
     CR_NOTE_LAUNCH();
     CUtensorMap tmap, tmap_dd;
@@ -1477,7 +1525,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     *ncols_out = ncols;
     if (ncols > B.max_cols) { set_host_detail(SITE_COLUMNS); return CR_ERR_WORKSPACE; }
     if (ncols == 0) return CR_OK;
-    if (ncols >= ((int64_t)1 << 31)) return CR_ERR_TOO_LARGE;
+    if (ncols >= ((int64_t)1 << 31) - 1) return CR_ERR_TOO_LARGE;  // owner field of a pivot-table entry
     // cohomology order: decreasing edge key (keys were stored complemented)
     prof_begin(st, STAGE_H1_SORT);
     if (radix_sort_u64(B.colkey, B.colseg, B.colkey_tmp, B.colseg_tmp, ncols, 0, 64, B.sort_temp, B.sort_temp_bytes,
@@ -1486,7 +1534,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     prof_end(st, STAGE_H1_SORT, 8.0 * 24.0 * ncols);
     CR_NOTE_LAUNCH();
     k_not_keys<<<nb1(ncols), 256, 0, st>>>(B.colkey, ncols);
-    cudaMemsetAsync(B.P, 0xFF, (size_t)B.P_len * sizeof(int), st);
+    cudaMemsetAsync(B.P, 0xFF, (size_t)B.P_len * sizeof(unsigned long long), st);
     cudaMemsetAsync(B.cur, 0, (size_t)ncols * sizeof(unsigned long long), st);
     RedParams R;
     R.I = I;
@@ -1498,7 +1546,9 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     R.cur = B.cur;
     R.arena = B.arena;
     R.arena_top = &B.cnt[1];
-    R.arena_cap = B.arena_cap;
+    // ARENA_SLACK words of slack: a version is read speculatively past its end
+    R.arena_cap = B.arena_cap - ARENA_SLACK;
+    if (R.arena_cap > (int64_t)PIV_OFF_MASK) R.arena_cap = (int64_t)PIV_OFF_MASK;
     R.scratch = B.scratch;
     R.maxlen = B.maxlen;
     R.pool = B.pool;
@@ -1529,7 +1579,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     prof_end(st, STAGE_H1_REDUCE, 12.0 * ncols);
     CR_NOTE_LAUNCH();
     k_h1_emit<<<nb1(ncols), 256, 0, st>>>(B.colkey, B.colseg, ncols, segs, B.P, B.cur, B.arena, pb, flags, status);
-    cudaMemcpyAsync(g_h1_stats, &B.cnt[8], 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(g_h1_stats, &B.cnt[8], 24 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     g_h1_stats_cols = ncols;
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }

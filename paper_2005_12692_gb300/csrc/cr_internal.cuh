@@ -310,7 +310,7 @@ struct H1Bufs {
     int64_t max_cols;
     void *sort_temp;
     size_t sort_temp_bytes;
-    int *P;
+    unsigned long long *P;  // face -> owner and version (cr_h1.cu, piv_make)
     int64_t P_len;
     unsigned long long *cur;
     uint64_t *arena;
