@@ -593,9 +593,15 @@ __device__ bool g_long_iter_dummy;
 struct IterTimer {
     RedStats &s;
     long long t0;
-    __device__ explicit IterTimer(RedStats &st) : s(st), t0(clock64()) {}
+    __device__ explicit IterTimer(RedStats &st) : s(st), t0(0) {
+#ifdef __CUDA_ARCH__
+        t0 = clock64();
+#endif
+    }
     __device__ ~IterTimer() {
+#ifdef __CUDA_ARCH__
         if (s.lng) s.t[8] += (unsigned long long)(clock64() - t0);
+#endif
     }
 };
 #define TITER(st) IterTimer iter_timer_(st)
