@@ -605,10 +605,33 @@ struct IterTimer {
     }
 };
 #define TITER(st) IterTimer iter_timer_(st)
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// timestamps (ns): warps' start, start and end of columns longer than 16384
+// iterations, last column end; minima are kept as maxima of complements
+#define TSTAMP_KERNEL(R) \
+    if ((threadIdx.x & 31) == 0) atomicMax(&(R).stats[18], ~gtimer())
+#define TSTAMP_COLSTART(v) const unsigned long long v = gtimer()
+#define TSTAMP_COLEND(R, it, v)                                 \
+    if ((threadIdx.x & 31) == 0) {                              \
+        const unsigned long long e_ = gtimer();                 \
+        atomicMax(&(R).stats[21], e_);                          \
+        if ((it) > 16384) {                                     \
+            atomicMax(&(R).stats[19], ~(v));                    \
+            atomicMax(&(R).stats[20], e_);                      \
+            atomicAdd(&(R).stats[22], 1ull);                    \
+        }                                                       \
+    }
 #else
 #define TMARK(v)
 #define TADD(st, i, v)
 #define TITER(st)
+#define TSTAMP_KERNEL(R)
+#define TSTAMP_COLSTART(v)
+#define TSTAMP_COLEND(R, it, v)
 #endif
 __device__ void flush_stats(const RedParams &R, const RedStats &s) {
     if ((threadIdx.x & 31) != 0) return;
@@ -1297,11 +1320,13 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
     W.mg[0] = W.mg[1] = nullptr;
     W.mid_on = false;
     const int64_t CAP = R.cap;
+    TSTAMP_KERNEL(R);
     for (;;) {
         unsigned long long jj = 0;
         if (lane == 0) jj = atomicAdd(R.next, 1ull);
         jj = __shfl_sync(0xFFFFFFFFu, jj, 0);
         if ((int64_t)jj >= R.ncols) { flush_stats(R, st); return; }
+        TSTAMP_COLSTART(col_t0);
         int64_t j = (int64_t)jj;
         const uint64_t jkey = R.colkey[j];
         const Seg S = R.segs[R.colseg[j]];
@@ -1450,6 +1475,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
             }
             if (takeover) j = o;
         }
+        TSTAMP_COLEND(R, it, col_t0);
     }
 }
 
