@@ -609,8 +609,8 @@ def main():
             latency[k] = {"ms_per_launch": s["ms"] / s["launches"], "share_of_step": s["ms"] / sum(step_ms)}
     if "h1_reduce" in latency:
         import ctypes
-        st = (ctypes.c_int64 * 25)()
-        L.cr_h1_last_stats(st, 25)
+        st = (ctypes.c_int64 * 26)()
+        L.cr_h1_last_stats(st, 26)
         maxit = int(st[8])
         latency["h1_reduce"].update({
             "residual_columns": int(st[0]), "critical_path_iterations": maxit,

@@ -369,9 +369,17 @@ __global__ void k_h0_cross(const float *__restrict__ img, const Seg *__restrict_
     const Seg S = segs[si];
     int x, y, z0, z1;
     tile_column(S, x, y, z0, z1);
-    const bool inxy = x < S.nx && y < S.ny;
+    const bool inxy0 = x < S.nx && y < S.ny;
     const uint32_t nx = (uint32_t)S.nx, plane = (uint32_t)S.nx * (uint32_t)S.ny;
-    for (int z = z0; z < z1; z++) {
+    // Edges along one axis met in consecutive planes often join the same two
+    // basins; of parallel edges between two groups only the first in the
+    // order can merge them, so a run of equal pairs is kept as one edge (the
+    // smallest key).
+    uint64_t pk[3];
+    uint32_t pa[3], pb[3];
+    bool pend[3] = {false, false, false};
+    for (int z = z0; z <= z1; z++) {
+        const bool inxy = inxy0 && z < z1;
         const uint32_t lv = (uint32_t)z * plane + (uint32_t)y * nx + (uint32_t)x;
         const int64_t gv = S.voff + lv;
         uint32_t ov = 0, la = 0;
@@ -382,32 +390,54 @@ __global__ void k_h0_cross(const float *__restrict__ img, const Seg *__restrict_
             dv = dd[gv];
         }
         uint64_t keys[3];
-        uint32_t lbs[3];
+        uint32_t las[3], lbs[3];
         int cnt = 0;
         for (int ax = 0; ax < 3; ax++) {
-            if (!inxy) break;
-            int ext = ax == 0 ? S.nx : (ax == 1 ? S.ny : S.nz);
-            int c = ax == 0 ? x : (ax == 1 ? y : z);
-            if (c + 1 >= ext) continue;
-            uint32_t du = ax == 0 ? 1u : (ax == 1 ? nx : plane);
-            int64_t u = gv + du;
-            bool stencil = dv == (uint8_t)(2 * ax + 2) || dd[u] == (uint8_t)(2 * ax + 1);
-            uint32_t lb = lab[u];
-            if (stencil || lb == la) continue;
-            if (la >= ng || lb >= ng) {
-                set_status(status, CR_ERR_INTERNAL);
+            bool emit = false;
+            uint64_t key = 0;
+            uint32_t lb = 0;
+            if (inxy) {
+                const int ext = ax == 0 ? S.nx : (ax == 1 ? S.ny : S.nz);
+                const int c = ax == 0 ? x : (ax == 1 ? y : z);
+                if (c + 1 < ext) {
+                    const uint32_t du = ax == 0 ? 1u : (ax == 1 ? nx : plane);
+                    const int64_t u = gv + du;
+                    const bool stencil = dv == (uint8_t)(2 * ax + 2) || dd[u] == (uint8_t)(2 * ax + 1);
+                    lb = lab[u];
+                    if (!stencil && lb != la) {
+                        if (la >= ng || lb >= ng) {
+                            set_status(status, CR_ERR_INTERNAL);
+                        } else {
+                            const uint32_t ou = ord32(img[u]);
+                            key = make_key(ov > ou ? ov : ou, lv + (uint32_t)ax * plane * (uint32_t)S.nz);
+                            emit = true;
+                        }
+                    }
+                }
+            }
+            if (emit && pend[ax] && pa[ax] == la && pb[ax] == lb) {
+                pk[ax] = key < pk[ax] ? key : pk[ax];  // the same two groups: one edge
                 continue;
             }
-            uint32_t ou = ord32(img[u]);
-            keys[cnt] = make_key(ov > ou ? ov : ou, lv + (uint32_t)ax * plane * (uint32_t)S.nz);
-            lbs[cnt] = lb;
-            cnt++;
+            if (pend[ax] && (emit || z == z1)) {  // the run ends: its edge goes out
+                keys[cnt] = pk[ax];
+                las[cnt] = pa[ax];
+                lbs[cnt] = pb[ax];
+                cnt++;
+                pend[ax] = false;
+            }
+            if (emit) {
+                pk[ax] = key;
+                pa[ax] = la;
+                pb[ax] = lb;
+                pend[ax] = true;
+            }
         }
         int64_t i = block_append(cnt, ne);
         for (int k = 0; k < cnt; k++) {
             if (i + k < max_edges) {
                 ek[i + k] = keys[k];
-                ea[i + k] = la;
+                ea[i + k] = las[k];
                 eb[i + k] = lbs[k];
             } else {
                 fail_ws(status, SITE_EDGES);
@@ -721,8 +751,15 @@ __global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restric
     int x, y, z0, z1;
     tile_column(S, x, y, z0, z1);
     const bool inxy = S.ncell > 0 && x < S.nx && y < S.ny;
-    for (int z = z0; z < z1; z++) {
-        const bool in = inxy;
+    // Facets of one type met in consecutive planes often join the same two
+    // groups (groups of the dual are runs along z).  Of parallel edges
+    // between two groups only the first in the order can merge them, so a
+    // run of equal group pairs is kept as one edge: its smallest key.
+    uint64_t pk[3];
+    uint32_t pa[3], pb[3];
+    bool pend[3] = {false, false, false};
+    for (int z = z0; z <= z1; z++) {
+        const bool in = inxy && z < z1;
         uint64_t keys[3];
         uint32_t las[3], lbs[3];
         int cnt = 0;
@@ -780,11 +817,22 @@ __global__ void k_dual_cross(const float *__restrict__ img, const Seg *__restric
                 set_status(status, CR_ERR_INTERNAL);
                 emit = false;
             }
-            if (emit) {
-                keys[cnt] = key;
-                las[cnt] = la;
-                lbs[cnt] = lb;
+            if (emit && pend[m] && pa[m] == la && pb[m] == lb) {
+                pk[m] = key < pk[m] ? key : pk[m];  // the same two groups: one edge
+                continue;
+            }
+            if (pend[m] && (emit || z == z1)) {  // the run ends: its edge goes out
+                keys[cnt] = pk[m];
+                las[cnt] = pa[m];
+                lbs[cnt] = pb[m];
                 cnt++;
+                pend[m] = false;
+            }
+            if (emit) {
+                pk[m] = key;
+                pa[m] = la;
+                pb[m] = lb;
+                pend[m] = true;
             }
         }
         int64_t i = block_append(cnt, ne);
