@@ -300,15 +300,15 @@ int cr_profile_select(uint32_t stage_mask);
 void cr_profile_reset(void);
 int cr_profile_read(int stage, const char **name, double *total_ms, int64_t *count, double *bytes);
 int64_t cr_launch_count(void);
-/* Counters of the last 3D reduction on this process (out[0..n), n <= 26):
+/* Counters of the last 3D reduction on this process (out[0..n), n <= 25):
  * residual columns, loop iterations, apparent-column additions, column
  * additions, merged entries, pivot takeovers, lost races and stale reads,
  * long-column buffer growths, most iterations spent on one column; then
  * (builds with CR_H1_TIMING only, zero otherwise) cycles spent in the
  * iterations of long column runs per phase: front refills, lookups, apparent
  * additions, cached additions, staged additions, inbox flushes, then lookahead
- * misses, iterations timed, whole-iteration cycles, pivot-table reads,
- * helper-cache probes and hits; then timestamps.  Host-only. */
+ * misses, iterations timed, whole-iteration cycles and pivot-table reads,
+ * then timestamps.  Host-only. */
 int cr_h1_last_stats(int64_t *out, int n);
 
 /* Launch knobs, set by the autotuner (host-side, per process).  They change

@@ -469,7 +469,6 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
 struct RedParams {
     Img3 I;
     const Seg *segs;
-    int nseg;
     const uint64_t *colkey;   // edge key of column j, columns in cohomology order
     const uint32_t *colseg;
     int64_t ncols;
@@ -528,32 +527,7 @@ struct WarpSmem {
     int q[DMAX];           // merge scratch
     int pc[DMAX + 1];
 };
-// Helper cache, shared by the warps of a block.  A warp that finds no more
-// columns to take becomes a helper: it looks up the entries just behind the
-// pivot in the front of a warp of its block that is still reducing (a long
-// column, typically the last ones of the reduction, when most of the GPU is
-// idle) and leaves the results in slots of its own.  The reducing warp reads
-// a slot when its lookahead misses instead of filling it with dependent
-// global loads.  Nothing waits for a helper: a slot is used only if its key
-// still equals the pivot after its fields were read (the key is cleared
-// first and written last), and a slot's data is immutable for its key (an
-// apparent pivot's column tail; an owner with the arena offset of a version
-// that has the key as pivot, which stays a valid column to add).
-constexpr int HC_PER_WARP = 64;
-constexpr int HC_SLOTS = RED_WARPS * HC_PER_WARP;
-struct HelpSlot {
-    unsigned long long key;  // 0 while the slot is being written
-    unsigned long long c1, c2, c3, ver;
-    int kind, k, own, pad;
-};
-struct CtaShared {
-    HelpSlot slot[HC_SLOTS];  // warp w writes slots [w * HC_PER_WARP, (w + 1) * HC_PER_WARP)
-    int busy[RED_WARPS];      // warp w is reducing columns
-    int fb[RED_WARPS], fh[RED_WARPS], fn[RED_WARPS];  // its front, as of its last iteration
-    unsigned int seg[RED_WARPS];                      // the image of its column
-    int helpers;                                      // warps that have become helpers
-};
-constexpr size_t RED_SMEM = RED_WARPS * sizeof(WarpSmem) + sizeof(CtaShared);
+constexpr size_t RED_SMEM = RED_WARPS * sizeof(WarpSmem);
 
 // Lookahead cache: one entry per lane, filled for the next 32 entries of the
 // front in one parallel step, so that a pivot needs no dependent global
@@ -602,13 +576,12 @@ struct Work {
 // diagnostic counters (cnt[8..15]): iterations, apparent additions, column
 // additions, merged entries, takeovers, stale or lost races, base rebuilds,
 // max iterations spent on one column
-constexpr int NT = 12;
+constexpr int NT = 10;
 struct RedStats {
     unsigned long long it = 0, app = 0, add = 0, merged = 0, take = 0, retry = 0, flush = 0, maxit = 0;
     // cycles per phase (diagnostic builds): refill, lookup, apparent, cached, staged, inbox
-    // flushes, misses, long iterations, whole iterations, pivot-table reads; then
-    // helper-cache probes and hits
-    unsigned long long t[NT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // flushes, misses, long iterations, whole iterations, pivot-table reads
+    unsigned long long t[NT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     bool lng = false;
 };
 #ifdef CR_H1_TIMING
@@ -640,16 +613,16 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // timestamps (ns): warps' start, start and end of columns longer than 16384
 // iterations, last column end; minima are kept as maxima of complements
 #define TSTAMP_KERNEL(R) \
-    if ((threadIdx.x & 31) == 0) atomicMax(&(R).stats[20], ~gtimer())
+    if ((threadIdx.x & 31) == 0) atomicMax(&(R).stats[18], ~gtimer())
 #define TSTAMP_COLSTART(v) const unsigned long long v = gtimer()
 #define TSTAMP_COLEND(R, it, v)                                 \
     if ((threadIdx.x & 31) == 0) {                              \
         const unsigned long long e_ = gtimer();                 \
-        atomicMax(&(R).stats[23], e_);                          \
+        atomicMax(&(R).stats[21], e_);                          \
         if ((it) > 16384) {                                     \
-            atomicMax(&(R).stats[21], ~(v));                    \
-            atomicMax(&(R).stats[22], e_);                      \
-            atomicAdd(&(R).stats[24], 1ull);                    \
+            atomicMax(&(R).stats[19], ~(v));                    \
+            atomicMax(&(R).stats[20], e_);                      \
+            atomicAdd(&(R).stats[22], 1ull);                    \
         }                                                       \
     }
 #else
@@ -1232,19 +1205,9 @@ __device__ bool toggle_list(const RedParams &R, Work &W, WarpSmem &sm, const uin
 // apparent face then needs its latest facet's cofacets (a second), an owned
 // face its owner's version and, when short, that version's entries (a second
 // and a third).
-// a face L-index of this image (helpers read fronts that may be changing)
-__device__ __forceinline__ bool face_in_image(const Seg &S, uint32_t L) {
-    if (S.edim != 3) return false;
-    const uint32_t P = (uint32_t)S.nx * (uint32_t)S.ny * (uint32_t)S.nz;
-    if (L >= 3u * P) return false;
-    int fm, c[3];
-    decode_L(S, L, fm, c);
-    const int a = fm == 2 ? 1 : 0, b = fm == 0 ? 1 : 2;
-    const int na = a == 0 ? S.nx : S.ny, nb = b == 1 ? S.ny : S.nz;
-    return c[a] + 1 < na && c[b] + 1 < nb;
-}
-
-__device__ __noinline__ void look_fill(const RedParams &R, const Seg &S, uint64_t cand, Look &L) {
+__device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, const WarpSmem &sm, Look &L) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t cand = W.fh + lane < W.fn ? sm.f[W.fb][W.fh + lane] : ~0ull;
     L.key = cand;
     L.kind = 0;
     L.k = 0;
@@ -1306,13 +1269,6 @@ __device__ __noinline__ void look_fill(const RedParams &R, const Seg &S, uint64_
     }
 }
 
-// this lane's entry of the lookahead cache: the front's entry at fh + lane
-__device__ __forceinline__ void look_refill(const RedParams &R, const Seg &S, const Work &W, const WarpSmem &sm,
-                                            Look &L) {
-    const int lane = threadIdx.x & 31;
-    look_fill(R, S, W.fh + lane < W.fn ? sm.f[W.fb][W.fh + lane] : ~0ull, L);
-}
-
 // publish the working column as column j's current version; *voff is the
 // arena offset of its header (for the pivot-table entry)
 __device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &sm, RedStats &st,
@@ -1340,127 +1296,22 @@ __device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &s
     for (int k = lane; k < nf; k += 32) __stcg((unsigned long long *)&R.arena[off + 1 + k], sm.f[W.fb][W.fh + k]);
     for (int k = lane; k < nrest; k += 32)
         __stcg((unsigned long long *)&R.arena[off + 1 + nf + k], levels ? ld_cg(rest + k) : rest[k]);
+    // the entries are visible before the pivot-table entry that names them
+    // (the caller's CAS); the column's current version is read only after
+    // the kernel, by the emission of the pairs
     __threadfence();
     __syncwarp();
-    if (lane == 0) atomicExch(&R.cur[j], (off << 24) | (unsigned long long)n);
-    __threadfence();
+    if (lane == 0) R.cur[j] = (off << 24) | (unsigned long long)n;
     __syncwarp();
     *voff = off;
     return true;
 }
 
-// The slot of the helper cache that holds pivot p, read by lane 0 under the
-// slot's key check; false if no helper has looked p up.
-__device__ bool probe_helpers(CtaShared &cs, uint64_t p, int &kind, uint64_t &c1, uint64_t &c2, uint64_t &c3,
-                              int &k, unsigned long long &ver) {
+__global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
+    extern __shared__ __align__(16) unsigned char red_smem[];
+    WarpSmem *smem = reinterpret_cast<WarpSmem *>(red_smem);
     const int lane = threadIdx.x & 31;
-    volatile HelpSlot *sl = cs.slot;
-    int found = -1;
-    for (int q = lane; q < HC_SLOTS; q += 32)
-        if (sl[q].key == p) found = q;
-    const unsigned m = __ballot_sync(0xFFFFFFFFu, found >= 0);
-    if (!m) return false;
-    const int q = __shfl_sync(0xFFFFFFFFu, found, __ffs(m) - 1);
-    int ok = 0, kd = 0, kk = 0;
-    uint64_t a1 = 0, a2 = 0, a3 = 0;
-    unsigned long long v = 0;
-    if (lane == 0) {
-        a1 = sl[q].c1;
-        a2 = sl[q].c2;
-        a3 = sl[q].c3;
-        v = sl[q].ver;
-        kd = sl[q].kind;
-        kk = sl[q].k;
-        __threadfence_block();
-        ok = sl[q].key == p && (kd == 1 || kd == 2);
-    }
-    if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) return false;
-    kind = __shfl_sync(0xFFFFFFFFu, kd, 0);
-    k = __shfl_sync(0xFFFFFFFFu, kk, 0);
-    c1 = __shfl_sync(0xFFFFFFFFu, a1, 0);
-    c2 = __shfl_sync(0xFFFFFFFFu, a2, 0);
-    c3 = __shfl_sync(0xFFFFFFFFu, a3, 0);
-    ver = __shfl_sync(0xFFFFFFFFu, v, 0);
-    return true;
-}
-
-// A warp with no column left: look up entries behind the pivot in the front
-// of a warp of this block that is still reducing, until none is.  Helpers
-// take consecutive windows of 32 front positions by their rank.  Bounded: a
-// helper stops after 2^24 rounds or when the call reports an error.
-__device__ void help(const RedParams &R, WarpSmem *smem, CtaShared &cs) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    volatile int *busy = cs.busy;
-    volatile HelpSlot *ring = cs.slot + w * HC_PER_WARP;
-    int head = 0;
-    for (long long round = 0; round < (1ll << 24); round++) {
-        // the decisions are lane 0's, so that the warp stays converged
-        int target = -1, rank = 0, fb = 0, fh = 0, fn = 0;
-        unsigned int sg = 0;
-        if (lane == 0 && !*(volatile int *)R.status) {
-            for (int t = 0; t < RED_WARPS; t++)
-                if (t != w && busy[t]) { target = t; break; }
-            if (target >= 0) {
-                for (int u = 0; u < w; u++)
-                    if (u != target && !busy[u]) rank++;
-                fb = ((volatile int *)cs.fb)[target];
-                fh = ((volatile int *)cs.fh)[target];
-                fn = ((volatile int *)cs.fn)[target];
-                sg = ((volatile unsigned int *)cs.seg)[target];
-            }
-        }
-        target = __shfl_sync(0xFFFFFFFFu, target, 0);
-        if (target < 0) return;
-        rank = __shfl_sync(0xFFFFFFFFu, rank, 0);
-        fb = __shfl_sync(0xFFFFFFFFu, fb, 0);
-        fh = __shfl_sync(0xFFFFFFFFu, fh, 0);
-        fn = __shfl_sync(0xFFFFFFFFu, fn, 0);
-        sg = __shfl_sync(0xFFFFFFFFu, sg, 0);
-        const int pos = fh + 1 + 32 * rank + lane;
-        uint64_t cand = ~0ull;
-        if ((fb == 0 || fb == 1) && fh >= 0 && pos < fn && pos < FCAP && sg < (unsigned int)R.nseg)
-            cand = ((volatile unsigned long long *)smem[target].f[fb])[pos];
-        bool want = false;
-        Seg S = R.segs[0];
-        if (cand != ~0ull && cand != 0ull) {
-            S = R.segs[sg];
-            want = face_in_image(S, key_L(cand));
-        }
-        for (int q = 0; q < HC_PER_WARP; q++)
-            if (ring[q].key == cand) want = false;  // looked up already
-        Look L;
-        L.kind = 0;
-        L.k = 0;
-        L.own = 0;
-        L.ver = 0;
-        L.c1 = L.c2 = L.c3 = ~0ull;
-        if (want) look_fill(R, S, cand, L);
-        const bool keep = want && (L.kind == 1 || L.kind == 2);
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
-        if (keep) {
-            volatile HelpSlot *h = ring + ((head + __popc(m & lt)) % HC_PER_WARP);
-            h->key = 0ull;
-            __threadfence_block();
-            h->c1 = L.c1;
-            h->c2 = L.c2;
-            h->c3 = L.c3;
-            h->ver = L.ver;
-            h->kind = L.kind;
-            h->k = L.k;
-            h->own = L.own;
-            __threadfence_block();
-            h->key = cand;
-        }
-        head = (head + __popc(m)) % HC_PER_WARP;
-        __syncwarp();
-        if (!m) __nanosleep(200);
-    }
-}
-
-// the reduction loop of one warp: returns when no column is left, or on an error (status set)
-__device__ void reduce_columns(RedParams &R, WarpSmem &sm, CtaShared &cs) {
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    WarpSmem &sm = smem[threadIdx.x >> 5];
     RedStats st;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     Work W;
@@ -1481,7 +1332,6 @@ __device__ void reduce_columns(RedParams &R, WarpSmem &sm, CtaShared &cs) {
         int64_t j = (int64_t)jj;
         const uint64_t jkey = R.colkey[j];
         const Seg S = R.segs[R.colseg[j]];
-        if (lane == 0) ((volatile unsigned int *)cs.seg)[wi] = R.colseg[j];
         // the coboundary of edge j is the front; nothing lies beyond it
         {
             int a, c[3];
@@ -1521,45 +1371,22 @@ __device__ void reduce_columns(RedParams &R, WarpSmem &sm, CtaShared &cs) {
             if (W.fh == W.fn) { if (lane == 0) set_status(R.status, CR_ERR_INTERNAL); break; }
             const uint64_t p = sm.f[W.fb][W.fh];
             const int64_t gidx = S.loff + key_L(p);
-            if (lane == 0) {  // the front, for helpers of this block
-                ((volatile int *)cs.fb)[wi] = W.fb;
-                ((volatile int *)cs.fh)[wi] = W.fh;
-                ((volatile int *)cs.fn)[wi] = W.fn;
-            }
             TMARK(t1);
-            int hkind, hk;
-            uint64_t c1, c2, c3;
-            unsigned long long hver;
             unsigned hit = __ballot_sync(0xFFFFFFFFu, look.key == p);
-            bool helped = false;
             if (!hit) {
 #ifdef CR_H1_TIMING
                 if (st.lng) st.t[6]++;
 #endif
-                if (__shfl_sync(0xFFFFFFFFu, *(volatile int *)&cs.helpers, 0) > 0) {
-#ifdef CR_H1_TIMING
-                    if (st.lng) st.t[10]++;
-#endif
-                    helped = probe_helpers(cs, p, hkind, c1, c2, c3, hk, hver);
-#ifdef CR_H1_TIMING
-                    if (st.lng && helped) st.t[11]++;
-#endif
-                }
-                if (!helped) {
-                    look_refill(R, S, W, sm, look);  // p is lane 0's entry
-                    hit = __ballot_sync(0xFFFFFFFFu, look.key == p);
-                }
+                look_refill(R, S, W, sm, look);  // p is lane 0's entry
+                hit = __ballot_sync(0xFFFFFFFFu, look.key == p);
             }
-            if (!helped) {
-                const int hl = hit ? __ffs(hit) - 1 : 0;
-                hkind = hit ? __shfl_sync(0xFFFFFFFFu, look.kind, hl) : 0;
-                c1 = __shfl_sync(0xFFFFFFFFu, look.c1, hl);
-                c2 = __shfl_sync(0xFFFFFFFFu, look.c2, hl);
-                c3 = __shfl_sync(0xFFFFFFFFu, look.c3, hl);
-                hk = __shfl_sync(0xFFFFFFFFu, look.k, hl);
-                hver = __shfl_sync(0xFFFFFFFFu, look.ver, hl);
-                if (hit && lane == hl) look.key = ~0ull;  // used once
-            }
+            const int hl = hit ? __ffs(hit) - 1 : 0;
+            const int hkind = hit ? __shfl_sync(0xFFFFFFFFu, look.kind, hl) : 0;
+            const uint64_t c1 = __shfl_sync(0xFFFFFFFFu, look.c1, hl), c2 = __shfl_sync(0xFFFFFFFFu, look.c2, hl),
+                           c3 = __shfl_sync(0xFFFFFFFFu, look.c3, hl);
+            const int hk = __shfl_sync(0xFFFFFFFFu, look.k, hl), hown = __shfl_sync(0xFFFFFFFFu, look.own, hl);
+            const unsigned long long hver = __shfl_sync(0xFFFFFFFFu, look.ver, hl);
+            if (hit && lane == hl) look.key = ~0ull;  // used once
             TADD(st, 1, t1);
             if (hkind == 1) {
                 st.app++;
@@ -1576,7 +1403,7 @@ __device__ void reduce_columns(RedParams &R, WarpSmem &sm, CtaShared &cs) {
             }
             TMARK(t9);
             const unsigned long long pe = hkind == 2 ? hver : __ldcg(&R.P[gidx]);
-            const int o = piv_owner(pe);
+            const int o = hkind == 2 ? hown : piv_owner(pe);
 #ifdef CR_H1_TIMING
             if (hkind != 2) (void)__shfl_sync(0xFFFFFFFFu, (int)pe, 0);  // make the read complete here
 #endif
@@ -1654,32 +1481,6 @@ __device__ void reduce_columns(RedParams &R, WarpSmem &sm, CtaShared &cs) {
     }
 }
 
-__global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
-    extern __shared__ __align__(16) unsigned char red_smem[];
-    WarpSmem *smem = reinterpret_cast<WarpSmem *>(red_smem);
-    CtaShared &cs = *reinterpret_cast<CtaShared *>(red_smem + RED_WARPS * sizeof(WarpSmem));
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < HC_SLOTS; i += blockDim.x) cs.slot[i].key = 0ull;
-    if (lane == 0) {
-        cs.busy[w] = 1;
-        cs.fb[w] = 0;
-        cs.fh[w] = 0;
-        cs.fn[w] = 0;
-        cs.seg[w] = 0;
-    }
-    if (threadIdx.x == 0) cs.helpers = 0;
-    __syncthreads();
-    reduce_columns(R, smem[w], cs);
-    __syncwarp();
-    if (lane == 0) {
-        ((volatile int *)cs.busy)[w] = 0;
-        atomicAdd(&cs.helpers, 1);
-    }
-    __threadfence_block();
-    __syncwarp();
-    help(R, smem, cs);
-}
-
 __global__ void k_h1_emit(const uint64_t *__restrict__ colkey, const uint32_t *__restrict__ colseg, int64_t ncols,
                           const Seg *__restrict__ segs, const unsigned long long *__restrict__ P,
                           const unsigned long long *__restrict__ cur, const uint64_t *__restrict__ arena, PairBuf pb,
@@ -1709,11 +1510,11 @@ __global__ void k_not_keys(uint64_t *k, int64_t n) {
 
 static inline unsigned nb1(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-static unsigned long long g_h1_stats[32];
+static unsigned long long g_h1_stats[24];
 static int64_t g_h1_stats_cols = 0;
 int h1_stats(int64_t *out, int n) {
     out[0] = g_h1_stats_cols;
-    for (int i = 0; i < 25 && i + 1 < n; i++) out[i + 1] = (int64_t)g_h1_stats[i];
+    for (int i = 0; i < 24 && i + 1 < n; i++) out[i + 1] = (int64_t)g_h1_stats[i];
     return CR_OK;
 }
 
@@ -1722,7 +1523,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
            int64_t *ncols_out, cudaStream_t st) {
     Img3 I{img, dd, extra, B.appmask};
     cudaMemsetAsync(B.appmask, 0, (size_t)((3 * vtot + 31) / 32) * sizeof(uint32_t), st);
-    cudaMemsetAsync(B.cnt, 0, 40 * sizeof(unsigned long long), st);  // counters and statistics (CNT_H1 .. CNT_H1 + 40)
+    cudaMemsetAsync(B.cnt, 0, 32 * sizeof(unsigned long long), st);  // counters and statistics (CNT_H1 .. CNT_H1 + 32)
     prof_begin(st, STAGE_H1_SCAN);
     CR_NOTE_LAUNCH();
     CUtensorMap tmap, tmap_dd;
@@ -1772,7 +1573,6 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     RedParams R;
     R.I = I;
     R.segs = segs;
-    R.nseg = nseg;
     R.colkey = B.colkey;
     R.colseg = B.colseg;
     R.ncols = ncols;
@@ -1813,7 +1613,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     prof_end(st, STAGE_H1_REDUCE, 12.0 * ncols);
     CR_NOTE_LAUNCH();
     k_h1_emit<<<nb1(ncols), 256, 0, st>>>(B.colkey, B.colseg, ncols, segs, B.P, B.cur, B.arena, pb, flags, status);
-    cudaMemcpyAsync(g_h1_stats, &B.cnt[8], 25 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(g_h1_stats, &B.cnt[8], 24 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     g_h1_stats_cols = ncols;
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
