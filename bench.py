@@ -258,7 +258,7 @@ def tune_candidates(W, data):
     """Knob values the autotuner tries for a workload (knobs that cannot change its launches are left out:
     a batch or a volume always fills every SM with union-find blocks; only volumes run the reduction)."""
     if W["kind"] == "batch":
-        return {"uf_compact": [1, 2, 4, 8]}
+        return {"batch_threads": [0, 1, 2, 3], "uf_compact": [1, 4]}
     if len(data.shape) == 3 and min(data.shape) > 1:
         return {"red_warps": [8, 16], "uf_compact": [1, 4]}
     return {"uf_items": [2, 4, 8, 16, 32], "uf_compact": [1, 2, 4, 8]}

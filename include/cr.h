@@ -324,6 +324,12 @@ int cr_h1_last_stats(int64_t *out, int n);
  *   CR_TUNE_UF_COMPACT the union-find rounds compact their edge list while it
  *                      holds more than this many edges per launched thread,
  *                      then mark dead edges in place; 1..64, default 1.
+ *   CR_TUNE_BATCH_THREADS  batches of 2D images (every extent >= 2): the
+ *                      union-finds run in one persistent launch, each block
+ *                      taking whole images from a queue ordered by size,
+ *                      largest first, with 256 (1), 512 (2, default) or 1024
+ *                      (3) threads per block; 0 runs them as grid-wide
+ *                      kernels over all images at once instead.
  * cr_tune_set returns CR_ERR_INVALID_ARG for an unknown knob or a value out of
  * range (the knob keeps its value); cr_tune_get writes the current value to
  * *value.  A launch sequence cached as a CUDA graph is captured afresh after a
@@ -331,7 +337,8 @@ int cr_h1_last_stats(int64_t *out, int n);
 #define CR_TUNE_UF_ITEMS 0
 #define CR_TUNE_RED_WARPS 1
 #define CR_TUNE_UF_COMPACT 2
-#define CR_TUNE_COUNT 3
+#define CR_TUNE_BATCH_THREADS 3
+#define CR_TUNE_COUNT 4
 int cr_tune_set(int knob, int value);
 int cr_tune_get(int knob, int *value);
 

@@ -2,7 +2,9 @@
 
 The knobs set launch shapes only: how many blocks the cooperative union-find
 grids use, when its rounds stop compacting their edge list, how many warps per
-SM run the 3D reduction.  Results never depend on them (the parity tests run
+SM run the 3D reduction, and the block size of the persistent launch that
+takes the images of a 2D batch from a queue (or the grid-wide kernels
+instead).  Results never depend on them (the parity tests run
 under every candidate value), so the tuner may pick any candidate by time
 alone.
 
@@ -20,15 +22,17 @@ import statistics
 from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional, Sequence, Tuple
 
-from . import (CR_TUNE_RED_WARPS, CR_TUNE_UF_COMPACT, CR_TUNE_UF_ITEMS, cr_tune_get, cr_tune_set)
+from . import (CR_TUNE_BATCH_THREADS, CR_TUNE_RED_WARPS, CR_TUNE_UF_COMPACT, CR_TUNE_UF_ITEMS, cr_tune_get,
+               cr_tune_set)
 
 KNOBS: Dict[str, int] = {
     "uf_items": CR_TUNE_UF_ITEMS,
     "red_warps": CR_TUNE_RED_WARPS,
     "uf_compact": CR_TUNE_UF_COMPACT,
+    "batch_threads": CR_TUNE_BATCH_THREADS,
 }
 
-DEFAULTS: Dict[str, int] = {"uf_items": 8, "red_warps": 16, "uf_compact": 1}
+DEFAULTS: Dict[str, int] = {"uf_items": 8, "red_warps": 16, "uf_compact": 1, "batch_threads": 2}
 
 
 def current() -> Dict[str, int]:

@@ -19,9 +19,9 @@ namespace cr {
 // ---------------------------------------------------------------------------
 // Launch knobs (host-side, per process): see cr_tune_set in include/cr.h.
 // ---------------------------------------------------------------------------
-static std::atomic<int> g_tune[CR_TUNE_COUNT] = {{8}, {16}, {1}};
+static std::atomic<int> g_tune[CR_TUNE_COUNT] = {{8}, {16}, {1}, {2}};
 static std::atomic<uint32_t> g_tune_epoch{0};
-static const int g_tune_lo[CR_TUNE_COUNT] = {1, 1, 1}, g_tune_hi[CR_TUNE_COUNT] = {64, 16, 64};
+static const int g_tune_lo[CR_TUNE_COUNT] = {1, 1, 1, 0}, g_tune_hi[CR_TUNE_COUNT] = {64, 16, 64, 3};
 int tune_value(int knob) { return g_tune[knob].load(std::memory_order_relaxed); }
 uint32_t tune_epoch() { return g_tune_epoch.load(std::memory_order_relaxed); }
 
@@ -546,9 +546,20 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     cudaMemsetAsync(cnt, 0, CR_CNT_SLOTS * sizeof(unsigned long long), st);
     if (P.any_mid) cudaMemsetAsync(extra, 0, (size_t)mask_words * 4, st);
 
+    // ---- batches of 2D images: both union-finds in one persistent launch,
+    // one image per block from a queue ordered by size (unless the launch knob
+    // selects the grid-wide kernels, or the region cannot hold a block) ----
+    bool batched_done = false;
+    if (n > 1 && P.all_2d && !P.any_mid && (P.any_h0 || P.any_dual) && tune_value(CR_TUNE_BATCH_THREADS) > 0) {
+        rc = run_batch2d(imgs, segs, P.segs, region, region_cap, pb, flags, P.any_h0, P.any_dual, &cnt[9], status,
+                         st, tune_value(CR_TUNE_BATCH_THREADS));
+        if (rc != CR_OK && rc != CR_ERR_WORKSPACE) return rc;
+        batched_done = rc == CR_OK;
+        rc = CR_OK;
+    }
     // ---- H0 and the top dimension by duality: two independent union-finds,
     // run side by side in halves of the region ----
-    if (P.any_h0 || P.any_dual) {
+    if (!batched_done && (P.any_h0 || P.any_dual)) {
         const bool both = P.any_h0 && P.any_dual && !P.serial_uf;
         const size_t half = both ? (region_cap / 2) & ~(size_t)255 : region_cap;
         // several 2D images: both stencils in one kernel over 32x32 super-tiles

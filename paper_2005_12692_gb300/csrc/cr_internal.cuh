@@ -303,6 +303,14 @@ int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
            int64_t ntiles, int64_t nstiles, UF *u0, UF *u1, const PairBuf &pb, uint32_t flags, uint32_t *extra_mask,
            int *status, cudaStream_t st);
 
+// both union-finds of a batch of 2D images in one persistent launch, one image
+// per block (cr_batch2d.cu); CR_ERR_WORKSPACE if the region cannot hold one
+// block's scratch (nothing launched).  threads_code: 1 = 256, 2 = 512,
+// 3 = 1024 threads per block.
+int run_batch2d(const float *img, const Seg *segs, const std::vector<Seg> &hsegs, char *region, size_t region_cap,
+                const PairBuf &pb, uint32_t flags, bool primal, bool dual, unsigned long long *queue, int *status,
+                cudaStream_t st, int threads_code);
+
 // middle-dimension buffers (cr_h1.cu)
 struct H1Bufs {
     uint64_t *colkey, *colkey_tmp;

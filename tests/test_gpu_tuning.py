@@ -11,9 +11,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 SETTINGS = [
-    {"uf_items": 1, "uf_compact": 1, "red_warps": 1},
-    {"uf_items": 64, "uf_compact": 64, "red_warps": 16},
-    {"uf_items": 2, "uf_compact": 8, "red_warps": 4},
+    {"uf_items": 1, "uf_compact": 1, "red_warps": 1, "batch_threads": 0},
+    {"uf_items": 64, "uf_compact": 64, "red_warps": 16, "batch_threads": 1},
+    {"uf_items": 2, "uf_compact": 8, "red_warps": 4, "batch_threads": 3},
+    {"uf_items": 8, "uf_compact": 1, "red_warps": 16, "batch_threads": 2},
 ]
 
 
