@@ -9,6 +9,7 @@
 //           Rem. 2.1): dimension 1 of a 2D image, dimension 2 of a volume;
 //   output  pairs sorted by (image, dim, birth, birth cell).
 #include "cr_internal.cuh"
+#include <algorithm>
 #include <mutex>
 #include <vector>
 #include <cmath>
@@ -168,6 +169,7 @@ constexpr int SMALL_SORT = 16384;
 static size_t fixed_bytes(const HostPlan &P) {
     size_t b = 0;
     b += al(P.segs.size() * sizeof(Seg));
+    b += al(P.segs.size() * sizeof(uint32_t));          // work order of a batch (largest image first)
     b += al(CR_CNT_SLOTS * sizeof(unsigned long long));  // status + counters
     b += al((size_t)P.vtot * sizeof(uint32_t));  // primal labels
     b += al((size_t)P.ctot * sizeof(uint32_t));  // dual labels
@@ -366,34 +368,42 @@ static int carve_uf(char *base, size_t cap, int64_t nodes, int64_t vtot, UF &u) 
 }
 
 // ---------------------------------------------------------------------------
-// CUDA graphs of the launch sequence of single 1D/2D images.  The sequence
-// depends only on the arguments below, so the second call with the same
-// arguments captures it and later calls replay it with one launch; the
-// first call runs directly (it also sets kernel attributes, which are not
-// stream operations).  Capture failures fall back to direct launches.
+// CUDA graphs of the launch sequence of single 1D/2D images and of batches
+// of them, forward and backward.  The sequence depends only on the arguments
+// below, so the second call with the same arguments captures it and later
+// calls replay it with one launch; the first call runs directly (it also sets
+// kernel attributes, which are not stream operations).  Host data the
+// sequence reads (image table, work order) is copied before the captured part.
+// Capture failures fall back to direct launches.
 // ---------------------------------------------------------------------------
+// Everything a launch sequence depends on, as words: the entry point, the
+// pointers and sizes of the call, the images' shapes (hashed), the stream and
+// device, the stage-timing state and the launch-knob epoch (launch shapes
+// were fixed at capture).
 struct GraphKey {
-    const float *img;
-    int64_t vtot;
-    int nx, ny, nz, maxdim;
-    uint32_t flags;
-    cr_pair *pairs;
-    int64_t capacity;
-    void *ws;
-    size_t ws_bytes;
-    cudaStream_t st;
-    int device;
-    bool prof_on;
-    uint32_t prof_mask;
-    bool serial;
-    uint32_t tune;  // knob epoch: launch shapes were fixed at capture
+    static constexpr int NW = 20;
+    uint64_t w[NW] = {0};
+    int n = 0;
+    void add(uint64_t v) {
+        if (n < NW) w[n++] = v;
+    }
+    void addp(const void *p) { add((uint64_t)(uintptr_t)p); }
     bool operator==(const GraphKey &o) const {
-        return img == o.img && vtot == o.vtot && nx == o.nx && ny == o.ny && nz == o.nz && maxdim == o.maxdim &&
-               flags == o.flags && pairs == o.pairs && capacity == o.capacity && ws == o.ws &&
-               ws_bytes == o.ws_bytes && st == o.st && device == o.device && prof_on == o.prof_on &&
-               prof_mask == o.prof_mask && serial == o.serial && tune == o.tune;
+        if (n != o.n) return false;
+        for (int i = 0; i < n; i++)
+            if (w[i] != o.w[i]) return false;
+        return true;
     }
 };
+static uint64_t shapes_hash(const std::vector<Seg> &segs) {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the extents
+    for (const Seg &S : segs)
+        for (int32_t e : {S.nx, S.ny, S.nz}) {
+            h ^= (uint64_t)(uint32_t)e;
+            h *= 1099511628211ull;
+        }
+    return h ^ (uint64_t)segs.size();
+}
 struct GraphEntry {
     GraphKey key;
     int state;  // 0 seen once, 1 capturing, 2 replayable, -1 not capturable
@@ -514,6 +524,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     if (!ws || ws_bytes < need_min) { g_detail = SITE_FIXED; return CR_ERR_WORKSPACE; }
     Carver C(ws, ws_bytes);
     Seg *segs = C.take<Seg>(n);
+    uint32_t *order = C.take<uint32_t>(n);
     unsigned long long *cnt = C.take<unsigned long long>(CR_CNT_SLOTS);
     uint32_t *lab = C.take<uint32_t>(P.vtot);
     uint32_t *labc = C.take<uint32_t>(P.ctot);
@@ -528,6 +539,17 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     unsigned long long *pair_count = &cnt[1];
 
     cudaMemcpyAsync(segs, P.segs.data(), n * sizeof(Seg), cudaMemcpyHostToDevice, st);
+    const bool batch2d = n > 1 && P.all_2d && !P.any_mid && (P.any_h0 || P.any_dual) &&
+                         tune_value(CR_TUNE_BATCH_THREADS) > 0;
+    std::vector<uint32_t> horder;
+    if (batch2d) {  // the work queue of the persistent launch: images by size, largest first
+        horder.resize(n);
+        for (int i = 0; i < n; i++) horder[i] = (uint32_t)i;
+        std::stable_sort(horder.begin(), horder.end(), [&](uint32_t a, uint32_t b) {
+            return (int64_t)P.segs[a].nx * P.segs[a].ny > (int64_t)P.segs[b].nx * P.segs[b].ny;
+        });
+        cudaMemcpyAsync(order, horder.data(), (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    }
 
     PairBuf pb;
     pb.pairs = pairs_out;
@@ -550,9 +572,9 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     // one image per block from a queue ordered by size (unless the launch knob
     // selects the grid-wide kernels, or the region cannot hold a block) ----
     bool batched_done = false;
-    if (n > 1 && P.all_2d && !P.any_mid && (P.any_h0 || P.any_dual) && tune_value(CR_TUNE_BATCH_THREADS) > 0) {
-        rc = run_batch2d(imgs, segs, P.segs, region, region_cap, pb, flags, P.any_h0, P.any_dual, &cnt[9], status,
-                         st, tune_value(CR_TUNE_BATCH_THREADS));
+    if (batch2d) {
+        rc = run_batch2d(imgs, segs, P.segs, order, region, region_cap, pb, flags, P.any_h0, P.any_dual, &cnt[9],
+                         status, st, tune_value(CR_TUNE_BATCH_THREADS));
         if (rc != CR_OK && rc != CR_ERR_WORKSPACE) return rc;
         batched_done = rc == CR_OK;
         rc = CR_OK;
@@ -656,10 +678,25 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
     }
     return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
     };
-    if (n == 1 && !P.any_mid && P.graphs) {
-        const Seg &S0 = P.segs[0];
-        GraphKey key{imgs, P.vtot, S0.nx, S0.ny, S0.nz, maxdim, flags, pairs_out, capacity, ws, ws_bytes, st,
-                     current_device(), prof_active(), prof_mask(), P.serial_uf, tune_epoch()};
+    if (!P.any_mid && P.graphs) {
+        GraphKey key;
+        key.add(0);  // forward
+        key.addp(imgs);
+        key.add((uint64_t)P.vtot);
+        key.add(shapes_hash(P.segs));
+        key.add((uint64_t)maxdim);
+        key.add(flags);
+        key.addp(pairs_out);
+        key.add((uint64_t)capacity);
+        key.addp(pair_offsets);
+        key.addp(ws);
+        key.add((uint64_t)ws_bytes);
+        key.addp(st);
+        key.add((uint64_t)current_device());
+        key.add(prof_active());
+        key.add(prof_mask());
+        key.add(P.serial_uf);
+        key.add(tune_epoch());
         rc = run_graphed(key, phase1, st);
     } else {
         rc = phase1(st);
@@ -828,23 +865,47 @@ static int backward_impl(const float *imgs, HostPlan &P, const cr_pair *pairs, c
     void *rtemp = C.take<char>(rt);
     if (!C.ok) { g_detail = SITE_FIXED; return CR_ERR_WORKSPACE; }
     cudaMemcpyAsync(segs, P.segs.data(), n * sizeof(Seg), cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(grad, 0, (size_t)P.vtot * sizeof(float), st);
-    if (np > 0) {
-        prof_begin(st, STAGE_BW_CONTRIB);
-        CR_NOTE_LAUNCH();
-        k_bw_contrib<<<nbk(np), 256, 0, st>>>(imgs, segs, n, pairs, np, pair_offsets, gb, gd, k0, v0);
-        int bits = 1;
-        while (((int64_t)1 << bits) <= P.vtot) bits++;
-        // the pixel sits in the high word; a stable sort on it keeps pair order inside a pixel
-        if (radix_sort_u64(k0, v0, k1, v1, nc, 32, 32 + (bits > 32 ? 32 : bits + 1), rtemp, rt, st) !=
-            cudaSuccess)
-            return CR_ERR_CUDA;
-        CR_NOTE_LAUNCH();
-        k_bw_sum<<<nbk(nc), 256, 0, st>>>(k0, v0, nc, grad);
-        prof_end(st, STAGE_BW_CONTRIB, 4.0 * P.vtot + 32.0 * np + 12.0 * nc);
-    }
-    if (cudaGetLastError() != cudaSuccess) return CR_ERR_CUDA;
+    // a fixed launch sequence for these arguments: replayed as a CUDA graph
+    auto launch_all = [&](cudaStream_t s) -> int {
+        cudaMemsetAsync(grad, 0, (size_t)P.vtot * sizeof(float), s);
+        if (np > 0) {
+            prof_begin(s, STAGE_BW_CONTRIB);
+            CR_NOTE_LAUNCH();
+            k_bw_contrib<<<nbk(np), 256, 0, s>>>(imgs, segs, n, pairs, np, pair_offsets, gb, gd, k0, v0);
+            int bits = 1;
+            while (((int64_t)1 << bits) <= P.vtot) bits++;
+            // the pixel sits in the high word; a stable sort on it keeps pair order inside a pixel
+            if (radix_sort_u64(k0, v0, k1, v1, nc, 32, 32 + (bits > 32 ? 32 : bits + 1), rtemp, rt, s) !=
+                cudaSuccess)
+                return CR_ERR_CUDA;
+            CR_NOTE_LAUNCH();
+            k_bw_sum<<<nbk(nc), 256, 0, s>>>(k0, v0, nc, grad);
+            prof_end(s, STAGE_BW_CONTRIB, 4.0 * P.vtot + 32.0 * np + 12.0 * nc);
+        }
+        return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+    };
+    GraphKey key;
+    key.add(1);  // backward
+    key.addp(imgs);
+    key.add((uint64_t)P.vtot);
+    key.add(shapes_hash(P.segs));
+    key.addp(pairs);
+    key.addp(pair_offsets);
+    key.add((uint64_t)np);
+    key.addp(gb);
+    key.addp(gd);
+    key.addp(grad);
+    key.addp(ws);
+    key.add((uint64_t)ws_bytes);
+    key.addp(st);
+    key.add((uint64_t)current_device());
+    key.add(prof_active());
+    key.add(prof_mask());
+    key.add(tune_epoch());
+    const int rc = run_graphed(key, launch_all, st);
+    if (rc) return rc;
     if (cudaStreamSynchronize(st) != cudaSuccess) return CR_ERR_CUDA;
+    prof_flush();
     return CR_OK;
 }
 

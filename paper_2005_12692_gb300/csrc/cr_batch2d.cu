@@ -14,7 +14,6 @@
 // younger end of a mutual pair hooks.  Group numbering and the order in which
 // pairs are written do not matter: the output is sorted afterwards.
 #include "cr_internal.cuh"
-#include <algorithm>
 #include <vector>
 
 namespace cr {
@@ -415,9 +414,9 @@ __global__ void __launch_bounds__(T) k_batch2d(B2Args A) {
 // image per block.  `region` holds the work order and the blocks' scratch.
 // Returns CR_ERR_WORKSPACE (nothing launched) when the region is too small
 // for one block; the caller then runs the grid-wide path.
-int run_batch2d(const float *img, const Seg *segs, const std::vector<Seg> &hsegs, char *region, size_t region_cap,
-                const PairBuf &pb, uint32_t flags, bool primal, bool dual, unsigned long long *queue, int *status,
-                cudaStream_t st, int threads_code) {
+int run_batch2d(const float *img, const Seg *segs, const std::vector<Seg> &hsegs, const uint32_t *order,
+                char *region, size_t region_cap, const PairBuf &pb, uint32_t flags, bool primal, bool dual,
+                unsigned long long *queue, int *status, cudaStream_t st, int threads_code) {
     const int n = (int)hsegs.size();
     int64_t nmax = 1;
     for (const Seg &S : hsegs) {
@@ -426,32 +425,23 @@ int run_batch2d(const float *img, const Seg *segs, const std::vector<Seg> &hsegs
     }
     const int64_t emax = 2 * nmax + 8;
     const size_t stride = b2_stride(nmax, emax);
-    const size_t order_bytes = b2_al((size_t)n * 4);
-    if (region_cap < order_bytes + stride) return CR_ERR_WORKSPACE;
+    if (region_cap < stride) return CR_ERR_WORKSPACE;
     int threads = threads_code == 1 ? 256 : (threads_code == 3 ? 1024 : 512);
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
     int64_t blocks = (int64_t)sms * (2048 / threads);
     if (blocks > n) blocks = n;
-    const int64_t fit = (int64_t)((region_cap - order_bytes) / stride);
+    const int64_t fit = (int64_t)(region_cap / stride);
     if (blocks > fit) blocks = fit;
-    // the work queue: images by size, largest first
-    std::vector<uint32_t> order(n);
-    for (int i = 0; i < n; i++) order[i] = (uint32_t)i;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
-        return (int64_t)hsegs[a].nx * hsegs[a].ny > (int64_t)hsegs[b].nx * hsegs[b].ny;
-    });
-    uint32_t *d_order = (uint32_t *)region;
-    cudaMemcpyAsync(d_order, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
     B2Args A;
     A.img = img;
     A.segs = segs;
-    A.order = d_order;
+    A.order = order;
     A.nimg = n;
     A.queue = queue;
-    A.scratch = region + order_bytes;
+    A.scratch = region;
     A.stride = stride;
     A.nmax = nmax;
     A.emax = emax;

@@ -304,12 +304,13 @@ int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
            int *status, cudaStream_t st);
 
 // both union-finds of a batch of 2D images in one persistent launch, one image
-// per block (cr_batch2d.cu); CR_ERR_WORKSPACE if the region cannot hold one
-// block's scratch (nothing launched).  threads_code: 1 = 256, 2 = 512,
-// 3 = 1024 threads per block.
-int run_batch2d(const float *img, const Seg *segs, const std::vector<Seg> &hsegs, char *region, size_t region_cap,
-                const PairBuf &pb, uint32_t flags, bool primal, bool dual, unsigned long long *queue, int *status,
-                cudaStream_t st, int threads_code);
+// per block (cr_batch2d.cu); order: device, the images by size, largest
+// first; CR_ERR_WORKSPACE if the region cannot hold one block's scratch
+// (nothing launched).  threads_code: 1 = 256, 2 = 512, 3 = 1024 threads per
+// block.
+int run_batch2d(const float *img, const Seg *segs, const std::vector<Seg> &hsegs, const uint32_t *order,
+                char *region, size_t region_cap, const PairBuf &pb, uint32_t flags, bool primal, bool dual,
+                unsigned long long *queue, int *status, cudaStream_t st, int threads_code);
 
 // middle-dimension buffers (cr_h1.cu)
 struct H1Bufs {

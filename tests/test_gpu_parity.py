@@ -205,3 +205,64 @@ def test_repeated_calls_replay_identically(cr, oracle_mod, shape):
         assert L.cr_launch_count() > before
         got = cells(cr.Pairs(out[: n.value]).numpy())
         assert got == oracle_cells(oracle_mod, src, keep_zero=False), k
+
+
+def test_batched_forward_and_backward_replay_identically(cr, oracle_mod):
+    # a batch through the C ABI with the same buffers four times: the second
+    # call of the forward and of the backward captures its launches as a graph,
+    # later calls replay it; the images change between calls, and every call
+    # must give the oracle's pairs and the FP64 oracle gradient
+    import ctypes
+    from paper_2005_12692_gb300 import synth
+    L = cr.lib()
+    shapes = [(40, 33), (64, 64), (17, 90), (90, 17), (2, 2), (128, 31)]
+    n = len(shapes)
+    offs = [0]
+    for s in shapes:
+        offs.append(offs[-1] + s[0] * s[1])
+    sh = (ctypes.c_int32 * (2 * n))(*[v for s in shapes for v in s])
+    of = (ctypes.c_int64 * (n + 1))(*offs)
+    sz = ctypes.c_size_t()
+    assert L.cr_workspace_size_batched(sh, n, 2, 1, 0, ctypes.byref(sz)) == 0
+    ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+    cap = offs[-1] + 16 * n
+    out = torch.empty((cap, 32), dtype=torch.uint8, device="cuda")
+    poffs = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    flat = torch.empty(offs[-1], dtype=torch.float32, device="cuda")
+    gb = torch.empty(cap, dtype=torch.float32, device="cuda")
+    gd = torch.empty(cap, dtype=torch.float32, device="cuda")
+    grad = torch.empty(offs[-1], dtype=torch.float32, device="cuda")
+    assert L.cr_backward_workspace_size(cap, n, ctypes.byref(sz)) == 0
+    bws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for k in range(4):
+        imgs = [synth.grf(s, 2.0, 800 + 10 * (k // 2) + i) for i, s in enumerate(shapes)]
+        flat.copy_(torch.from_numpy(np.concatenate([im.reshape(-1) for im in imgs])))
+        npairs = ctypes.c_int64(0)
+        rc = L.cr_persistence_batched(ctypes.c_void_p(flat.data_ptr()), of, sh, n, 2, 1,
+                                      ctypes.c_void_p(out.data_ptr()), cap, ctypes.c_void_p(poffs.data_ptr()),
+                                      ctypes.byref(npairs), ctypes.c_void_p(ws.data_ptr()), ws.numel(), stream, 0)
+        assert rc == 0, cr.error_string(rc)
+        p = cr.Pairs(out[: npairs.value]).numpy()
+        po = poffs.cpu().numpy()
+        for i, im in enumerate(imgs):
+            assert cells(p[po[i]:po[i + 1]]) == oracle_cells(oracle_mod, im, keep_zero=False), (k, i)
+        # gradient of the sum over H1 of lifetime^2 (the lifetimes written in place)
+        life = np.where((p["dim"] == 1) & np.isfinite(p["death"]),
+                        p["death"].astype(np.float64) - p["birth"].astype(np.float64), 0.0)
+        gb[: len(p)].copy_(torch.from_numpy((-2 * life).astype(np.float32)))
+        gd[: len(p)].copy_(torch.from_numpy((2 * life).astype(np.float32)))
+        rc = L.cr_backward_batched(ctypes.c_void_p(flat.data_ptr()), of, sh, n, 2, ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(poffs.data_ptr()), npairs.value, ctypes.c_void_p(gb.data_ptr()),
+                                   ctypes.c_void_p(gd.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                   ctypes.c_void_p(bws.data_ptr()), bws.numel(), stream)
+        assert rc == 0, cr.error_string(rc)
+        g = grad.cpu().numpy()
+        for i, im in enumerate(imgs):
+            q = oracle_mod.persistence(im)
+            ql = np.where((q["dim"] == 1) & np.isfinite(q["death"]),
+                          q["death"].astype(np.float64) - q["birth"].astype(np.float64), 0.0)
+            ref = oracle_mod.gradient(im, q, (-2 * ql).astype(np.float32), (2 * ql).astype(np.float32))
+            ref32 = ref.astype(np.float32).reshape(-1)
+            gi = g[offs[i]:offs[i + 1]].astype(np.float64)
+            assert np.all(np.abs(gi - ref32) <= np.spacing(np.abs(ref32)).astype(np.float64)), (k, i)
