@@ -288,7 +288,7 @@ int cr_persistence_noalloc(const float *img, int ndim, const int64_t *shape, int
 
 /* Diagnostics for benchmarks.  With profiling on, every stage of a call is
  * bracketed by CUDA events recorded on the caller's stream; totals per stage
- * are read with cr_profile_read (stage 0..16; name, total milliseconds,
+ * are read with cr_profile_read (stage 0..17; name, total milliseconds,
  * number of timed launches, algorithmic bytes the stage must move).  Returns
  * CR_ERR_INVALID_ARG past the last stage.  cr_profile_select restricts the
  * events to the stages whose bit is set in stage_mask (bit s = stage s;

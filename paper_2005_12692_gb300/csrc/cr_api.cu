@@ -203,7 +203,7 @@ static size_t region_bytes(const HostPlan &P, uint32_t flags, bool worst) {
         int64_t arena = worst ? 12 * P.vtot : 2 * P.vtot + (1 << 20);
         int64_t pool = worst ? 8 * P.vtot : 2 * P.vtot + (1 << 22);
         h1 = al((size_t)cols * 32) + al(radix_temp_bytes(cols)) + al((size_t)(3 * P.vtot) * 8) +
-             al((size_t)((3 * P.vtot + 31) / 32) * 4) +
+             al((size_t)P.vtot) +
              al((size_t)arena * 8) + al((size_t)pool * 8) + al((size_t)nw * 2 * ml * 8) + (1 << 20);
     }
     int64_t maxpairs = (flags & CR_KEEP_ZERO) ? P.cells / 2 + (int64_t)P.segs.size() + 16
@@ -626,7 +626,7 @@ static int pipeline(const float *imgs, HostPlan &P, int maxdim, uint32_t flags, 
         B.maxlen = ml;
         B.P_len = 3 * P.vtot;
         B.P = R.take<unsigned long long>(B.P_len);
-        B.appmask = R.take<uint32_t>((3 * P.vtot + 31) / 32);
+        B.code = R.take<uint8_t>(P.vtot);
         B.scratch = R.take<uint64_t>((size_t)nw * 2 * ml);
         B.cnt = &cnt[CNT_H1];
         if (!R.ok) { g_detail = SITE_H1_CARVE; return CR_ERR_WORKSPACE; }

@@ -9,7 +9,8 @@
 // 1. Scan: for every column edge s, t = its earliest cofacet; if s is the
 //    latest facet of t, (s, t) is an apparent pair -- a persistence pair
 //    that needs no reduction (the pairs Ripser calls apparent, inherited by
-//    the paper's adaptation of Ripser, Sec. 1).  Other columns are kept.
+//    the paper's adaptation of Ripser, Sec. 1).  The scan writes one code
+//    byte per voxel (below); a compaction lists the other columns.
 // 2. Reduction of the kept columns in the lock-free form of Morozov and
 //    Nigmetov: one warp per column, a pivot table face -> owning column,
 //    immutable published column versions in an arena.  When the pivot of
@@ -24,11 +25,23 @@
 
 namespace cr {
 
+// Code byte of voxel v, for the three edges anchored at v (v to v+x, v+y, v+z):
+//   bits 0-2  the x-edge is apparent with the face on its side: 1 +z, 2 -z,
+//             3 +y, 4 -y ({x,z} faces have type 1, {x,y} faces type 0);
+//   bits 3-4  the y-edge is apparent with its face ({y,z}, type 2): 1 +z, 2 -z;
+//   bits 5-7  the x-, y-, z-edge is a residual column (not killed in
+//             dimension 0, not apparent).
+// z-edges are never apparent, and y-edges only through their {y,z} faces: in
+// any other face an edge of equal value and smaller L is the latest facet.
+// A face is the pivot of at most one apparent pair, so whether it is one, and
+// with which edge, is read from the codes of the two edges that could pair it.
+constexpr uint8_t CODE_RX = 1u << 5, CODE_RY = 1u << 6, CODE_RZ = 1u << 7;
+
 struct Img3 {
     const float *img;
     const uint8_t *dd;       // primal stencil hooks
     const uint32_t *extra;   // edges that died in later union-find rounds (L-space bits)
-    uint32_t *appmask;       // faces that are the pivot of an apparent pair (L-space bits)
+    uint8_t *code;           // one code byte per voxel (above)
 };
 
 __device__ __forceinline__ uint32_t vord(const Img3 &I, const Seg &S, const int *c) {
@@ -131,56 +144,54 @@ __device__ __forceinline__ int seg_of_v(const Seg *segs, int n, int64_t gv) {
     return lo;
 }
 
-__global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, uint64_t *__restrict__ colkey,
-                          uint32_t *__restrict__ colseg, unsigned long long *ncol, int64_t max_cols, PairBuf pb,
-                          uint32_t flags, int *status) {
+// the side code of the apparent face t of the edge along axis a at c (see Img3)
+__device__ __forceinline__ int apparent_side(const Seg &S, int a, const int *c, uint64_t t) {
+    int fm, fc[3];
+    decode_L(S, key_L(t), fm, fc);
+    if (a == 0 && fm == 1) return fc[2] == c[2] ? 1 : 2;  // {x,z}: +z or -z
+    if (a == 0 && fm == 0) return fc[1] == c[1] ? 3 : 4;  // {x,y}: +y or -y
+    if (a == 1 && fm == 2) return fc[2] == c[2] ? 1 : 2;  // {y,z}: +z or -z
+    return 0;
+}
+
+__global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, PairBuf pb, uint32_t flags, int *status) {
     const int si = block_seg(segs, nseg);
     const Seg S = segs[si];
     int tx, ty, z0, z1;
     tile_column(S, tx, ty, z0, z1);
-    const bool inxy = S.edim == 3 && tx < S.nx && ty < S.ny;
+    if (S.edim != 3 || tx >= S.nx || ty >= S.ny) return;
     for (int zz = z0; zz < z1; zz++) {
-        const bool in = inxy;
         int c[3] = {tx, ty, zz};
-        uint64_t keeps[3];
-        int cnt = 0;
+        uint8_t code = 0;
         for (int a = 0; a < 3; a++) {
-            bool keep = false;
-            uint64_t sk = 0;
-            if (in && c[a] + 1 < ext_of(S, a) && !h0_negative(I, S, a, c)) {
-                sk = edge_key(I, S, a, c);
-                uint64_t cf[4];
-                int n = edge_cofacets(I, S, a, c, cf);
-                if (n == 0) {
-                    set_status(status, CR_ERR_INTERNAL);
-                } else {
-                    uint64_t t = cf[0];
-                    for (int i = 1; i < n; i++) t = cf[i] < t ? cf[i] : t;
-                    int fm, fc[3];
-                    decode_L(S, key_L(t), fm, fc);
-                    int ea, ec[3];
-                    uint64_t top = face_max_facet(I, S, fm, fc, ea, ec);
-                    if (top == sk) {
-                        int64_t bit = S.loff + key_L(t);
-                        atomicOr(&I.appmask[bit >> 5], 1u << (bit & 31));
-                        if (flags & CR_KEEP_ZERO)
-                            emit_pair(pb, (uint32_t)si, 1, key_value(sk), key_value(t), key_L(sk), key_L(t), 0);
-                    } else {
-                        keep = true;
-                    }
+            if (c[a] + 1 >= ext_of(S, a) || h0_negative(I, S, a, c)) continue;
+            const uint64_t sk = edge_key(I, S, a, c);
+            uint64_t cf[4];
+            const int n = edge_cofacets(I, S, a, c, cf);
+            if (n == 0) {
+                set_status(status, CR_ERR_INTERNAL);
+                continue;
+            }
+            uint64_t t = cf[0];
+            for (int i = 1; i < n; i++) t = cf[i] < t ? cf[i] : t;
+            int fm, fc[3];
+            decode_L(S, key_L(t), fm, fc);
+            int ea, ec[3];
+            const uint64_t top = face_max_facet(I, S, fm, fc, ea, ec);
+            if (top == sk) {
+                const int side = apparent_side(S, a, c, t);
+                if (side == 0 || a == 2) {
+                    set_status(status, CR_ERR_INTERNAL);  // excluded by the face order
+                    continue;
                 }
-            }
-            if (keep) keeps[cnt++] = sk;
-        }
-        int64_t i0 = block_append(cnt, ncol);
-        for (int k = 0; k < cnt; k++) {
-            if (i0 + k < max_cols) {
-                colkey[i0 + k] = ~keeps[k];  // sorted ascending below = cohomology order
-                colseg[i0 + k] = (uint32_t)si;
+                code |= (uint8_t)(a == 0 ? side : side << 3);
+                if (flags & CR_KEEP_ZERO)
+                    emit_pair(pb, (uint32_t)si, 1, key_value(sk), key_value(t), key_L(sk), key_L(t), 0);
             } else {
-                fail_ws(status, SITE_COLUMNS);
+                code |= (uint8_t)(CODE_RX << a);
             }
         }
+        I.code[S.voff + ((int64_t)zz * S.ny + ty) * S.nx + tx] = code;
     }
 }
 
@@ -191,35 +202,24 @@ __global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, uint64
 // of bytes, the tile's stencil hook codes up to one voxel past the tile in +x,
 // +y, +z (byte box; otherwise the threads stage them).  Meanwhile the threads
 // stage the words of the dimension-0 death mask covering the tile's edges.
-// Apparent pivots are collected in a shared bitmask of the tile's faces and
-// merged into the global mask once per word at the end; residual columns are
-// buffered per tile and appended with one global reservation per run.
+// Each thread then walks its column of 16 voxels in z and writes each
+// voxel's code byte; a warp writes 32 consecutive bytes.
 // ---------------------------------------------------------------------------
 constexpr int SC_DX = 48, SC_DY = TILE_Y + 1, SC_DZ = TILE_Z + 1;  // hook-code box (x0..x0+47)
 constexpr int SC_DD_BYTES = SC_DX * SC_DY * SC_DZ;
-constexpr int SC_WCAP = 192;  // residual columns buffered per warp (a plane adds at most 96)
 constexpr int SCAN_DYN_SMEM = TMA_BYTES + SC_DD_BYTES + 128;
 static_assert(TMA_BYTES % 128 == 0, "hook-code box must start on a 128-byte boundary");
 
 __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_constant__ CUtensorMap tmap,
                                                                const __grid_constant__ CUtensorMap tmap_dd,
                                                                int dd_by_tma, Img3 I, const Seg *__restrict__ segs,
-                                                               uint64_t *__restrict__ colkey,
-                                                               uint32_t *__restrict__ colseg,
-                                                               unsigned long long *ncol, int64_t max_cols,
                                                                PairBuf pb, uint32_t flags, int *status) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     unsigned char *dyn = dyn_smem + ((128u - (smem_u32(dyn_smem) & 127u)) & 127u);
     float(*box)[TMA_BY][TMA_BX] = reinterpret_cast<float(*)[TMA_BY][TMA_BX]>(dyn);
     uint8_t(*dds)[SC_DY][SC_DX] = reinterpret_cast<uint8_t(*)[SC_DY][SC_DX]>(dyn + TMA_BYTES);
     __shared__ __align__(8) uint64_t bar;
-    __shared__ uint32_t ext[3][TILE_Z][TILE_Y][2];          // death-mask words of each edge row
-    // apparent pivots, face rows from y0-1, z0-1: slots 0-2 = face types 0-2, slot 3 = type 0 marked from
-    // the -y side (so that every (slot, row) is written by one warp only, without atomics)
-    __shared__ uint32_t app[4][TILE_Z + 1][TILE_Y + 1][2];
-    __shared__ uint64_t cbuf[TILE_Y][SC_WCAP];  // residual columns, one run per warp
-    __shared__ int s_wn[TILE_Y];
-    __shared__ unsigned long long cbase;
+    __shared__ uint32_t ext[3][TILE_Z][TILE_Y][2];  // death-mask words of each edge row
     const Seg S = segs[0];
     const int nx = S.nx, ny = S.ny, nz = S.nz;
     int x0, y0, z0;
@@ -265,8 +265,6 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         ext[ax][dz][dy][0] = w0;
         ext[ax][dz][dy][1] = w1;
     }
-    for (int i = threadIdx.x; i < 4 * (TILE_Z + 1) * (TILE_Y + 1) * 2; i += TILE_X * TILE_Y)
-        (&app[0][0][0][0])[i] = 0u;
     __syncthreads();
     // the wait's outcome is made uniform so that no thread is left at a later barrier
     if (!__syncthreads_and(mbar_wait(&bar, 1ll << 24))) {
@@ -276,15 +274,15 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         }
         return;
     }
-    const int tx = threadIdx.x & (TILE_X - 1), ty = threadIdx.x / TILE_X, lane = threadIdx.x & 31;
+    const int tx = threadIdx.x & (TILE_X - 1), ty = threadIdx.x / TILE_X;
     const int x = x0 + tx, y = y0 + ty;
-    const bool inxy = x < nx && y < ny;
+    if (x >= nx || y >= ny) return;
     const int bx = tx + 4, by = ty + 1;
     const int zend = min(TILE_Z, nz - z0);
     const bool keep_zero = (flags & CR_KEEP_ZERO) != 0;
     const uint32_t lo = (uint32_t)S.loff;  // only its low bits matter for positions within mask words
     const bool hx = x + 1 < nx, hy = y + 1 < ny, my = y > 0;
-    int wn = 0;  // entries in this warp's run of residual columns (the same in every lane)
+    uint8_t *code = I.code + S.voff + (uint32_t)y * nx + (uint32_t)x;
     // Values of this thread's column roll through registers: f(x,y,z), f(x+1,y,z),
     // f(x,y+1,z) and the x- and y-edge values of planes z-1, z (and z+1 once read).
     // Out-of-image entries of the box are zero and never decide anything: each
@@ -299,95 +297,70 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         const bool hz = z + 1 < nz, mz = z > 0;
         const float fa1 = box[bz + 1][by][bx], fb1 = box[bz + 1][by][bx + 1], fc1 = box[bz + 1][by + 1][bx];
         const float exn = fmaxf(fa1, fb1), eyn = fmaxf(fa1, fc1);
-        float fsx = exc, fsy = eyc, fsz = fmaxf(fa, fa1);
-        bool colx = false, coly = false, colz = false;
-        int sx = 0, sy = 0;  // face of an apparent x- / y-edge (0: none)
-        if (inxy) {
-            const uint8_t dv = dds[zz][ty][tx];
-            // bit of this thread's x in a mask row whose first L-index is r0
+        const uint8_t dv = dds[zz][ty][tx];
+        uint32_t cd = 0;
+        // bit of this thread's x in a mask row whose first L-index is r0
 #define RB(r0) ((int)((lo + (r0)) & 31u) + tx)
-            // an edge killed in dimension 0 (a stencil hook or a later round's
-            // death) is not a column (and is never apparent, being paired with a vertex)
+        // an edge killed in dimension 0 (a stencil hook or a later round's
+        // death) is not a column (and is never apparent, being paired with a vertex)
 #define KILLED(AX, DU)                                                         \
-            (dv == (uint8_t)(2 * (AX) + 2) || (DU) == (uint8_t)(2 * (AX) + 1) || \
-             ((ext[AX][zz][ty][RB((AX) * P + rowL) >> 5] >> (RB((AX) * P + rowL) & 31)) & 1u))
-            // Candidates for the earliest cofacet of an edge sigma come in
-            // descending face-L order; the first whose parallel edge sigma' has
-            // value <= value(sigma) gives a face of value value(sigma), the least
-            // possible.  sigma is that face's latest facet unless an edge of the
-            // face with equal value has a smaller L: sigma' on the - side with
-            // equal value, or one of the two edges along the other axis b when
-            // b < a (one of them always has value(sigma)).  With no such
-            // candidate the earliest cofacet is larger than sigma and sigma is not
-            // its latest facet.  So z-edges (b < a always) are never apparent,
-            // y-edges only through their +-z faces, x-edges through any.
-            // -- x-edge (v, v+x): faces +z, -z ({x,z}, type 1), +y, -y ({x,y}, type 0)
-            if (hx) {
-                const float fs = exc;
-                const float cpy = fmaxf(fc, box[bz][by + 1][bx + 1]);
-                const float cmy = fmaxf(box[bz][by - 1][bx], box[bz][by - 1][bx + 1]);
-                int side = 0;  // 1 +z, 2 -z, 3 +y, 4 -y; the first qualifying wins
-                float fp = 0.f;
-                if (my && cmy <= fs) { side = 4; fp = cmy; }
-                if (hy && cpy <= fs) { side = 3; fp = cpy; }
-                if (mz && exp_ <= fs) { side = 2; fp = exp_; }
-                if (hz && exn <= fs) { side = 1; fp = exn; }
-                if (side != 0 && ((side & 1) || fp < fs)) {
-                    sx = side;
-                    if (keep_zero) {
-                        const int m = side <= 2 ? 1 : 0;
-                        const int dyf = side == 4 ? -1 : 0, dzf = side == 2 ? -1 : 0;
-                        const uint32_t fr = (uint32_t)m * P + rowL + (uint32_t)(dzf * (int)plane + dyf * nx);
-                        const float cv = unord32(ord32(fs));
-                        emit_pair(pb, 0u, 1, cv, cv, lv, fr + (uint32_t)tx, 0);
-                    }
-                } else {
-                    colx = !KILLED(0, dds[zz][ty][tx + 1]);
+        (dv == (uint8_t)(2 * (AX) + 2) || (DU) == (uint8_t)(2 * (AX) + 1) || \
+         ((ext[AX][zz][ty][RB((AX) * P + rowL) >> 5] >> (RB((AX) * P + rowL) & 31)) & 1u))
+        // Candidates for the earliest cofacet of an edge sigma come in
+        // descending face-L order; the first whose parallel edge sigma' has
+        // value <= value(sigma) gives a face of value value(sigma), the least
+        // possible.  sigma is that face's latest facet unless an edge of the
+        // face with equal value has a smaller L: sigma' on the - side with
+        // equal value, or one of the two edges along the other axis b when
+        // b < a (one of them always has value(sigma)).  With no such
+        // candidate the earliest cofacet is larger than sigma and sigma is not
+        // its latest facet.  So z-edges (b < a always) are never apparent,
+        // y-edges only through their +-z faces, x-edges through any.
+        // -- x-edge (v, v+x): faces +z, -z ({x,z}, type 1), +y, -y ({x,y}, type 0)
+        if (hx) {
+            const float fs = exc;
+            const float cpy = fmaxf(fc, box[bz][by + 1][bx + 1]);
+            const float cmy = fmaxf(box[bz][by - 1][bx], box[bz][by - 1][bx + 1]);
+            uint32_t side = 0;  // 1 +z, 2 -z, 3 +y, 4 -y; the first qualifying wins
+            float fp = 0.f;
+            if (my && cmy <= fs) { side = 4; fp = cmy; }
+            if (hy && cpy <= fs) { side = 3; fp = cpy; }
+            if (mz && exp_ <= fs) { side = 2; fp = exp_; }
+            if (hz && exn <= fs) { side = 1; fp = exn; }
+            if (side != 0 && ((side & 1) || fp < fs)) {
+                cd = side;
+                if (keep_zero) {
+                    const int m = side <= 2 ? 1 : 0;
+                    const int dyf = side == 4 ? -1 : 0, dzf = side == 2 ? -1 : 0;
+                    const uint32_t fr = (uint32_t)m * P + rowL + (uint32_t)(dzf * (int)plane + dyf * nx);
+                    const float cv = unord32(ord32(fs));
+                    emit_pair(pb, 0u, 1, cv, cv, lv, fr + (uint32_t)tx, 0);
                 }
+            } else if (!KILLED(0, dds[zz][ty][tx + 1])) {
+                cd = CODE_RX;
             }
-            // -- y-edge (v, v+y): only the {y,z} faces (+z, -z, type 2) can make it apparent
-            if (hy) {
-                const float fs = eyc;
-                const bool pz = hz && eyn <= fs;
-                const bool qz = !pz && mz && eyp < fs;
-                if (pz || qz) {
-                    sy = pz ? 1 : 2;
-                    if (keep_zero) {
-                        const uint32_t fr = 2u * P + rowL - (qz ? plane : 0u);
-                        const float cv = unord32(ord32(fs));
-                        emit_pair(pb, 0u, 1, cv, cv, lv + P, fr + (uint32_t)tx, 0);
-                    }
-                } else {
-                    coly = !KILLED(1, dds[zz][ty + 1][tx]);
+        }
+        // -- y-edge (v, v+y): only the {y,z} faces (+z, -z, type 2) can make it apparent
+        if (hy) {
+            const float fs = eyc;
+            const bool pz = hz && eyn <= fs;
+            const bool qz = !pz && mz && eyp < fs;
+            if (pz || qz) {
+                cd |= (pz ? 1u : 2u) << 3;
+                if (keep_zero) {
+                    const uint32_t fr = 2u * P + rowL - (qz ? plane : 0u);
+                    const float cv = unord32(ord32(fs));
+                    emit_pair(pb, 0u, 1, cv, cv, lv + P, fr + (uint32_t)tx, 0);
                 }
+            } else if (!KILLED(1, dds[zz][ty + 1][tx])) {
+                cd |= CODE_RY;
             }
-            // -- z-edge (v, v+z): a column whenever it survives dimension 0
-            if (hz) colz = !KILLED(2, dds[zz + 1][ty][tx]);
+        }
+        // -- z-edge (v, v+z): a column whenever it survives dimension 0
+        if (hz && !KILLED(2, dds[zz + 1][ty][tx])) cd |= CODE_RZ;
 #undef KILLED
 #undef RB
-        }
-        // apparent pivots: a warp's lanes are 32 consecutive x of one row, so
-        // each (face type, anchor row) gives one ballot, OR-ed into the tile
-        // mask (two words: the row need not start on a word boundary)
-        {
-            const unsigned m1 = __ballot_sync(0xFFFFFFFFu, sx == 1), m2 = __ballot_sync(0xFFFFFFFFu, sx == 2);
-            const unsigned m3 = __ballot_sync(0xFFFFFFFFu, sx == 3), m4 = __ballot_sync(0xFFFFFFFFu, sx == 4);
-            const unsigned m5 = __ballot_sync(0xFFFFFFFFu, sy == 1), m6 = __ballot_sync(0xFFFFFFFFu, sy == 2);
-            if (lane < 6) {
-                // lane k: x-edge +z, -z (type 1), +y, -y (type 0, slot 3); y-edge +z, -z (type 2)
-                const unsigned msk = lane == 0 ? m1 : lane == 1 ? m2 : lane == 2 ? m3 : lane == 3 ? m4 : lane == 4 ? m5 : m6;
-                if (msk) {
-                    const int m = lane < 2 ? 1 : (lane < 4 ? 0 : 2);
-                    const int slot = lane == 3 ? 3 : m;
-                    const int dzf = (lane == 1 || lane == 5) ? -1 : 0, dyf = lane == 3 ? -1 : 0;
-                    const uint32_t fr = (uint32_t)m * P + rowL + (uint32_t)(dzf * (int)plane + dyf * nx);
-                    const int off = (int)((lo + fr) & 31u);
-                    uint32_t *w = &app[slot][zz + 1 + dzf][ty + 1 + dyf][0];
-                    w[0] |= msk << off;
-                    if (off) w[1] |= msk >> (32 - off);
-                }
-            }
-        }
+        code[(size_t)z * plane] = (uint8_t)cd;
         fa = fa1;
         fb = fb1;
         fc = fc1;
@@ -395,72 +368,42 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         exc = exn;
         eyp = eyc;
         eyc = eyn;
-        // residual columns: appended to the warp's run in shared memory (no block
-        // barrier per plane); a run that could overflow goes out with its own
-        // global reservation, the rest with one reservation per tile
-        const int cnt = (int)colx + (int)coly + (int)colz;
-        const unsigned b0 = __ballot_sync(0xFFFFFFFFu, cnt & 1), b1 = __ballot_sync(0xFFFFFFFFu, cnt & 2);
-        const int total = __popc(b0) + 2 * __popc(b1);
-        if (total) {
-            if (wn + total > SC_WCAP) {
-                __syncwarp();
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(ncol, (unsigned long long)wn);
-                base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                if ((int64_t)base + wn > max_cols) {
-                    if (lane == 0) fail_ws(status, SITE_COLUMNS);
-                } else {
-                    for (int i = lane; i < wn; i += 32) {
-                        colkey[base + i] = cbuf[ty][i];
-                        colseg[base + i] = 0u;
-                    }
-                }
-                __syncwarp();
-                wn = 0;
-            }
-            const unsigned lt = (1u << lane) - 1u;
-            int j = wn + __popc(b0 & lt) + 2 * __popc(b1 & lt);
-            if (colx) cbuf[ty][j++] = ~make_key(ord32(fsx), lv);
-            if (coly) cbuf[ty][j++] = ~make_key(ord32(fsy), lv + P);
-            if (colz) cbuf[ty][j++] = ~make_key(ord32(fsz), lv + 2u * P);
-            wn += total;
-        }
     }
-    // the tile's remaining runs: one global reservation
-    if (lane == 0) s_wn[ty] = wn;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < TILE_Y; w++) t += s_wn[w];
-        cbase = t ? atomicAdd(ncol, (unsigned long long)t) : 0ull;
-    }
-    __syncthreads();
-    {
-        int before = 0, t = 0;
-        for (int w = 0; w < TILE_Y; w++) {
-            if (w < ty) before += s_wn[w];
-            t += s_wn[w];
-        }
-        const int64_t b0g = (int64_t)cbase;
-        if (b0g + t > max_cols) {
-            if (threadIdx.x == 0 && t) fail_ws(status, SITE_COLUMNS);
-        } else {
-            for (int i = lane; i < wn; i += 32) {
-                colkey[b0g + before + i] = cbuf[ty][i];
-                colseg[b0g + before + i] = 0u;
+}
+
+// The residual columns listed from the code bytes: each with its edge's key
+// (stored complemented, so that the ascending sort gives cohomology order)
+// and its image.  Thread per voxel, one reservation per block.
+__global__ void k_h1_columns(const float *__restrict__ img, const uint8_t *__restrict__ code,
+                             const Seg *__restrict__ segs, int nseg, int64_t vtot, uint64_t *__restrict__ colkey,
+                             uint32_t *__restrict__ colseg, unsigned long long *ncol, int64_t max_cols, int *status) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < vtot; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gv = base + threadIdx.x;
+        uint32_t cd = gv < vtot ? (uint32_t)code[gv] & 0xE0u : 0u;
+        uint64_t keys[3];
+        int cnt = 0, si = 0;
+        if (cd) {
+            si = seg_of_v(segs, nseg, gv);
+            const Seg S = segs[si];
+            const uint32_t lv = (uint32_t)(gv - S.voff);
+            const uint32_t plane = (uint32_t)S.nx * (uint32_t)S.ny, P = plane * (uint32_t)S.nz;
+            const uint32_t ov = ord32(img[gv]);
+            const uint32_t du[3] = {1u, (uint32_t)S.nx, plane};
+            for (int a = 0; a < 3; a++) {
+                if (!((cd >> (5 + a)) & 1u)) continue;
+                const uint32_t ou = ord32(img[gv + du[a]]);
+                keys[cnt++] = ~make_key(ov > ou ? ov : ou, lv + (uint32_t)a * P);
             }
         }
-    }
-    __syncthreads();
-    // merge the tile's apparent pivots into the global mask, one atomic per nonzero word
-    for (int i = threadIdx.x; i < 3 * (TILE_Z + 1) * (TILE_Y + 1) * 2; i += TILE_X * TILE_Y) {
-        const int half = i & 1, r = i >> 1;
-        const int dy = r % (TILE_Y + 1), r2 = r / (TILE_Y + 1);
-        const int dz = r2 % (TILE_Z + 1), m = r2 / (TILE_Z + 1);
-        const uint32_t w = app[m][dz][dy][half] | (m == 0 ? app[3][dz][dy][half] : 0u);
-        if (!w) continue;
-        const int64_t r0 = S.loff + (int64_t)m * P + (int64_t)(z0 - 1 + dz) * plane + (int64_t)(y0 - 1 + dy) * nx + x0;
-        atomicOr(&I.appmask[(r0 >> 5) + half], w);
+        const int64_t i0 = block_append(cnt, ncol);
+        for (int k = 0; k < cnt; k++) {
+            if (i0 + k < max_cols) {
+                colkey[i0 + k] = keys[k];
+                colseg[i0 + k] = (uint32_t)si;
+            } else {
+                fail_ws(status, SITE_COLUMNS);
+            }
+        }
     }
 }
 
@@ -1215,34 +1158,28 @@ __device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, con
     const uint32_t fl = key_L(cand);
     int fm, c[3];
     decode_L(S, fl, fm, c);
-    const int a = fm == 2 ? 1 : 0, b = fm == 0 ? 1 : 2;
     const int64_t bit = S.loff + fl;
+    // the two edges that could pair this face as apparent (the code bytes of
+    // their voxels): {x,z} (type 1) the x-edges at c (+z) and c+z (-z); {x,y}
+    // (type 0) the x-edges at c (+y) and c+y (-y); {y,z} (type 2) the y-edges
+    // at c (+z) and c+z (-z)
     const int64_t v0 = S.voff + ((int64_t)c[2] * S.ny + c[1]) * S.nx + c[0];
-    const int64_t da = a == 0 ? 1 : (int64_t)S.nx, db = b == 1 ? (int64_t)S.nx : (int64_t)S.nx * S.ny;
-    const uint32_t am = __ldcg(&R.I.appmask[bit >> 5]);
+    const int64_t v1 = v0 + (fm == 0 ? (int64_t)S.nx : (int64_t)S.nx * S.ny);
+    const uint32_t k0 = R.I.code[v0], k1 = R.I.code[v1];
     const unsigned long long pe = __ldcg(&R.P[bit]);
-    const float g0 = R.I.img[v0], g1 = R.I.img[v0 + da], g2 = R.I.img[v0 + db], g3 = R.I.img[v0 + da + db];
-    if ((am >> (bit & 31)) & 1u) {
-        // the face's latest facet: the apparent edge
-        const uint32_t u0 = ord32(g0), u1 = ord32(g1), u2 = ord32(g2), u3 = ord32(g3);
-        int ea = a, ec[3] = {c[0], c[1], c[2]};
-        uint64_t best = make_key(u0 > u1 ? u0 : u1, cube_L(S, a, c[0], c[1], c[2]));
-        {
-            int d[3] = {c[0], c[1], c[2]};
-            d[b] += 1;
-            const uint64_t k1 = make_key(u2 > u3 ? u2 : u3, cube_L(S, a, d[0], d[1], d[2]));
-            if (k1 > best) { best = k1; ea = a; ec[0] = d[0]; ec[1] = d[1]; ec[2] = d[2]; }
-        }
-        {
-            const uint64_t k2 = make_key(u0 > u2 ? u0 : u2, cube_L(S, b, c[0], c[1], c[2]));
-            if (k2 > best) { best = k2; ea = b; ec[0] = c[0]; ec[1] = c[1]; ec[2] = c[2]; }
-        }
-        {
-            int d[3] = {c[0], c[1], c[2]};
-            d[a] += 1;
-            const uint64_t k3 = make_key(u1 > u3 ? u1 : u3, cube_L(S, b, d[0], d[1], d[2]));
-            if (k3 > best) { best = k3; ea = b; ec[0] = d[0]; ec[1] = d[1]; ec[2] = d[2]; }
-        }
+    int ea = -1, ec[3] = {c[0], c[1], c[2]};
+    if (fm == 2) {
+        if (((k0 >> 3) & 3u) == 1u) ea = 1;
+        else if (((k1 >> 3) & 3u) == 2u) { ea = 1; ec[2] += 1; }
+    } else if (fm == 1) {
+        if ((k0 & 7u) == 1u) ea = 0;
+        else if ((k1 & 7u) == 2u) { ea = 0; ec[2] += 1; }
+    } else {
+        if ((k0 & 7u) == 3u) ea = 0;
+        else if ((k1 & 7u) == 4u) { ea = 0; ec[1] += 1; }
+    }
+    if (ea >= 0) {
+        // the apparent edge's column: its cofacets, the face itself first
         uint64_t cf[4];
         const int n = edge_cofacets(R.I, S, ea, ec, cf);
         sort4(cf, n);
@@ -1521,8 +1458,7 @@ int h1_stats(int64_t *out, int n) {
 int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, const Seg *hseg, int nseg,
            int64_t vtot, int64_t ntiles, H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status,
            int64_t *ncols_out, cudaStream_t st) {
-    Img3 I{img, dd, extra, B.appmask};
-    cudaMemsetAsync(B.appmask, 0, (size_t)((3 * vtot + 31) / 32) * sizeof(uint32_t), st);
+    Img3 I{img, dd, extra, B.code};
     cudaMemsetAsync(B.cnt, 0, 32 * sizeof(unsigned long long), st);  // counters and statistics (CNT_H1 .. CNT_H1 + 32)
     prof_begin(st, STAGE_H1_SCAN);
     CR_NOTE_LAUNCH();
@@ -1537,16 +1473,27 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
         }
         const int dd_tma = make_u8_map(&tmap_dd, dd, *hseg, SC_DX, SC_DY, SC_DZ) ? 1 : 0;
         if (!dd_tma) memset(&tmap_dd, 0, sizeof(tmap_dd));
-        k_h1_scan_tma<<<(unsigned)ntiles, TILE_X * TILE_Y, SCAN_DYN_SMEM, st>>>(
-            tmap, tmap_dd, dd_tma, I, segs, B.colkey, B.colseg, &B.cnt[0], B.max_cols, pb, flags, status);
+        k_h1_scan_tma<<<(unsigned)ntiles, TILE_X * TILE_Y, SCAN_DYN_SMEM, st>>>(tmap, tmap_dd, dd_tma, I, segs,
+                                                                               pb, flags, status);
     } else {
-        k_h1_scan<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(I, segs, nseg, B.colkey, B.colseg, &B.cnt[0],
-                                                                B.max_cols, pb, flags, status);
+        k_h1_scan<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(I, segs, nseg, pb, flags, status);
     }
-    // algorithmic bytes: value and hook code read (5 B), death-mask bits read and
-    // apparent-pivot bits written (3/8 B each) per voxel; 12 B per residual
-    // column written (added below once the count is known)
-    prof_end(st, STAGE_H1_SCAN, 5.75 * vtot);
+    // algorithmic bytes: value and hook code read (5 B), death-mask bits read
+    // (3/8 B) and the code byte written (1 B) per voxel
+    prof_end(st, STAGE_H1_SCAN, 6.375 * vtot);
+    // the residual columns from the codes (1 B read per voxel; 12 B written per
+    // column and its two values read, added below once the count is known)
+    prof_begin(st, STAGE_H1_COLUMNS);
+    CR_NOTE_LAUNCH();
+    {
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+        const int64_t want = (vtot + 255) / 256, cap = (int64_t)sms * 16;
+        k_h1_columns<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(img, B.code, segs, nseg, vtot, B.colkey,
+                                                                           B.colseg, &B.cnt[0], B.max_cols, status);
+    }
+    prof_end(st, STAGE_H1_COLUMNS, 1.0 * vtot);
     unsigned long long hc = 0;
     int hstatus = 0;
     cudaMemcpyAsync(&hc, &B.cnt[0], sizeof(hc), cudaMemcpyDeviceToHost, st);
@@ -1555,7 +1502,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     // an earlier stage failed (its status is returned by the caller): no reduction on its output
     if (hstatus) return CR_OK;
     int64_t ncols = (int64_t)hc;
-    prof_add_bytes(STAGE_H1_SCAN, 12.0 * (double)(ncols < B.max_cols ? ncols : B.max_cols));
+    prof_add_bytes(STAGE_H1_COLUMNS, 20.0 * (double)(ncols < B.max_cols ? ncols : B.max_cols));
     *ncols_out = ncols;
     if (ncols > B.max_cols) { set_host_detail(SITE_COLUMNS); return CR_ERR_WORKSPACE; }
     if (ncols == 0) return CR_OK;

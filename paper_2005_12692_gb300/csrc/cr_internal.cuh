@@ -327,7 +327,7 @@ struct H1Bufs {
     uint64_t *scratch;        // 2 * maxlen per warp
     int64_t nwarps;
     int maxlen;
-    uint32_t *appmask;        // apparent pivot faces (3 * vtot bits)
+    uint8_t *code;            // one code byte per voxel: apparent and residual edges (cr_h1.cu)
     uint64_t *pool;           // grown column buffers for columns longer than maxlen
     int64_t pool_cap;
     unsigned long long *cnt;  // [0] columns, [1] arena top, [2] work counter, [3] pool top
@@ -355,7 +355,7 @@ size_t scan_temp_bytes(int64_t n);
 enum Stage {
     STAGE_H0_STENCIL, STAGE_JUMP, STAGE_ROOTS, STAGE_RELABEL, STAGE_H0_CROSS, STAGE_UF_ROUND,
     STAGE_DUAL_STENCIL, STAGE_DUAL_CROSS, STAGE_H1_SCAN, STAGE_H1_SORT, STAGE_H1_REDUCE, STAGE_H1_EMIT,
-    STAGE_OUT_SORT, STAGE_BW_CONTRIB, STAGE_BW_SORT, STAGE_BW_SUM, STAGE_IMAGES, STAGE_COUNT
+    STAGE_OUT_SORT, STAGE_BW_CONTRIB, STAGE_BW_SORT, STAGE_BW_SUM, STAGE_IMAGES, STAGE_H1_COLUMNS, STAGE_COUNT
 };
 extern std::atomic<long long> g_launch_count;
 void prof_begin(cudaStream_t st, int stage);

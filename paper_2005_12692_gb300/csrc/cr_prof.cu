@@ -13,7 +13,7 @@ std::atomic<long long> g_launch_count{0};
 static const char *kStageNames[STAGE_COUNT] = {
     "h0_stencil", "jump",        "roots",      "relabel",    "h0_cross",   "uf_round",
     "dual_stencil", "dual_cross", "h1_scan",   "h1_sort",    "h1_reduce",  "h1_emit",
-    "out_sort",   "bw_contrib",  "bw_sort",    "bw_sum",     "images"};
+    "out_sort",   "bw_contrib",  "bw_sort",    "bw_sum",     "images",     "h1_columns"};
 
 struct Pending {
     int stage;
