@@ -159,11 +159,11 @@ __global__ void k_h1_scan(Img3 I, const Seg *__restrict__ segs, int nseg, PairBu
     const Seg S = segs[si];
     int tx, ty, z0, z1;
     tile_column(S, tx, ty, z0, z1);
-    if (S.edim != 3 || tx >= S.nx || ty >= S.ny) return;
+    if (tx >= S.nx || ty >= S.ny) return;
     for (int zz = z0; zz < z1; zz++) {
         int c[3] = {tx, ty, zz};
-        uint8_t code = 0;
-        for (int a = 0; a < 3; a++) {
+        uint8_t code = 0;  // images of a batch that are not volumes have no middle dimension: code 0
+        for (int a = 0; a < 3 && S.edim == 3; a++) {
             if (c[a] + 1 >= ext_of(S, a) || h0_negative(I, S, a, c)) continue;
             const uint64_t sk = edge_key(I, S, a, c);
             uint64_t cf[4];
@@ -373,17 +373,45 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
 
 // The residual columns listed from the code bytes: each with its edge's key
 // (stored complemented, so that the ascending sort gives cohomology order)
-// and its image.  Thread per voxel, one reservation per block.
+// and its image.  A thread reads 16 code bytes at once (the code array starts
+// on a 256-byte boundary); one reservation per warp.
 __global__ void k_h1_columns(const float *__restrict__ img, const uint8_t *__restrict__ code,
                              const Seg *__restrict__ segs, int nseg, int64_t vtot, uint64_t *__restrict__ colkey,
                              uint32_t *__restrict__ colseg, unsigned long long *ncol, int64_t max_cols, int *status) {
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < vtot; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t gv = base + threadIdx.x;
-        uint32_t cd = gv < vtot ? (uint32_t)code[gv] & 0xE0u : 0u;
-        uint64_t keys[3];
-        int cnt = 0, si = 0;
-        if (cd) {
-            si = seg_of_v(segs, nseg, gv);
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunk = (vtot + 15) / 16;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nchunk; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ch = base + threadIdx.x;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (ch < nchunk) {
+            if (ch * 16 + 16 <= vtot) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(code) + ch);
+                w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
+            } else {
+                for (int64_t v = ch * 16; v < vtot; v++) w[(v - ch * 16) >> 2] |= (uint32_t)code[v] << (8 * (v & 3));
+            }
+        }
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) cnt += __popc(w[k] & 0xE0E0E0E0u);
+        // warp reservation
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        unsigned long long wbase = 0;
+        if (lane == 31 && total) wbase = atomicAdd(ncol, (unsigned long long)total);
+        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
+        if (!cnt) continue;
+        int64_t i = (int64_t)wbase + (incl - cnt);
+        for (int b = 0; b < 16; b++) {
+            const uint32_t cd = (w[b >> 2] >> (8 * (b & 3))) & 0xE0u;
+            if (!cd) continue;
+            const int64_t gv = ch * 16 + b;
+            const int si = seg_of_v(segs, nseg, gv);
             const Seg S = segs[si];
             const uint32_t lv = (uint32_t)(gv - S.voff);
             const uint32_t plane = (uint32_t)S.nx * (uint32_t)S.ny, P = plane * (uint32_t)S.nz;
@@ -392,16 +420,13 @@ __global__ void k_h1_columns(const float *__restrict__ img, const uint8_t *__res
             for (int a = 0; a < 3; a++) {
                 if (!((cd >> (5 + a)) & 1u)) continue;
                 const uint32_t ou = ord32(img[gv + du[a]]);
-                keys[cnt++] = ~make_key(ov > ou ? ov : ou, lv + (uint32_t)a * P);
-            }
-        }
-        const int64_t i0 = block_append(cnt, ncol);
-        for (int k = 0; k < cnt; k++) {
-            if (i0 + k < max_cols) {
-                colkey[i0 + k] = keys[k];
-                colseg[i0 + k] = (uint32_t)si;
-            } else {
-                fail_ws(status, SITE_COLUMNS);
+                if (i < max_cols) {
+                    colkey[i] = ~make_key(ov > ou ? ov : ou, lv + (uint32_t)a * P);
+                    colseg[i] = (uint32_t)si;
+                } else {
+                    fail_ws(status, SITE_COLUMNS);
+                }
+                i++;
             }
         }
     }
@@ -1489,7 +1514,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
         int sms = 0, dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
-        const int64_t want = (vtot + 255) / 256, cap = (int64_t)sms * 16;
+        const int64_t want = ((vtot + 15) / 16 + 255) / 256, cap = (int64_t)sms * 8;
         k_h1_columns<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(img, B.code, segs, nseg, vtot, B.colkey,
                                                                            B.colseg, &B.cnt[0], B.max_cols, status);
     }
