@@ -373,28 +373,25 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
 
 // The residual columns listed from the code bytes: each with its edge's key
 // (stored complemented, so that the ascending sort gives cohomology order)
-// and its image.  A thread reads 16 code bytes at once (the code array starts
+// and its image.  A thread reads 4 code bytes at once (the code array starts
 // on a 256-byte boundary); one reservation per warp.
 __global__ void k_h1_columns(const float *__restrict__ img, const uint8_t *__restrict__ code,
                              const Seg *__restrict__ segs, int nseg, int64_t vtot, uint64_t *__restrict__ colkey,
                              uint32_t *__restrict__ colseg, unsigned long long *ncol, int64_t max_cols, int *status) {
     const int lane = threadIdx.x & 31;
-    const int64_t nchunk = (vtot + 15) / 16;
+    const int64_t nchunk = (vtot + 3) / 4;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nchunk; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ch = base + threadIdx.x;
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        uint32_t w = 0u;
         if (ch < nchunk) {
-            if (ch * 16 + 16 <= vtot) {
-                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(code) + ch);
-                w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
+            if (ch * 4 + 4 <= vtot) {
+                w = __ldg(reinterpret_cast<const uint32_t *>(code) + ch);
             } else {
-                for (int64_t v = ch * 16; v < vtot; v++) w[(v - ch * 16) >> 2] |= (uint32_t)code[v] << (8 * (v & 3));
+                for (int64_t v = ch * 4; v < vtot; v++) w |= (uint32_t)code[v] << (8 * (v & 3));
             }
         }
-        int cnt = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) cnt += __popc(w[k] & 0xE0E0E0E0u);
-        // warp reservation
+        w &= 0xE0E0E0E0u;  // the residual bits
+        const int cnt = __popc(w);
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -402,27 +399,35 @@ __global__ void k_h1_columns(const float *__restrict__ img, const uint8_t *__res
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (!total) continue;  // the whole warp has none
         unsigned long long wbase = 0;
-        if (lane == 31 && total) wbase = atomicAdd(ncol, (unsigned long long)total);
+        if (lane == 31) wbase = atomicAdd(ncol, (unsigned long long)total);
         wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
         if (!cnt) continue;
         int64_t i = (int64_t)wbase + (incl - cnt);
-        for (int b = 0; b < 16; b++) {
-            const uint32_t cd = (w[b >> 2] >> (8 * (b & 3))) & 0xE0u;
+        const int si = seg_of_v(segs, nseg, ch * 4);  // a chunk of four voxels can straddle two images
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const uint32_t cd = (w >> (8 * b)) & 0xE0u;
             if (!cd) continue;
-            const int64_t gv = ch * 16 + b;
-            const int si = seg_of_v(segs, nseg, gv);
-            const Seg S = segs[si];
+            const int64_t gv = ch * 4 + b;
+            const int sj = (si + 1 < nseg && gv >= segs[si + 1].voff) ? seg_of_v(segs, nseg, gv) : si;
+            const Seg S = segs[sj];
             const uint32_t lv = (uint32_t)(gv - S.voff);
             const uint32_t plane = (uint32_t)S.nx * (uint32_t)S.ny, P = plane * (uint32_t)S.nz;
-            const uint32_t ov = ord32(img[gv]);
-            const uint32_t du[3] = {1u, (uint32_t)S.nx, plane};
+            const float f0 = img[gv];
+            const float fx = (cd & CODE_RX) ? img[gv + 1] : 0.f;
+            const float fy = (cd & CODE_RY) ? img[gv + S.nx] : 0.f;
+            const float fz = (cd & CODE_RZ) ? img[gv + plane] : 0.f;
+            const uint32_t ov = ord32(f0);
+            const float fu[3] = {fx, fy, fz};
+#pragma unroll
             for (int a = 0; a < 3; a++) {
                 if (!((cd >> (5 + a)) & 1u)) continue;
-                const uint32_t ou = ord32(img[gv + du[a]]);
+                const uint32_t ou = ord32(fu[a]);
                 if (i < max_cols) {
                     colkey[i] = ~make_key(ov > ou ? ov : ou, lv + (uint32_t)a * P);
-                    colseg[i] = (uint32_t)si;
+                    colseg[i] = (uint32_t)sj;
                 } else {
                     fail_ws(status, SITE_COLUMNS);
                 }
@@ -479,10 +484,24 @@ __device__ __forceinline__ unsigned long long piv_off(unsigned long long e) { re
 // or a header and 31 entries): the arena keeps this much slack
 constexpr int ARENA_SLACK = 32;
 
-constexpr int DMAX = 256;      // entries of a published column staged in shared memory
-constexpr int FCAP = 256;      // capacity of the front
-constexpr int ICAP = 1024;     // capacity of the inbox
-constexpr int TT = 256;        // merged positions per tile of a merge of sorted runs
+// sizes of a warp's working column and its residency (compile-time; the
+// defaults were chosen by measurement, see the design notes)
+#ifndef CR_RED_DMAX
+#define CR_RED_DMAX 256
+#endif
+#ifndef CR_RED_ICAP
+#define CR_RED_ICAP 1024
+#endif
+#ifndef CR_RED_TT
+#define CR_RED_TT 256
+#endif
+#ifndef CR_RED_BLOCKS_PER_SM
+#define CR_RED_BLOCKS_PER_SM 2
+#endif
+constexpr int DMAX = CR_RED_DMAX;  // entries of a published column staged in shared memory
+constexpr int FCAP = 256;          // capacity of the front
+constexpr int ICAP = CR_RED_ICAP;  // capacity of the inbox
+constexpr int TT = CR_RED_TT;      // merged positions per tile of a merge of sorted runs
 constexpr int RED_WARPS = 4;
 
 struct WarpSmem {
@@ -1269,7 +1288,7 @@ __device__ bool publish_work(const RedParams &R, int64_t j, Work &W, WarpSmem &s
     return true;
 }
 
-__global__ void __launch_bounds__(RED_WARPS * 32, 2) k_h1_reduce(RedParams R) {
+__global__ void __launch_bounds__(RED_WARPS * 32, CR_RED_BLOCKS_PER_SM) k_h1_reduce(RedParams R) {
     extern __shared__ __align__(16) unsigned char red_smem[];
     WarpSmem *smem = reinterpret_cast<WarpSmem *>(red_smem);
     const int lane = threadIdx.x & 31;
@@ -1514,7 +1533,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
         int sms = 0, dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
-        const int64_t want = ((vtot + 15) / 16 + 255) / 256, cap = (int64_t)sms * 8;
+        const int64_t want = ((vtot + 3) / 4 + 255) / 256, cap = (int64_t)sms * 64;
         k_h1_columns<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(img, B.code, segs, nseg, vtot, B.colkey,
                                                                            B.colseg, &B.cnt[0], B.max_cols, status);
     }
