@@ -503,6 +503,10 @@ constexpr int FCAP = 256;          // capacity of the front
 constexpr int ICAP = CR_RED_ICAP;  // capacity of the inbox
 constexpr int TT = CR_RED_TT;      // merged positions per tile of a merge of sorted runs
 constexpr int RED_WARPS = 4;
+// a long version's entries up to tau (at most a front's worth) are staged in
+// the column buffer before they are merged into the front
+static_assert(DMAX >= FCAP, "the staged-column buffer must hold a full front");
+static_assert(TT % 32 == 0 && ICAP % 32 == 0 && ICAP >= 128, "warp-sized tiles and inbox");
 
 struct WarpSmem {
     uint64_t f[2][FCAP];   // the front: sorted, distinct (double buffered)
