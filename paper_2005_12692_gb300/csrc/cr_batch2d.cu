@@ -30,15 +30,15 @@ struct B2Work {
     uint64_t *mA, *mB, *dkey;
     uint32_t *hook;
     uint8_t *dead;
-    uint64_t *ek;
-    uint32_t *ea, *eb;
+    uint64_t *ek[2];
+    uint32_t *ea[2], *eb[2];  // two edge buffers: the rounds compact the live edges into the other
 };
 
 __host__ __device__ __forceinline__ size_t b2_al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 __host__ __device__ __forceinline__ size_t b2_stride(int64_t nmax, int64_t emax) {
-    return b2_al(nmax * 4) + b2_al(nmax) + 4 * b2_al(nmax * 8) + b2_al(nmax * 4) + b2_al(nmax) + b2_al(emax * 8) +
-           2 * b2_al(emax * 4);
+    return b2_al(nmax * 4) + b2_al(nmax) + 4 * b2_al(nmax * 8) + b2_al(nmax * 4) + b2_al(nmax) +
+           2 * (b2_al(emax * 8) + 2 * b2_al(emax * 4));
 }
 
 struct B2Args {
@@ -69,9 +69,11 @@ __device__ __forceinline__ B2Work b2_work(const B2Args &A) {
     W.dkey = (uint64_t *)(b + o); o += b2_al(A.nmax * 8);
     W.hook = (uint32_t *)(b + o); o += b2_al(A.nmax * 4);
     W.dead = (uint8_t *)(b + o); o += b2_al(A.nmax);
-    W.ek = (uint64_t *)(b + o); o += b2_al(A.emax * 8);
-    W.ea = (uint32_t *)(b + o); o += b2_al(A.emax * 4);
-    W.eb = (uint32_t *)(b + o);
+    for (int k = 0; k < 2; k++) {
+        W.ek[k] = (uint64_t *)(b + o); o += b2_al(A.emax * 8);
+        W.ea[k] = (uint32_t *)(b + o); o += b2_al(A.emax * 4);
+        W.eb[k] = (uint32_t *)(b + o); o += b2_al(A.emax * 4);
+    }
     return W;
 }
 
@@ -84,6 +86,23 @@ __device__ __forceinline__ int b2_take(bool pred, int *counter) {
     if (lane == leader) base = atomicAdd(counter, __popc(m));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
     return pred ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
+// block-aggregated increment of a shared counter by cnt; every thread of the
+// block calls it (warp-aggregated atomics; no block barrier)
+__device__ __forceinline__ int b2_take_block(int cnt, int *counter) {
+    const int lane = threadIdx.x & 31;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    int base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, total);
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    return base + incl - cnt;
 }
 
 // One graph of one image.  mode 0: the pixels (H0); mode 1: the squares and
@@ -281,9 +300,9 @@ __device__ bool b2_graph(const B2Args &A, const B2Work &W, const Seg &S, int si,
                 fail_ws(A.status, SITE_EDGES);
                 continue;
             }
-            W.ek[e] = keys[k];
-            W.ea[e] = las[k];
-            W.eb[e] = lbs[k];
+            W.ek[0][e] = keys[k];
+            W.ea[0][e] = las[k];
+            W.eb[0][e] = lbs[k];
             atomicMin((unsigned long long *)&W.mA[las[k]], keys[k]);
             atomicMin((unsigned long long *)&W.mA[lbs[k]], keys[k]);
         }
@@ -293,28 +312,52 @@ __device__ bool b2_graph(const B2Args &A, const B2Work &W, const Seg &S, int si,
     const int64_t ne = *s_ne < A.emax ? *s_ne : A.emax;
     if (*s_flag) return false;
 
-    // 5. Borůvka rounds under the elder rule
+    // 5. Borůvka rounds under the elder rule.  The edge loops take four edges
+    // per thread at a time (their loads are independent), and the edges that
+    // stay live are compacted into the other buffer.
+    constexpr int U = 4;
     uint64_t *mcur = W.mA, *mnext = W.mB;
+    int64_t nlive = ne;
+    int cb = 0;  // edge buffer in use
     for (long long round = 0;; round++) {
         if (round >= A.round_cap) {
             if (tid == 0) set_status(A.status, CR_ERR_TIMEOUT);
             return false;
         }
+        const uint64_t *ek = W.ek[cb];
+        const uint32_t *ea = W.ea[cb], *eb = W.eb[cb];
         // B: the edge attaining the younger end's minimum edge kills it
-        for (int64_t i = tid; i < ne; i += T) {
-            const uint32_t e0 = W.ea[i], e1 = W.eb[i];
-            if (e0 == e1) continue;
-            const uint64_t k = W.ek[i];
-            const bool young0 = W.gkey[e1] < W.gkey[e0];
-            const uint32_t g = young0 ? e0 : e1, t = young0 ? e1 : e0;
-            if (mcur[g] != k) continue;
-            W.hook[g] = t;
-            W.dead[g] = 1;
-            W.dkey[g] = k;
+        for (int64_t i0 = tid; i0 < nlive; i0 += (int64_t)U * T) {
+            uint32_t e0[U], e1[U];
+            uint64_t k[U], k0[U], k1[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t i = i0 + (int64_t)u * T;
+                e0[u] = i < nlive ? ea[i] : 0u;
+                e1[u] = i < nlive ? eb[i] : 0u;
+                k[u] = i < nlive ? ek[i] : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                k0[u] = W.gkey[e0[u]];
+                k1[u] = W.gkey[e1[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (e0[u] == e1[u]) continue;  // past the end (0, 0)
+                const bool young0 = k1[u] < k0[u];
+                const uint32_t g = young0 ? e0[u] : e1[u], t = young0 ? e1[u] : e0[u];
+                if (mcur[g] != k[u]) continue;
+                W.hook[g] = t;
+                W.dead[g] = 1;
+                W.dkey[g] = k[u];
+            }
         }
         for (int g = tid; g < G; g += T) mnext[g] = ~0ull;
         __syncthreads();
-        // C: pointer jumping to this round's roots
+        // C: pointer jumping to this round's roots (and the live-edge counter
+        // reset: every thread read it before the barrier above)
+        if (tid == 0) *s_ne = 0;
         for (int g = tid; g < G; g += T) {
             uint32_t p = W.hook[g];
             if (p == (uint32_t)g) continue;
@@ -326,28 +369,45 @@ __device__ bool b2_graph(const B2Args &A, const B2Work &W, const Seg &S, int si,
             }
         }
         __syncthreads();
-        // D: edges move to their roots and are offered to the next minimum edges
-        int live = 0;
-        for (int64_t i = tid; i < ne; i += T) {
-            const uint32_t e0 = W.ea[i], e1 = W.eb[i];
-            if (e0 == e1) continue;
-            const uint32_t a = W.hook[e0], b = W.hook[e1];
-            if (a == b) {
-                W.ea[i] = a;
-                W.eb[i] = a;
-                continue;
+        // D: edges move to their roots; those between two groups go to the
+        // other buffer and are offered to the next minimum edges
+        uint64_t *ok = W.ek[cb ^ 1];
+        uint32_t *oa = W.ea[cb ^ 1], *ob = W.eb[cb ^ 1];
+        for (int64_t base = 0; base < nlive; base += (int64_t)U * T) {
+            uint32_t a[U], b[U];
+            uint64_t k[U];
+            bool keep[U];
+            int cnt = 0;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t i = base + tid + (int64_t)u * T;
+                const bool in = i < nlive;
+                const uint32_t e0 = in ? ea[i] : 0u, e1 = in ? eb[i] : 0u;
+                k[u] = in ? ek[i] : 0ull;
+                a[u] = W.hook[e0];
+                b[u] = W.hook[e1];
+                keep[u] = in && a[u] != b[u];
+                cnt += keep[u];
             }
-            if (a != e0) W.ea[i] = a;
-            if (b != e1) W.eb[i] = b;
-            const uint64_t k = W.ek[i];
-            atomicMin((unsigned long long *)&mnext[a], k);
-            atomicMin((unsigned long long *)&mnext[b], k);
-            live = 1;
+            int64_t j = b2_take_block(cnt, s_ne);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (!keep[u]) continue;
+                ok[j] = k[u];
+                oa[j] = a[u];
+                ob[j] = b[u];
+                j++;
+                atomicMin((unsigned long long *)&mnext[a[u]], k[u]);
+                atomicMin((unsigned long long *)&mnext[b[u]], k[u]);
+            }
         }
+        __syncthreads();
+        nlive = *s_ne;
+        cb ^= 1;
         uint64_t *t = mcur;
         mcur = mnext;
         mnext = t;
-        if (!__syncthreads_or(live)) break;
+        if (nlive == 0) break;
     }
 
     // 6. the pairs: a dead group dies at its death edge; the surviving primal
