@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
     float(*box)[TMA_BY][TMA_BX] = reinterpret_cast<float(*)[TMA_BY][TMA_BX]>(dyn);
     uint8_t(*dds)[SC_DY][SC_DX] = reinterpret_cast<uint8_t(*)[SC_DY][SC_DX]>(dyn + TMA_BYTES);
     __shared__ __align__(8) uint64_t bar;
-    __shared__ uint32_t ext[3][TILE_Z][TILE_Y][2];  // death-mask words of each edge row
+    __shared__ uint32_t ext[3][TILE_Z][TILE_Y];  // death-mask bits of each edge row, bit tx = x0 + tx
     const Seg S = segs[0];
     const int nx = S.nx, ny = S.ny, nz = S.nz;
     int x0, y0, z0;
@@ -255,15 +255,15 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         const int dy = i % TILE_Y, r = i / TILE_Y;
         const int dz = r % TILE_Z, ax = r / TILE_Z;
         const int gy = y0 + dy, gz = z0 + dz;
-        uint32_t w0 = 0, w1 = 0;
+        uint32_t w0 = 0, w1 = 0, sh = 0;
         if (gy < ny && gz < nz) {
             const int64_t bit = S.loff + (int64_t)ax * P + (int64_t)gz * plane + (int64_t)gy * nx + x0;
             const int64_t last = (S.loff + (int64_t)3 * P + 31) >> 5;  // words of the mask
             w0 = __ldg(I.extra + (bit >> 5));
             if ((bit >> 5) + 1 < last) w1 = __ldg(I.extra + (bit >> 5) + 1);
+            sh = (uint32_t)(bit & 31);
         }
-        ext[ax][dz][dy][0] = w0;
-        ext[ax][dz][dy][1] = w1;
+        ext[ax][dz][dy] = __funnelshift_r(w0, w1, sh);  // 32 bits starting at x0's
     }
     __syncthreads();
     // the wait's outcome is made uniform so that no thread is left at a later barrier
@@ -280,7 +280,6 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
     const int bx = tx + 4, by = ty + 1;
     const int zend = min(TILE_Z, nz - z0);
     const bool keep_zero = (flags & CR_KEEP_ZERO) != 0;
-    const uint32_t lo = (uint32_t)S.loff;  // only its low bits matter for positions within mask words
     const bool hx = x + 1 < nx, hy = y + 1 < ny, my = y > 0;
     uint8_t *code = I.code + S.voff + (uint32_t)y * nx + (uint32_t)x;
     // Values of this thread's column roll through registers: f(x,y,z), f(x+1,y,z),
@@ -290,7 +289,9 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
     float fa = box[1][by][bx], fb = box[1][by][bx + 1], fc = box[1][by + 1][bx];
     float exc = fmaxf(fa, fb), eyc = fmaxf(fa, fc);
     float exp_ = fmaxf(box[0][by][bx], box[0][by][bx + 1]), eyp = fmaxf(box[0][by][bx], box[0][by + 1][bx]);
-    for (int zz = 0; zz < zend; zz++) {
+#pragma unroll
+    for (int zz = 0; zz < TILE_Z; zz++) {
+        if (zz >= zend) break;
         const int z = z0 + zz, bz = zz + 1;
         const uint32_t rowL = (uint32_t)z * plane + (uint32_t)y * nx + (uint32_t)x0;  // L of (x0, y, z)
         const uint32_t lv = rowL + (uint32_t)tx;
@@ -299,13 +300,11 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         const float exn = fmaxf(fa1, fb1), eyn = fmaxf(fa1, fc1);
         const uint8_t dv = dds[zz][ty][tx];
         uint32_t cd = 0;
-        // bit of this thread's x in a mask row whose first L-index is r0
-#define RB(r0) ((int)((lo + (r0)) & 31u) + tx)
         // an edge killed in dimension 0 (a stencil hook or a later round's
         // death) is not a column (and is never apparent, being paired with a vertex)
 #define KILLED(AX, DU)                                                         \
         (dv == (uint8_t)(2 * (AX) + 2) || (DU) == (uint8_t)(2 * (AX) + 1) || \
-         ((ext[AX][zz][ty][RB((AX) * P + rowL) >> 5] >> (RB((AX) * P + rowL) & 31)) & 1u))
+         ((ext[AX][zz][ty] >> tx) & 1u))
         // Candidates for the earliest cofacet of an edge sigma come in
         // descending face-L order; the first whose parallel edge sigma' has
         // value <= value(sigma) gives a face of value value(sigma), the least
@@ -359,7 +358,6 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
         // -- z-edge (v, v+z): a column whenever it survives dimension 0
         if (hz && !KILLED(2, dds[zz + 1][ty][tx])) cd |= CODE_RZ;
 #undef KILLED
-#undef RB
         code[(size_t)z * plane] = (uint8_t)cd;
         fa = fa1;
         fb = fb1;
@@ -1059,9 +1057,14 @@ __device__ __forceinline__ bool front_ready(const RedParams &R, Work &W, WarpSme
 }
 
 // Toggle x1 < x2 < x3 (the first m of them; all above the removed pivot).
-// Entries up to tau are merged into the front in one pass (lane e locates
-// entry e in the front; results are broadcast by shuffles), the rest go to
-// the inbox.
+// Entries up to tau are merged into the front, the rest go to the inbox.
+// Added tails usually land among the front's first entries, so the merge is
+// done in place when every entry to toggle falls among the first 32 and the
+// front has room at its head: the entries before the last toggled position
+// shift by the net count of insertions and cancellations behind them, the
+// rest stay where they are.  Otherwise one pass writes the merged front into
+// the other buffer, leaving FRONT_SLACK free slots at its head.
+constexpr int FRONT_SLACK = 4;
 __device__ bool toggle_small(const RedParams &R, Work &W, WarpSmem &sm, uint64_t x1, uint64_t x2, uint64_t x3,
                              int m, RedStats &st) {
     const int lane = threadIdx.x & 31;
@@ -1077,9 +1080,44 @@ __device__ bool toggle_small(const RedParams &R, Work &W, WarpSmem &sm, uint64_t
         if (!inbox_add(R, W, sm, v, mhi, st)) return false;
     }
     if (mlo == 0) return true;
-    const uint64_t *D = &sm.f[W.fb][W.fh];
-    uint64_t *out = sm.f[W.fb ^ 1];
     const int nd = W.fn - W.fh;
+    const uint64_t v0 = x1, v1 = mlo > 1 ? x2 : ~0ull, v2 = mlo > 2 ? x3 : ~0ull;
+    {
+        // in place: lane i holds the front's entry i (i < 32)
+        uint64_t *F = &sm.f[W.fb][W.fh];
+        const bool live = lane < nd;
+        const uint64_t d = live ? F[lane] : ~0ull;
+        const unsigned lt0 = __ballot_sync(0xFFFFFFFFu, live && d < v0), eq0m = __ballot_sync(0xFFFFFFFFu, live && d == v0);
+        const unsigned lt1 = __ballot_sync(0xFFFFFFFFu, live && d < v1), eq1m = __ballot_sync(0xFFFFFFFFu, live && d == v1);
+        const unsigned lt2 = __ballot_sync(0xFFFFFFFFu, live && d < v2), eq2m = __ballot_sync(0xFFFFFFFFu, live && d == v2);
+        const int q0 = __popc(lt0), q1 = __popc(lt1), q2 = __popc(lt2);
+        const int e0 = eq0m != 0, e1 = mlo > 1 && eq1m != 0, e2 = mlo > 2 && eq2m != 0;
+        const int E = e0 + e1 + e2;
+        const int qmax = mlo > 2 ? q2 : (mlo > 1 ? q1 : q0);  // the last toggled position
+        const int shift = mlo - 2 * E;                        // net entries added
+        if ((nd <= 32 || qmax < 32) && W.fh >= shift) {
+            // entry i moves by (insertions before it) - (cancellations before it) - shift
+            const int ins = (v0 < d && !e0) + (mlo > 1 && v1 < d && !e1) + (mlo > 2 && v2 < d && !e2);
+            const int can = (v0 < d && e0) + (mlo > 1 && v1 < d && e1) + (mlo > 2 && v2 < d && e2);
+            const bool drop = d == v0 || (mlo > 1 && d == v1) || (mlo > 2 && d == v2);
+            __syncwarp();  // every lane has read its entry
+            if (live && lane < 32 && !drop) F[lane + ins - can - shift] = d;
+            // inserted entry k lands after the q_k entries below it, the
+            // k - E_{<k} insertions before it, less the E_{<k} cancelled entries
+            if (lane < mlo) {
+                const int k = lane;
+                const uint64_t v = k == 0 ? v0 : (k == 1 ? v1 : v2);
+                const int q = k == 0 ? q0 : (k == 1 ? q1 : q2);
+                const int ek = k == 0 ? e0 : (k == 1 ? e1 : e2);
+                const int eb = (k > 0 ? e0 : 0) + (k > 1 ? e1 : 0);
+                if (!ek) F[q + k - 2 * eb - shift] = v;
+            }
+            __syncwarp();
+            W.fh -= shift;
+            return true;
+        }
+    }
+    const uint64_t *D = &sm.f[W.fb][W.fh];
     const uint64_t mine = lane == 0 ? x1 : (lane == 1 ? x2 : x3);
     int myq = 0, myeq = 0;
     if (lane < mlo) {
@@ -1093,7 +1131,9 @@ __device__ bool toggle_small(const RedParams &R, Work &W, WarpSmem &sm, uint64_t
     }
     const int eq0 = __shfl_sync(0xFFFFFFFFu, myeq, 0), eq1 = __shfl_sync(0xFFFFFFFFu, myeq, 1),
               eq2 = __shfl_sync(0xFFFFFFFFu, myeq, 2);
-    const uint64_t v0 = x1, v1 = mlo > 1 ? x2 : ~0ull, v2 = mlo > 2 ? x3 : ~0ull;
+    const int n2 = nd + mlo - 2 * (eq0 + (mlo > 1 ? eq1 : 0) + (mlo > 2 ? eq2 : 0));
+    const int off = min(FRONT_SLACK, FCAP - n2);
+    uint64_t *out = sm.f[W.fb ^ 1] + off;
     for (int i = lane; i < nd; i += 32) {
         const uint64_t d = D[i];
         int ins = 0, can = 0;
@@ -1109,8 +1149,8 @@ __device__ bool toggle_small(const RedParams &R, Work &W, WarpSmem &sm, uint64_t
     }
     __syncwarp();
     W.fb ^= 1;
-    W.fh = 0;
-    W.fn = nd + mlo - 2 * (eq0 + (mlo > 1 ? eq1 : 0) + (mlo > 2 ? eq2 : 0));
+    W.fh = off;
+    W.fn = off + n2;
     return true;
 }
 
