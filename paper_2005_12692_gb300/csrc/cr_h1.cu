@@ -104,13 +104,47 @@ __device__ __forceinline__ int edge_cofacets(const Img3 &I, const Seg &S, int a,
     return n;
 }
 
-__device__ __forceinline__ void sort4(uint64_t *v, int n) {
-    for (int i = 1; i < n; i++) {
-        uint64_t x = v[i];
-        int j = i - 1;
-        while (j >= 0 && v[j] > x) { v[j + 1] = v[j]; j--; }
-        v[j + 1] = x;
-    }
+// The cofacets of the edge along axis a at c in ascending order, in four
+// registers (absent ones are ~0 and sort last); returns how many exist.  A
+// face's value is the larger of the edge's and its parallel edge's, so the
+// ten vertex values are independent loads issued together.
+__device__ __forceinline__ void cswap(uint64_t &x, uint64_t &y) {
+    const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
+    x = lo;
+    y = hi;
+}
+__device__ __forceinline__ int edge_cofacets_sorted(const Img3 &I, const Seg &S, int a, const int *c, uint64_t &k0,
+                                                    uint64_t &k1, uint64_t &k2, uint64_t &k3) {
+    // axis quantities by selection (no dynamically indexed local arrays)
+    const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;  // the other two axes, b1 < b2
+    const int x = c[0], y = c[1], z = c[2];
+    const int64_t sxy = (int64_t)S.nx * S.ny;
+    const int64_t sa = a == 0 ? 1 : (a == 1 ? (int64_t)S.nx : sxy);
+    const int64_t s1 = b1 == 0 ? 1 : (int64_t)S.nx;
+    const int64_t s2 = b2 == 1 ? (int64_t)S.nx : sxy;
+    const int c1 = b1 == 0 ? x : y, c2 = b2 == 1 ? y : z;
+    const int n1 = b1 == 0 ? S.nx : S.ny, n2 = b2 == 1 ? S.ny : S.nz;
+    const float *f = I.img + S.voff + ((int64_t)z * S.ny + y) * S.nx + x;
+    const bool p1 = c1 + 1 < n1, m1 = c1 >= 1;
+    const bool p2 = c2 + 1 < n2, m2 = c2 >= 1;
+    const uint32_t e0 = ord32(f[0]), e1 = ord32(f[sa]);
+    const uint32_t u0 = p1 ? ord32(f[s1]) : 0u, u1 = p1 ? ord32(f[s1 + sa]) : 0u;
+    const uint32_t v0 = m1 ? ord32(f[-s1]) : 0u, v1 = m1 ? ord32(f[sa - s1]) : 0u;
+    const uint32_t w0 = p2 ? ord32(f[s2]) : 0u, w1 = p2 ? ord32(f[s2 + sa]) : 0u;
+    const uint32_t x0 = m2 ? ord32(f[-s2]) : 0u, x1 = m2 ? ord32(f[sa - s2]) : 0u;
+    const uint32_t ve = max(e0, e1);
+    const int t1 = min(a, b1) + max(a, b1) - 1, t2 = min(a, b2) + max(a, b2) - 1;  // face types
+    // the - faces are anchored one step back along b1 (x or y) or b2 (y or z)
+    k0 = p1 ? make_key(max(ve, max(u0, u1)), cube_L(S, t1, x, y, z)) : ~0ull;
+    k1 = m1 ? make_key(max(ve, max(v0, v1)), cube_L(S, t1, x - (b1 == 0), y - (b1 == 1), z)) : ~0ull;
+    k2 = p2 ? make_key(max(ve, max(w0, w1)), cube_L(S, t2, x, y, z)) : ~0ull;
+    k3 = m2 ? make_key(max(ve, max(x0, x1)), cube_L(S, t2, x, y - (b2 == 1), z - (b2 == 2))) : ~0ull;
+    cswap(k0, k1);
+    cswap(k2, k3);
+    cswap(k0, k2);
+    cswap(k1, k3);
+    cswap(k1, k2);
+    return (int)p1 + (int)m1 + (int)p2 + (int)m2;
 }
 
 // latest facet (max key) of the face of type fm at c; its axis and anchor returned
@@ -1231,11 +1265,11 @@ __device__ bool toggle_list(const RedParams &R, Work &W, WarpSmem &sm, const uin
     return true;
 }
 
-// Fill the lookahead cache for the front's next 32 entries.  The apparent
-// bit, the owner and the face's four vertices are read in one round trip; an
-// apparent face then needs its latest facet's cofacets (a second), an owned
-// face its owner's version and, when short, that version's entries (a second
-// and a third).
+// Fill the lookahead cache for the front's next 32 entries in two round
+// trips: the code bytes of the two edges that could pair the face as
+// apparent and its pivot-table entry, then either the apparent edge's vertex
+// values (its column is generated from them) or the head of the owner's
+// version.
 __device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, const WarpSmem &sm, Look &L) {
     const int lane = threadIdx.x & 31;
     const uint64_t cand = W.fh + lane < W.fn ? sm.f[W.fb][W.fh + lane] : ~0ull;
@@ -1266,31 +1300,38 @@ __device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, con
         if ((k0 & 7u) == 3u) ea = 0;
         else if ((k1 & 7u) == 4u) { ea = 0; ec[1] += 1; }
     }
+    // the second round trip: the apparent edge's vertex values, or the
+    // owner's version (its header and first four entries; the arena keeps
+    // ARENA_SLACK words of slack past its last version), issued together
+    const bool owned = ea < 0 && pe != PIV_FREE;
+    uint64_t vn = 0, vh = 0, a1 = 0, a2 = 0, a3 = 0;
+    if (owned) {
+        const uint64_t *C = R.arena + piv_off(pe);
+        vn = ld_cg(C);
+        vh = ld_cg(C + 1);
+        a1 = ld_cg(C + 2);
+        a2 = ld_cg(C + 3);
+        a3 = ld_cg(C + 4);
+    }
     if (ea >= 0) {
         // the apparent edge's column: its cofacets, the face itself first
-        uint64_t cf[4];
-        const int n = edge_cofacets(R.I, S, ea, ec, cf);
-        sort4(cf, n);
+        uint64_t f0, f1, f2, f3;
+        L.k = edge_cofacets_sorted(R.I, S, ea, ec, f0, f1, f2, f3);
         L.kind = 1;
-        L.c1 = n > 1 ? cf[1] : ~0ull;
-        L.c2 = n > 2 ? cf[2] : ~0ull;
-        L.c3 = n > 3 ? cf[3] : ~0ull;
-        L.k = n;
+        L.c1 = f1;
+        L.c2 = f2;
+        L.c3 = f3;
         return;
     }
-    if (pe == PIV_FREE) return;
+    if (!owned) return;
     L.kind = 2;
     L.own = piv_owner(pe);
     L.ver = pe;
-    // the version's header and first four entries in one round trip (the
-    // arena keeps ARENA_SLACK words of slack past its last version)
-    const uint64_t *C = R.arena + piv_off(pe);
-    const uint64_t n = ld_cg(C), h = ld_cg(C + 1), a1 = ld_cg(C + 2), a2 = ld_cg(C + 3), a3 = ld_cg(C + 4);
-    if (n >= 1 && n <= 4 && h == cand) {
-        L.c1 = n > 1 ? a1 : ~0ull;
-        L.c2 = n > 2 ? a2 : ~0ull;
-        L.c3 = n > 3 ? a3 : ~0ull;
-        L.k = (int)n;
+    if (vn >= 1 && vn <= 4 && vh == cand) {
+        L.c1 = vn > 1 ? a1 : ~0ull;
+        L.c2 = vn > 2 ? a2 : ~0ull;
+        L.c3 = vn > 3 ? a3 : ~0ull;
+        L.k = (int)vn;
     }
 }
 
@@ -1361,10 +1402,9 @@ __global__ void __launch_bounds__(RED_WARPS * 32, CR_RED_BLOCKS_PER_SM) k_h1_red
         {
             int a, c[3];
             decode_L(S, key_L(jkey), a, c);
-            uint64_t cf[4];
-            const int k = edge_cofacets(R.I, S, a, c, cf);
-            sort4(cf, k);
-            if (lane < k) sm.f[0][lane] = cf[lane];
+            uint64_t f0, f1, f2, f3;
+            const int k = edge_cofacets_sorted(R.I, S, a, c, f0, f1, f2, f3);
+            if (lane < k) sm.f[0][lane] = lane == 0 ? f0 : (lane == 1 ? f1 : (lane == 2 ? f2 : f3));
             W.fb = 0;
             W.fh = 0;
             W.fn = k;
