@@ -1195,13 +1195,22 @@ __device__ bool toggle_small(const RedParams &R, Work &W, WarpSmem &sm, uint64_t
 template <bool XG>
 __device__ bool toggle_list(const RedParams &R, Work &W, WarpSmem &sm, const uint64_t *X, int n, RedStats &st) {
     const int lane = threadIdx.x & 31;
+    // entries <= t: 32 evenly spaced probes per round narrow [lo, hi] 32-fold,
+    // so a run in global memory costs a few round trips, not one per halving
     auto count_le = [&](uint64_t t) {
         int lo = 0, hi = n;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((XG ? ld_cg(X + mid) : X[mid]) <= t) lo = mid + 1; else hi = mid;
+        while (hi - lo > 32) {
+            const int step = (hi - lo + 31) / 32;
+            const int idx = lo + lane * step;
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, idx < hi && (XG ? ld_cg(X + idx) : X[idx]) <= t);
+            const int cnt = __popc(m);  // a prefix of the lanes
+            if (cnt == 0) return lo;
+            const int nhi = min(hi, lo + cnt * step);
+            lo += (cnt - 1) * step + 1;
+            hi = nhi;
         }
-        return lo;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, lo + lane < hi && (XG ? ld_cg(X + lo + lane) : X[lo + lane]) <= t);
+        return lo + __popc(m);
     };
     int nlo = count_le(W.tau);
     if (nlo > 0 && W.fn - W.fh + nlo > FCAP) {
