@@ -244,7 +244,8 @@ constexpr int SC_DD_BYTES = SC_DX * SC_DY * SC_DZ;
 constexpr int SCAN_DYN_SMEM = TMA_BYTES + SC_DD_BYTES + 128;
 static_assert(TMA_BYTES % 128 == 0, "hook-code box must start on a 128-byte boundary");
 
-__global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_constant__ CUtensorMap tmap,
+constexpr int SCAN_THREADS = TILE_X * TILE_Y;
+__global__ void __launch_bounds__(SCAN_THREADS) k_h1_scan_tma(const __grid_constant__ CUtensorMap tmap,
                                                                const __grid_constant__ CUtensorMap tmap_dd,
                                                                int dd_by_tma, Img3 I, const Seg *__restrict__ segs,
                                                                PairBuf pb, uint32_t flags, int *status) {
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_h1_scan_tma(const __grid_con
     float fa = box[1][by][bx], fb = box[1][by][bx + 1], fc = box[1][by + 1][bx];
     float exc = fmaxf(fa, fb), eyc = fmaxf(fa, fc);
     float exp_ = fmaxf(box[0][by][bx], box[0][by][bx + 1]), eyp = fmaxf(box[0][by][bx], box[0][by + 1][bx]);
-#pragma unroll
+#pragma unroll 4  // a full unroll stalls on instruction fetch
     for (int zz = 0; zz < TILE_Z; zz++) {
         if (zz >= zend) break;
         const int z = z0 + zz, bz = zz + 1;
@@ -1610,7 +1611,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
         }
         const int dd_tma = make_u8_map(&tmap_dd, dd, *hseg, SC_DX, SC_DY, SC_DZ) ? 1 : 0;
         if (!dd_tma) memset(&tmap_dd, 0, sizeof(tmap_dd));
-        k_h1_scan_tma<<<(unsigned)ntiles, TILE_X * TILE_Y, SCAN_DYN_SMEM, st>>>(tmap, tmap_dd, dd_tma, I, segs,
+        k_h1_scan_tma<<<(unsigned)ntiles, SCAN_THREADS, SCAN_DYN_SMEM, st>>>(tmap, tmap_dd, dd_tma, I, segs,
                                                                                pb, flags, status);
     } else {
         k_h1_scan<<<(unsigned)ntiles, TILE_X * TILE_Y, 0, st>>>(I, segs, nseg, pb, flags, status);
