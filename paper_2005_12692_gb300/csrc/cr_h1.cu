@@ -439,28 +439,36 @@ __global__ void k_h1_columns(const float *__restrict__ img, const uint8_t *__res
         if (!cnt) continue;
         int64_t i = (int64_t)wbase + (incl - cnt);
         const int si = seg_of_v(segs, nseg, ch * 4);  // a chunk of four voxels can straddle two images
+        // every value the four voxels' columns need is loaded before any is used
+        int sj[4];
+        float f0[4], fu[4][3];
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const uint32_t cd = (w >> (8 * b)) & 0xE0u;
+            const int64_t gv = ch * 4 + b;
+            sj[b] = (cd && si + 1 < nseg && gv >= segs[si + 1].voff) ? seg_of_v(segs, nseg, gv) : si;
+            const int64_t nx = segs[sj[b]].nx, plane = nx * segs[sj[b]].ny;
+            f0[b] = cd ? img[gv] : 0.f;
+            fu[b][0] = (cd & CODE_RX) ? img[gv + 1] : 0.f;
+            fu[b][1] = (cd & CODE_RY) ? img[gv + nx] : 0.f;
+            fu[b][2] = (cd & CODE_RZ) ? img[gv + plane] : 0.f;
+        }
 #pragma unroll
         for (int b = 0; b < 4; b++) {
             const uint32_t cd = (w >> (8 * b)) & 0xE0u;
             if (!cd) continue;
             const int64_t gv = ch * 4 + b;
-            const int sj = (si + 1 < nseg && gv >= segs[si + 1].voff) ? seg_of_v(segs, nseg, gv) : si;
-            const Seg S = segs[sj];
+            const Seg S = segs[sj[b]];
             const uint32_t lv = (uint32_t)(gv - S.voff);
-            const uint32_t plane = (uint32_t)S.nx * (uint32_t)S.ny, P = plane * (uint32_t)S.nz;
-            const float f0 = img[gv];
-            const float fx = (cd & CODE_RX) ? img[gv + 1] : 0.f;
-            const float fy = (cd & CODE_RY) ? img[gv + S.nx] : 0.f;
-            const float fz = (cd & CODE_RZ) ? img[gv + plane] : 0.f;
-            const uint32_t ov = ord32(f0);
-            const float fu[3] = {fx, fy, fz};
+            const uint32_t P = (uint32_t)S.nx * (uint32_t)S.ny * (uint32_t)S.nz;
+            const uint32_t ov = ord32(f0[b]);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 if (!((cd >> (5 + a)) & 1u)) continue;
-                const uint32_t ou = ord32(fu[a]);
+                const uint32_t ou = ord32(fu[b][a]);
                 if (i < max_cols) {
                     colkey[i] = ~make_key(ov > ou ? ov : ou, lv + (uint32_t)a * P);
-                    colseg[i] = (uint32_t)sj;
+                    colseg[i] = (uint32_t)sj[b];
                 } else {
                     fail_ws(status, SITE_COLUMNS);
                 }

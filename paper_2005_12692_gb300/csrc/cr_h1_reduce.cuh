@@ -790,8 +790,10 @@ __global__ void __launch_bounds__(RED_WARPS * 32, RED_BLOCKS) k_h1_reduce(RedPar
                 return;
             }
             if (W.fh == W.fn) { if (lane == 0) set_status(R.status, CR_ERR_INTERNAL); break; }
-            if (!keep && it > R.budget) {
-                // over budget: publish the column as it stands and set it aside
+            // over budget, or the queue is drained (then the rest of the pass
+            // would run at this instance's lower speed per column): publish the
+            // column as it stands and set it aside
+            if (!keep && (it > R.budget || ((it & 31) == 0 && __shfl_sync(0xFFFFFFFFu, __ldcg(R.next), 0) >= (unsigned long long)R.ncols))) {
                 unsigned long long voff = 0;
                 if (!publish_work(R, j, W, sm, st, &voff)) { if (lane == 0) fail_ws(R.status, SITE_ARENA); flush_stats(R, st); return; }
                 unsigned long long di = 0;
