@@ -1090,6 +1090,44 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int &
 }
 
 // ---------------------------------------------------------------------------
+// Hooks of a volume's dual graph run along z only: a cube's minimum dual edge
+// is one of its two z-facets (see k_dual_stencil_tma), so it hooks to the cube
+// below, the cube above, the outer node or nothing.  A chain of hooks keeps
+// its direction (a cube hooked to the one below is older than it, so that
+// cube cannot hook back up).  One upward sweep of each (x, y) column of cubes
+// therefore resolves the downward chains and one downward sweep the upward
+// ones, leaving every cube pointing at its root; pointer jumping would take
+// log2 of the longest chain (up to nz) passes over every cube to get there.
+// ---------------------------------------------------------------------------
+__global__ void k_dual_zsweep(uint32_t *__restrict__ parent, uint32_t coff, int cx, int cy, int cz) {
+    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= (int64_t)cx * cy) return;
+    const uint32_t pl = (uint32_t)cx * (uint32_t)cy;
+    uint32_t *p = parent + coff + col;
+    const uint32_t g0 = coff + (uint32_t)col;
+    uint32_t below = 0;  // the final target of the cube below
+#pragma unroll 4
+    for (int z = 0; z < cz; z++) {
+        uint32_t t = __ldcg(p + (size_t)z * pl);
+        if (z > 0 && t == g0 + (uint32_t)(z - 1) * pl) {
+            t = below;
+            p[(size_t)z * pl] = t;
+        }
+        below = t;
+    }
+    uint32_t above = 0;  // the final target of the cube above
+#pragma unroll 4
+    for (int z = cz - 1; z >= 0; z--) {
+        uint32_t t = __ldcg(p + (size_t)z * pl);
+        if (z + 1 < cz && t == g0 + (uint32_t)(z + 1) * pl) {
+            t = above;
+            p[(size_t)z * pl] = t;
+        }
+        above = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Basins in one cooperative launch (one 1024-thread block per SM), for one or
 // both graphs at once:
 //   passes of in-place pointer doubling until a pass changes nothing (every
@@ -1558,6 +1596,7 @@ int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
         }
         prof_end(st, STAGE_H0_STENCIL, 9.0 * vtot);
     }
+    bool dual_z_only = false;  // the dual's hooks all run along z (a single volume's stencil)
     if (u1 && nstiles == 0) {
         prof_begin(st, STAGE_DUAL_STENCIL);
         CR_NOTE_LAUNCH();
@@ -1565,9 +1604,11 @@ int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
         const int edim = hsegs[0].edim;
         if (nseg == 1 && (edim == 2 || edim == 3) &&
             make_image_map(&tmap, img, hsegs[0], DUAL_BX, DUAL_BY, edim == 3 ? DUAL_BZ3 : 1)) {
-            if (edim == 3)
+            if (edim == 3) {
                 k_dual_stencil_tma<3><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u1->lab,
                                                                                        u1->dd, status, pb, flags);
+                dual_z_only = true;
+            }
             else
                 k_dual_stencil_tma<2><<<(unsigned)ntiles, dim3(TILE_X, TILE_Y), 0, st>>>(tmap, segs, u1->lab,
                                                                                        u1->dd, status, pb, flags);
@@ -1597,6 +1638,15 @@ int run_uf(const float *img, const Seg *segs, const Seg *hsegs, int nseg, int64_
         }
         void *args[] = {&A};
         prof_begin(st, STAGE_JUMP);
+        if (dual_z_only) {
+            const Seg &H = hsegs[0];
+            const int cx = H.nx - 1, cy = H.ny - 1, cz = H.nz - 1;
+            const int64_t cols = (int64_t)cx * cy;
+            if (cols > 0 && cz > 0) {
+                CR_NOTE_LAUNCH();
+                k_dual_zsweep<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(u1->lab, (uint32_t)H.coff, cx, cy, cz);
+            }
+        }
         CR_NOTE_LAUNCH();
         cudaError_t e = cudaLaunchCooperativeKernel((void *)k_basins, dim3(coop_blocks(work)), dim3(BASIN_THREADS),
                                                     args, 0, st);
