@@ -286,7 +286,7 @@ def load_peaks():
 # ---------------------------------------------------------------------------
 # oracle (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
-VOLUME_SAMPLE = 80  # side of the corner crop of a volume the oracle times (a few seconds of CPU work)
+VOLUME_SAMPLE = 144  # corner crop side: about 10 s of the oracle on one core
 
 
 def _oracle_one(a):
@@ -296,7 +296,7 @@ def _oracle_one(a):
     return a.size
 
 
-def oracle_sample(name, data, batch_images=256):
+def oracle_sample(name, data, batch_images=1024):
     """A bounded sample of the workload for the CPU oracle: (arrays, units, unit-scale, description)."""
     if name in ("uniform64", "grf1024"):
         return [data], num_cells(data.shape), "the full %s image" % "x".join(map(str, data.shape))

@@ -1102,30 +1102,46 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int &
 __global__ void k_dual_zsweep(uint32_t *__restrict__ parent, uint32_t coff, int cx, int cy, int cz) {
     const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= (int64_t)cx * cy) return;
-    const uint32_t pl = (uint32_t)cx * (uint32_t)cy;
+    const int64_t pl = (int64_t)cx * cy;
     uint32_t *p = parent + coff + col;
     const uint32_t g0 = coff + (uint32_t)col;
+    // targets are read eight planes at a time (a sweep writes only the cube
+    // it is at, so the cubes ahead still hold their stencil hooks)
+    constexpr int DEPTH = 8;
     uint32_t below = 0;  // the final target of the cube below
-#pragma unroll 4
-    for (int z = 0; z < cz; z++) {
-        uint32_t t = __ldcg(p + (size_t)z * pl);
-        if (z > 0 && t == g0 + (uint32_t)(z - 1) * pl) {
-            t = below;
-            p[(size_t)z * pl] = t;
+    for (int z0 = 0; z0 < cz; z0 += DEPTH) {
+        uint32_t t[DEPTH];
+#pragma unroll
+        for (int k = 0; k < DEPTH; k++) t[k] = z0 + k < cz ? __ldcg(p + (z0 + k) * pl) : 0u;
+#pragma unroll
+        for (int k = 0; k < DEPTH; k++) {
+            const int z = z0 + k;
+            if (z >= cz) break;
+            if (z > 0 && t[k] == g0 + (uint32_t)((z - 1) * pl)) {
+                t[k] = below;
+                p[z * pl] = below;
+            }
+            below = t[k];
         }
-        below = t;
     }
     uint32_t above = 0;  // the final target of the cube above
-#pragma unroll 4
-    for (int z = cz - 1; z >= 0; z--) {
-        uint32_t t = __ldcg(p + (size_t)z * pl);
-        if (z + 1 < cz && t == g0 + (uint32_t)(z + 1) * pl) {
-            t = above;
-            p[(size_t)z * pl] = t;
+    for (int z1 = cz - 1; z1 >= 0; z1 -= DEPTH) {
+        uint32_t t[DEPTH];
+#pragma unroll
+        for (int k = 0; k < DEPTH; k++) t[k] = z1 - k >= 0 ? __ldcg(p + (z1 - k) * pl) : 0u;
+#pragma unroll
+        for (int k = 0; k < DEPTH; k++) {
+            const int z = z1 - k;
+            if (z < 0) break;
+            if (z + 1 < cz && t[k] == g0 + (uint32_t)((z + 1) * pl)) {
+                t[k] = above;
+                p[z * pl] = above;
+            }
+            above = t[k];
         }
-        above = t;
     }
 }
+
 
 // ---------------------------------------------------------------------------
 // Basins in one cooperative launch (one 1024-thread block per SM), for one or
