@@ -260,7 +260,7 @@ def tune_candidates(W, data):
     if W["kind"] == "batch":
         return {"batch_threads": [0, 1, 2, 3], "uf_compact": [1, 4]}
     if len(data.shape) == 3 and min(data.shape) > 1:
-        return {"red_warps": [8, 16], "uf_compact": [1, 4]}
+        return {"red_warps": [8, 16], "uf_compact": [1, 4], "red_budget": [512, 1024, 2048]}
     return {"uf_items": [2, 4, 8, 16, 32], "uf_compact": [1, 2, 4, 8]}
 
 
@@ -414,18 +414,26 @@ def plain_path(cr, data, dev, stream, sub=512):
     return {"images_per_s": sub / (pms / 1e3), "sample": "first %d images, same loss, one stream" % sub}
 
 
-def measure_extra(cr, name, dev, stream, flush, steps=10, warmup=3):
-    """One of the other configurations, device-resident, L2 flushed between steps."""
+def measure_extra(cr, name, dev, stream, flush, steps=10, warmup=3, tune=True):
+    """One of the other configurations, device-resident, L2 flushed between steps; its launch knobs tuned
+    for it first, as the headline's are (outside the timed region)."""
     W = WORKLOADS[name]
     data = make_input(name)
     step, units, st = make_step(cr, W, data, dev)
+    tuned = None
+    if tune:
+        from paper_2005_12692_gb300 import autotune as at
+        try:
+            tuned = at.autotune(step, tune_candidates(W, data), warmup=2, repeats=3).best
+        except cr.CRError:  # keep the default launch shapes
+            at.apply(at.DEFAULTS)
     for _ in range(warmup):
         step()
     ms = time_calls(step, steps, stream, flush, dev)
     m = statistics.mean(ms)
     unit = "images/s" if W["kind"] == "batch" else "cells/s"
     out = {"value": units / (m / 1e3), "unit": unit, "ms_per_step": m, "steps": steps, "warmup": warmup,
-           "config": workload_config(name, W, data, 1)}
+           "config": workload_config(name, W, data, 1), "tuning": tuned}
     if W["kind"] == "batch":
         pl = plain_path(cr, data, dev, stream)
         out["plain_path"] = pl
@@ -724,7 +732,8 @@ def main():
             for name in EXTRA_WORKLOADS:
                 try:
                     extra[name] = measure_extra(cr, name, dev, stream, flush,
-                                                steps=min(WORKLOADS[name]["steps"], 20))
+                                                steps=min(WORKLOADS[name]["steps"], 20),
+                                                tune=args.autotune == "on")
                 except Exception as e:  # reported, never fatal to the headline numbers
                     extra[name] = {"error": str(e)[:200]}
                 torch.cuda.empty_cache()

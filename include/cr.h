@@ -318,9 +318,15 @@ int cr_h1_last_stats(int64_t *out, int n);
  *                      1..64, default 8.  A smaller value launches more blocks
  *                      for mid-size inputs: more parallel work, more blocks
  *                      arriving at every grid barrier.
- *   CR_TUNE_RED_WARPS  warps per SM working on the middle-dimension reduction
- *                      of 3D images; 1..16, default 16 (the workspace is sized
- *                      for 16).
+ *   CR_TUNE_RED_WARPS  warps per SM launched for the deep pass of the
+ *                      middle-dimension reduction of 3D images; 1..16,
+ *                      default 16 (the workspace is sized for 16).
+ *   CR_TUNE_RED_BUDGET steps a residual column may take in the wide pass of
+ *                      that reduction (16 warps per SM, small buffers) before
+ *                      it is published and set aside for the deep pass;
+ *                      0..2^24, default 1024; 0 runs the deep pass alone.
+ *                      Any budget gives the same pairs: the reduction reaches
+ *                      the same pivots whatever the order of its additions.
  *   CR_TUNE_UF_COMPACT the union-find rounds compact their edge list while it
  *                      holds more than this many edges per launched thread,
  *                      then mark dead edges in place; 1..64, default 1.
@@ -338,7 +344,8 @@ int cr_h1_last_stats(int64_t *out, int n);
 #define CR_TUNE_RED_WARPS 1
 #define CR_TUNE_UF_COMPACT 2
 #define CR_TUNE_BATCH_THREADS 3
-#define CR_TUNE_COUNT 4
+#define CR_TUNE_RED_BUDGET 4
+#define CR_TUNE_COUNT 5
 int cr_tune_set(int knob, int value);
 int cr_tune_get(int knob, int *value);
 

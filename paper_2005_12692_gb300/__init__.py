@@ -47,6 +47,7 @@ CR_TUNE_UF_ITEMS = 0
 CR_TUNE_RED_WARPS = 1
 CR_TUNE_UF_COMPACT = 2
 CR_TUNE_BATCH_THREADS = 3
+CR_TUNE_RED_BUDGET = 4
 CR_PAIR_ESSENTIAL = 1
 
 PAIR_BYTES = 32
@@ -616,6 +617,8 @@ class PersistentHomology(torch.autograd.Function):
 __all__ = [
     "build", "lib", "cr_persistence", "cr_persistence_batched", "cr_backward", "cr_backward_batched",
     "PersistentHomology", "Pairs", "BatchedPairs", "CRError", "cell_location", "error_string",
-    "CR_KEEP_ZERO", "CR_TOPDIM_ONLY", "CR_LOC_DEATH", "pair_table", "cr_tune_set", "cr_tune_get", "cr_persistence_f64", "Pairs64",
-    "CR_TUNE_UF_ITEMS", "CR_TUNE_RED_WARPS", "CR_TUNE_UF_COMPACT", "CR_TUNE_BATCH_THREADS", "debug_limits",
+    "CR_KEEP_ZERO", "CR_TOPDIM_ONLY", "CR_LOC_DEATH", "pair_table", "cr_tune_set", "cr_tune_get", "cr_persistence_f64",
+    "Pairs64",
+    "CR_TUNE_UF_ITEMS", "CR_TUNE_RED_WARPS", "CR_TUNE_UF_COMPACT", "CR_TUNE_BATCH_THREADS", "CR_TUNE_RED_BUDGET",
+    "debug_limits",
 ]

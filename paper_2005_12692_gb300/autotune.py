@@ -22,17 +22,18 @@ import statistics
 from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional, Sequence, Tuple
 
-from . import (CR_TUNE_BATCH_THREADS, CR_TUNE_RED_WARPS, CR_TUNE_UF_COMPACT, CR_TUNE_UF_ITEMS, cr_tune_get,
-               cr_tune_set)
+from . import (CR_TUNE_BATCH_THREADS, CR_TUNE_RED_BUDGET, CR_TUNE_RED_WARPS, CR_TUNE_UF_COMPACT, CR_TUNE_UF_ITEMS,
+               cr_tune_get, cr_tune_set)
 
 KNOBS: Dict[str, int] = {
     "uf_items": CR_TUNE_UF_ITEMS,
     "red_warps": CR_TUNE_RED_WARPS,
     "uf_compact": CR_TUNE_UF_COMPACT,
     "batch_threads": CR_TUNE_BATCH_THREADS,
+    "red_budget": CR_TUNE_RED_BUDGET,
 }
 
-DEFAULTS: Dict[str, int] = {"uf_items": 8, "red_warps": 16, "uf_compact": 1, "batch_threads": 2}
+DEFAULTS: Dict[str, int] = {"uf_items": 8, "red_warps": 16, "uf_compact": 1, "batch_threads": 2, "red_budget": 1024}
 
 
 def current() -> Dict[str, int]:

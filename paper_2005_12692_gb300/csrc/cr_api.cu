@@ -20,9 +20,9 @@ namespace cr {
 // ---------------------------------------------------------------------------
 // Launch knobs (host-side, per process): see cr_tune_set in include/cr.h.
 // ---------------------------------------------------------------------------
-static std::atomic<int> g_tune[CR_TUNE_COUNT] = {{8}, {16}, {1}, {2}};
+static std::atomic<int> g_tune[CR_TUNE_COUNT] = {{8}, {16}, {1}, {2}, {1024}};
 static std::atomic<uint32_t> g_tune_epoch{0};
-static const int g_tune_lo[CR_TUNE_COUNT] = {1, 1, 1, 0}, g_tune_hi[CR_TUNE_COUNT] = {64, 16, 64, 3};
+static const int g_tune_lo[CR_TUNE_COUNT] = {1, 1, 1, 0, 0}, g_tune_hi[CR_TUNE_COUNT] = {64, 16, 64, 3, 1 << 24};
 int tune_value(int knob) { return g_tune[knob].load(std::memory_order_relaxed); }
 uint32_t tune_epoch() { return g_tune_epoch.load(std::memory_order_relaxed); }
 

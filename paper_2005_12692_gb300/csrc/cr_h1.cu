@@ -536,7 +536,8 @@ constexpr int ARENA_SLACK = 32;
 // is compiled twice (cr_h1_reduce.cuh): a wide instance, 16 warps per SM with
 // a small inbox, takes every column first and sets aside the few that run
 // past an iteration budget; a deep instance, 8 warps per SM with a large
-// inbox and merge tiles, then finishes those.
+// inbox and merge tiles, then finishes those (the budget is a launch knob,
+// CR_TUNE_RED_BUDGET).
 #ifndef CR_RED_DMAX
 #define CR_RED_DMAX 256
 #endif
@@ -557,9 +558,6 @@ constexpr int ARENA_SLACK = 32;
 #endif
 #ifndef CR_RED_WIDE_BLOCKS_PER_SM
 #define CR_RED_WIDE_BLOCKS_PER_SM 4
-#endif
-#ifndef CR_RED_BUDGET
-#define CR_RED_BUDGET 1024  // iterations a column may take in the wide pass (0: one deep pass only)
 #endif
 constexpr int DMAX = CR_RED_DMAX;  // entries of a published column staged in shared memory
 constexpr int FCAP = 256;          // capacity of the front
@@ -595,8 +593,11 @@ struct Look {
 // shared-memory store.  When the front runs empty it is refilled with the
 // entries of the other three parts up to a new cut.
 // ---------------------------------------------------------------------------
-constexpr int MIDMAX = 8192;
-constexpr int MID_ON = 8192;
+#ifndef CR_RED_MIDMAX
+#define CR_RED_MIDMAX 8192
+#endif
+constexpr int MIDMAX = CR_RED_MIDMAX;  // the middle level is merged into the base past this many entries
+constexpr int MID_ON = 8192;          // base entries from which a column keeps a middle level
 constexpr int MIDCAP = 2 * MIDMAX + DMAX;
 
 struct Work {
@@ -858,12 +859,13 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
         }
     }
     prof_begin(st, STAGE_H1_REDUCE);
-    if (CR_RED_BUDGET > 0) {
+    const int budget = tune_value(CR_TUNE_RED_BUDGET);  // steps a column may take in the wide pass
+    if (budget > 0) {
         // the wide pass: every column, those past the budget set aside
         int64_t w = (int64_t)sms * RED_WARPS * wide::RED_BLOCKS;
         if (w > B.nwarps) w = B.nwarps;  // the scratch holds B.nwarps warps
         if (w > ncols) w = ncols;
-        R.budget = CR_RED_BUDGET;
+        R.budget = budget;
         R.resume = 0;
         CR_NOTE_LAUNCH();
         wide::k_h1_reduce<<<(unsigned)((w + RED_WARPS - 1) / RED_WARPS), RED_WARPS * 32, wide::RED_SMEM, st>>>(R);

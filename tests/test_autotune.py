@@ -16,7 +16,8 @@ def at(cr):
 
 def test_defaults_and_bounds(cr, at):
     assert at.current() == at.DEFAULTS
-    for name, lo, hi in (("uf_items", 1, 64), ("red_warps", 1, 16), ("uf_compact", 1, 64), ("batch_threads", 0, 3)):
+    for name, lo, hi in (("uf_items", 1, 64), ("red_warps", 1, 16), ("uf_compact", 1, 64), ("batch_threads", 0, 3),
+                         ("red_budget", 0, 1 << 24)):
         k = at.KNOBS[name]
         for bad in (lo - 1, hi + 1):
             with pytest.raises(cr.CRError) as e:
@@ -28,7 +29,7 @@ def test_defaults_and_bounds(cr, at):
         cr.cr_tune_set(k, hi)
         assert cr.cr_tune_get(k) == hi
     with pytest.raises(cr.CRError):
-        cr.cr_tune_set(4, 1)
+        cr.cr_tune_set(5, 1)
     with pytest.raises(cr.CRError):
         cr.cr_tune_get(-1)
 
@@ -47,7 +48,7 @@ def test_coordinate_descent_picks_the_fastest(cr, at):
 
     res = at.autotune(run, {"uf_items": [2, 4, 8, 16], "uf_compact": [1, 4, 16, 64]}, warmup=1, repeats=3,
                       timer=timer)
-    assert res.best == {"uf_items": 4, "red_warps": 16, "uf_compact": 16, "batch_threads": 2}
+    assert res.best == {"uf_items": 4, "red_warps": 16, "uf_compact": 16, "batch_threads": 2, "red_budget": 1024}
     assert at.current() == res.best  # left set in the library
     # every candidate was timed once in the table; the second knob was timed with the first at its best
     assert [(k, v) for k, v, _ in res.table] == [("uf_items", 2), ("uf_items", 4), ("uf_items", 8),
