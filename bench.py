@@ -289,6 +289,14 @@ def load_peaks():
 VOLUME_SAMPLE = 144  # corner crop side: about 10 s of the oracle on one core
 
 
+def volume_sample_side(calls):
+    """Crop side for an oracle run repeated `calls` times: about 150 s in all at the oracle's ~1.8 M cells/s on
+    one core of the box (8 cells per voxel), never above VOLUME_SAMPLE."""
+    per_call = 150.0 / max(1, calls)
+    side = int((per_call * 1.8e6 / 8.0) ** (1.0 / 3.0))
+    return max(32, min(VOLUME_SAMPLE, side))
+
+
 def _oracle_one(a):
     import oracle
     oracle.build()
@@ -296,12 +304,12 @@ def _oracle_one(a):
     return a.size
 
 
-def oracle_sample(name, data, batch_images=1024):
+def oracle_sample(name, data, batch_images=1024, side=VOLUME_SAMPLE):
     """A bounded sample of the workload for the CPU oracle: (arrays, units, unit-scale, description)."""
     if name in ("uniform64", "grf1024"):
         return [data], num_cells(data.shape), "the full %s image" % "x".join(map(str, data.shape))
     if name in ("grf256cube_salt", "grf512cube"):
-        k = VOLUME_SAMPLE
+        k = side
         sub = np.ascontiguousarray(data[:k, :k, :k])
         return [sub], num_cells(sub.shape), "a %d^3 corner crop of the %d^3 volume, scaled to cells/s" % (
             k, data.shape[0])
@@ -316,8 +324,9 @@ class OracleRunner:
     """Times the oracle on a sample.  Batches run one image per task on a pool
     of all host cores, started with 'spawn' (no GPU state is inherited)."""
 
-    def __init__(self, name):
+    def __init__(self, name, side=VOLUME_SAMPLE):
         self.name = name
+        self.side = side
         self.pool = None
         self.cores = 1
         if WORKLOADS[name]["kind"] == "batch":
@@ -329,7 +338,7 @@ class OracleRunner:
     def run(self, data):
         import oracle
         oracle.build()
-        arrs, units, desc = oracle_sample(self.name, data)
+        arrs, units, desc = oracle_sample(self.name, data, side=self.side)
         t0 = time.perf_counter()
         if self.pool is not None:
             self.pool.map(_oracle_one, arrs, chunksize=1)
@@ -478,7 +487,7 @@ def main():
         if rank != 0:
             return 0
         data = make_input(args.workload, args.size)
-        runner = OracleRunner(args.workload)
+        runner = OracleRunner(args.workload, side=volume_sample_side(args.warmup + args.steps))
         vals = []
         try:
             for i in range(args.warmup + args.steps):
