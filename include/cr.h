@@ -357,7 +357,8 @@ int cr_tune_get(int knob, int *value);
  *   barrier_polls          polls of one grid-barrier wait of the union-find
  *                          kernels (0 = the default, 2^24);
  *   reduce_iters           iterations one column of the 3D middle-dimension
- *                          reduction may take (0 = the default, 2^24);
+ *                          reduction may take in one pass (0 = the default,
+ *                          2^24);
  *   barrier_unsatisfiable  1: the grid barriers wait for one block more than
  *                          the grid has (a flag that nothing sets), so every
  *                          barrier wait runs out after barrier_polls polls;
