@@ -205,18 +205,31 @@ __device__ bool merge_mid(const RedParams &R, Work &W, WarpSmem &sm, RedStats &s
     return true;
 }
 
-// ascending sort of a[0..n) in shared memory by the warp; n a power of two, 2 <= n <= 1024
+// ascending sort of a[0..n) in shared memory by the warp; n a power of two, 2 <= n <= 1024.
+// The compare-exchanges of one stage touch disjoint pairs, so a lane loads
+// four pairs before it writes any: the sort runs on a lone warp at the end of
+// the reduction, where dependent shared-memory round trips set its time.
 __device__ void warp_bitonic(uint64_t *a, int n) {
     const int lane = threadIdx.x & 31;
+    const int half = n >> 1;
     for (int k = 2; k <= n; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = lane; t < (n >> 1); t += 32) {
-                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));  // t with a zero bit inserted at j
-                const int l = i | j;
-                const uint64_t x = a[i], y = a[l];
-                if ((x > y) == ((i & k) == 0)) {
-                    a[i] = y;
-                    a[l] = x;
+            for (int t0 = lane; t0 < half; t0 += 4 * 32) {
+                int i[4];
+                uint64_t x[4], y[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int t = t0 + 32 * u;
+                    i[u] = ((t & ~(j - 1)) << 1) | (t & (j - 1));  // t with a zero bit inserted at j
+                    x[u] = t < half ? a[i[u]] : 0ull;
+                    y[u] = t < half ? a[i[u] | j] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (t0 + 32 * u < half && (x[u] > y[u]) == ((i[u] & k) == 0)) {
+                        a[i[u]] = y[u];
+                        a[i[u] | j] = x[u];
+                    }
                 }
             }
             __syncwarp();
@@ -237,6 +250,7 @@ __device__ int sort_inbox(WarpSmem &sm, int ni) {
     __syncwarp();
     warp_bitonic(sm.in, n2);
     unsigned keep = 0;  // bit t: entry t*32 + lane survives
+#pragma unroll 4
     for (int t = 0; t * 32 < n2; t++) {
         const int i = t * 32 + lane;
         const uint64_t v = sm.in[i];
@@ -247,14 +261,25 @@ __device__ int sort_inbox(WarpSmem &sm, int ni) {
         }
     }
     __syncwarp();
+    // compaction four chunks at a time: a chunk's survivors land no further
+    // than its own slots, so the chunks read ahead are not yet overwritten
     const unsigned lt = (1u << lane) - 1u;
     int n = 0;
-    for (int t = 0; t * 32 < n2; t++) {
-        const bool k = (keep >> t) & 1u;
-        const uint64_t v = sm.in[t * 32 + lane];
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, k);
-        if (k) sm.in[n + __popc(m & lt)] = v;
-        n += __popc(m);
+    for (int t0 = 0; t0 * 32 < n2; t0 += 4) {
+        uint64_t v[4];
+        unsigned m[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int t = t0 + u;
+            const bool in = t * 32 < n2;
+            v[u] = in ? sm.in[t * 32 + lane] : 0ull;
+            m[u] = __ballot_sync(0xFFFFFFFFu, in && ((keep >> t) & 1u));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if ((m[u] >> lane) & 1u) sm.in[n + __popc(m[u] & lt)] = v[u];
+            n += __popc(m[u]);
+        }
         __syncwarp();
     }
     return n;
@@ -352,6 +377,7 @@ __device__ bool front_refill(const RedParams &R, Work &W, WarpSmem &sm, RedStats
         uint64_t cut = nbr > 32 ? cb : ~0ull;
         if (nmr > 32 && cm < cut) cut = cm;
         int nic = 0;
+#pragma unroll 4
         for (int i0 = 0; i0 < W.ni; i0 += 32) {
             const int i = i0 + lane;
             nic += __popc(__ballot_sync(0xFFFFFFFFu, i < W.ni && sm.in[i] <= cut));
