@@ -121,6 +121,7 @@ __device__ int tiled_xor(const uint64_t *A, int na, const uint64_t *B, int nb, u
     uint64_t prev = 0;
     bool hasprev = false;
     while (i + j < na + nb) {
+#pragma unroll
         for (int k = lane; k <= TT; k += 32) {
             ta[k] = i + k < na ? (AG ? ld_cg(A + i + k) : A[i + k]) : ~0ull;
             tb[k] = j + k < nb ? (BG ? ld_cg(B + j + k) : B[j + k]) : ~0ull;
@@ -129,17 +130,25 @@ __device__ int tiled_xor(const uint64_t *A, int na, const uint64_t *B, int nb, u
         const int left = na + nb - i - j;
         const int T = min(TT, left);
         const int wa = min(TT + 1, na - i), wb = min(TT + 1, nb - j);
-        // A entries among the first d merged positions (ties: A first)
-        auto split = [&](int d) {
-            int lo = max(0, d - wb), hi = min(d, wa);
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (ta[mid] <= tb[d - 1 - mid]) lo = mid + 1; else hi = mid;
-            }
-            return lo;
-        };
         const int s = min(lane * PER, T), e = min(s + PER, T);
-        int ia = split(s), ib = s - ia;
+        // A entries among the first d merged positions (ties: A first), for d =
+        // this lane's start s and the tile's end T: two binary searches run in step
+        int ia, ca;
+        {
+            int lo1 = max(0, s - wb), hi1 = min(s, wa), lo2 = max(0, T - wb), hi2 = min(T, wa);
+            while (lo1 < hi1 || lo2 < hi2) {
+                const int m1 = (lo1 + hi1) >> 1, m2 = (lo2 + hi2) >> 1;
+                const bool g1 = lo1 < hi1, g2 = lo2 < hi2;
+                const uint64_t a1 = g1 ? ta[m1] : 0ull, b1 = g1 ? tb[s - 1 - m1] : 0ull;
+                const uint64_t a2 = g2 ? ta[m2] : 0ull, b2 = g2 ? tb[T - 1 - m2] : 0ull;
+                if (g1) { if (a1 <= b1) lo1 = m1 + 1; else hi1 = m1; }
+                if (g2) { if (a2 <= b2) lo2 = m2 + 1; else hi2 = m2; }
+            }
+            ia = lo1;
+            ca = lo2;
+        }
+        int ib = s - ia;
+        const uint64_t la = ca > 0 ? ta[ca - 1] : 0ull, lb = T - ca > 0 ? tb[T - ca - 1] : 0ull;
         uint64_t pv = prev;
         bool hp = hasprev;
         if (s > 0) {
@@ -175,8 +184,6 @@ __device__ int tiled_xor(const uint64_t *A, int na, const uint64_t *B, int nb, u
         for (int t = 0; t < PER; t++)
             if ((kf >> t) & 1u) out[no + base + __popc(kf & ((1u << t) - 1u))] = kv[t];
         no += total;
-        const int ca = split(T);
-        const uint64_t la = ca > 0 ? ta[ca - 1] : 0ull, lb = T - ca > 0 ? tb[T - ca - 1] : 0ull;
         prev = la > lb ? la : lb;
         hasprev = true;
         i += ca;
@@ -392,17 +399,28 @@ __device__ bool front_refill(const RedParams &R, Work &W, WarpSmem &sm, RedStats
         sm.cand[64 + lane] = ~0ull;
         sm.cand[96 + lane] = ~0ull;
         __syncwarp();
+        // four chunks read before any is written: kept entries land no further
+        // than their own chunk's slots, so the chunks read ahead are intact
         int nk = 0, nt = 0;
-        for (int i0 = 0; i0 < W.ni; i0 += 32) {
-            const int i = i0 + lane;
-            const bool valid = i < W.ni;
-            const uint64_t x = valid ? sm.in[i] : ~0ull;
-            const bool take = valid && x <= cut;
-            const unsigned mt = __ballot_sync(0xFFFFFFFFu, take), mk = __ballot_sync(0xFFFFFFFFu, valid && !take);
-            if (take) sm.cand[64 + nk + __popc(mt & lt)] = x;
-            if (valid && !take) sm.in[nt + __popc(mk & lt)] = x;  // never past this chunk's own slots
-            nk += __popc(mt);
-            nt += __popc(mk);
+        for (int i0 = 0; i0 < W.ni; i0 += 4 * 32) {
+            uint64_t x[4];
+            unsigned mt[4], mk[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int i = i0 + 32 * u + lane;
+                const bool valid = i < W.ni;
+                x[u] = valid ? sm.in[i] : ~0ull;
+                const bool take = valid && x[u] <= cut;
+                mt[u] = __ballot_sync(0xFFFFFFFFu, take);
+                mk[u] = __ballot_sync(0xFFFFFFFFu, valid && !take);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if ((mt[u] >> lane) & 1u) sm.cand[64 + nk + __popc(mt[u] & lt)] = x[u];
+                if ((mk[u] >> lane) & 1u) sm.in[nt + __popc(mk[u] & lt)] = x[u];
+                nk += __popc(mt[u]);
+                nt += __popc(mk[u]);
+            }
             __syncwarp();
         }
         W.ni = nt;
@@ -579,6 +597,7 @@ __device__ bool toggle_list(const RedParams &R, Work &W, WarpSmem &sm, const uin
     if (nlo > 0) {
         const uint64_t *D = X;
         if (XG) {
+#pragma unroll 8
             for (int k = lane; k < nlo; k += 32) sm.c[k] = ld_cg(X + k);
             __syncwarp();
             D = sm.c;
