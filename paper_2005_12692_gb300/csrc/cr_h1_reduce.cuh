@@ -91,11 +91,11 @@ __device__ int insert_merge(const uint64_t *A, int na, const uint64_t *D, int nD
             int i = c0 + lane + 32 * t;
             v[t] = i < na ? ld_a<AG>(A, i) : 0;
         }
+        int kk = klo;  // #{k : q[k] <= i}, carried forward: i grows with t
 #pragma unroll
         for (int t = 0; t < 8; t++) {
             int i = c0 + lane + 32 * t;
             if (i >= na) break;
-            int kk = klo;  // #{k : q[k] <= i}
             while (kk < khi && sm.q[kk] <= i) kk++;
             bool cancel = kk > 0 && sm.q[kk - 1] == i && (sm.pc[kk] - sm.pc[kk - 1]);
             if (!cancel) out[i + kk - 2 * sm.pc[kk]] = v[t];
@@ -659,17 +659,21 @@ __device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, con
     L.k = 0;
     if (cand == ~0ull) return;
     const uint32_t fl = key_L(cand);
-    int fm, c[3];
-    decode_L(S, fl, fm, c);
     const int64_t bit = S.loff + fl;
+    // the face's type and anchor voxel need no division (L = type * P + voxel),
+    // so the first loads go out before the anchor's coordinates are decoded
+    const uint32_t P3 = (uint32_t)S.nx * (uint32_t)S.ny * (uint32_t)S.nz;
+    const int fm = (fl >= P3) + (fl >= 2u * P3);
     // the two edges that could pair this face as apparent (the code bytes of
     // their voxels): {x,z} (type 1) the x-edges at c (+z) and c+z (-z); {x,y}
     // (type 0) the x-edges at c (+y) and c+y (-y); {y,z} (type 2) the y-edges
     // at c (+z) and c+z (-z)
-    const int64_t v0 = S.voff + ((int64_t)c[2] * S.ny + c[1]) * S.nx + c[0];
+    const int64_t v0 = S.voff + (int64_t)(fl - (uint32_t)fm * P3);
     const int64_t v1 = v0 + (fm == 0 ? (int64_t)S.nx : (int64_t)S.nx * S.ny);
     const uint32_t k0 = R.I.code[v0], k1 = R.I.code[v1];
     const unsigned long long pe = __ldcg(&R.P[bit]);
+    int fm2, c[3];
+    decode_L(S, fl, fm2, c);  // fm2 == fm
     int ea = -1, ec[3] = {c[0], c[1], c[2]};
     if (fm == 2) {
         if (((k0 >> 3) & 3u) == 1u) ea = 1;
@@ -935,6 +939,7 @@ __global__ void __launch_bounds__(RED_WARPS * 32, RED_BLOCKS) k_h1_reduce(RedPar
             bool ok2;
             if (len - 1 <= DMAX) {
                 if (lane >= 1 && lane <= len) sm.c[lane - 1] = w;
+#pragma unroll 8
                 for (int q2 = 31 + lane; q2 < len; q2 += 32) sm.c[q2] = ld_cg(V + 1 + q2);
                 __syncwarp();
                 if (sm.c[0] != p) { st.retry++; continue; }
