@@ -303,7 +303,8 @@ int64_t cr_launch_count(void);
 /* Counters of the last 3D reduction on this process (out[0..n), n <= 25):
  * residual columns, loop iterations, apparent-column additions, column
  * additions, merged entries, pivot takeovers, lost races and stale reads,
- * long-column buffer growths, most iterations spent on one column; then
+ * long-column buffer growths, most iterations spent on one column in one
+ * pass (the counts add up both passes of the reduction); then
  * (builds with CR_H1_TIMING only, zero otherwise) cycles spent in the
  * iterations of long column runs per phase: front refills, lookups, apparent
  * additions, cached additions, staged additions, inbox flushes, then lookahead
