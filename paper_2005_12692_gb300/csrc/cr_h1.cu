@@ -315,12 +315,15 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_h1_scan_tma(const __grid_const
     const int bx = tx + 4, by = ty + 1;
     const int zend = min(TILE_Z, nz - z0);
     const bool keep_zero = (flags & CR_KEEP_ZERO) != 0;
-    const bool hx = x + 1 < nx, hy = y + 1 < ny, my = y > 0;
+    const bool hx = x + 1 < nx, hy = y + 1 < ny;
     uint8_t *code = I.code + S.voff + (uint32_t)y * nx + (uint32_t)x;
     // Values of this thread's column roll through registers: f(x,y,z), f(x+1,y,z),
     // f(x,y+1,z) and the x- and y-edge values of planes z-1, z (and z+1 once read).
-    // Out-of-image entries of the box are zero and never decide anything: each
-    // use is guarded by the existence of the cell it belongs to.
+    // Out-of-image entries of the box are NaN (the tensor map's fill), and so is
+    // the value of an edge outside the image (fmaxf of two NaNs): every
+    // comparison with it is false, so a face beyond the image never qualifies
+    // and needs no test of its own.  The edge itself is tested (hx, hy, hz):
+    // an edge with one vertex outside would take the other vertex's value.
     float fa = box[1][by][bx], fb = box[1][by][bx + 1], fc = box[1][by + 1][bx];
     float exc = fmaxf(fa, fb), eyc = fmaxf(fa, fc);
     float exp_ = fmaxf(box[0][by][bx], box[0][by][bx + 1]), eyp = fmaxf(box[0][by][bx], box[0][by + 1][bx]);
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_h1_scan_tma(const __grid_const
         const int z = z0 + zz, bz = zz + 1;
         const uint32_t rowL = (uint32_t)z * plane + (uint32_t)y * nx + (uint32_t)x0;  // L of (x0, y, z)
         const uint32_t lv = rowL + (uint32_t)tx;
-        const bool hz = z + 1 < nz, mz = z > 0;
+        const bool hz = z + 1 < nz;
         const float fa1 = box[bz + 1][by][bx], fb1 = box[bz + 1][by][bx + 1], fc1 = box[bz + 1][by + 1][bx];
         const float exn = fmaxf(fa1, fb1), eyn = fmaxf(fa1, fc1);
         const uint8_t dv = dds[zz][ty][tx];
@@ -357,10 +360,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_h1_scan_tma(const __grid_const
             const float cmy = fmaxf(box[bz][by - 1][bx], box[bz][by - 1][bx + 1]);
             uint32_t side = 0;  // 1 +z, 2 -z, 3 +y, 4 -y; the first qualifying wins
             float fp = 0.f;
-            if (my && cmy <= fs) { side = 4; fp = cmy; }
-            if (hy && cpy <= fs) { side = 3; fp = cpy; }
-            if (mz && exp_ <= fs) { side = 2; fp = exp_; }
-            if (hz && exn <= fs) { side = 1; fp = exn; }
+            if (cmy <= fs) { side = 4; fp = cmy; }
+            if (cpy <= fs) { side = 3; fp = cpy; }
+            if (exp_ <= fs) { side = 2; fp = exp_; }
+            if (exn <= fs) { side = 1; fp = exn; }
             if (side != 0 && ((side & 1) || fp < fs)) {
                 cd = side;
                 if (keep_zero) {
@@ -377,8 +380,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_h1_scan_tma(const __grid_const
         // -- y-edge (v, v+y): only the {y,z} faces (+z, -z, type 2) can make it apparent
         if (hy) {
             const float fs = eyc;
-            const bool pz = hz && eyn <= fs;
-            const bool qz = !pz && mz && eyp < fs;
+            const bool pz = eyn <= fs;
+            const bool qz = !pz && eyp < fs;
             if (pz || qz) {
                 cd |= (pz ? 1u : 2u) << 3;
                 if (keep_zero) {
@@ -765,7 +768,7 @@ int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg
     prof_begin(st, STAGE_H1_SCAN);
     CR_NOTE_LAUNCH();
     CUtensorMap tmap, tmap_dd;
-    if (nseg == 1 && hseg && hseg->edim == 3 && make_image_map(&tmap, img, *hseg)) {
+    if (nseg == 1 && hseg && hseg->edim == 3 && make_image_map(&tmap, img, *hseg, TMA_BX, TMA_BY, TMA_BZ, true)) {
         static int attr_dev = -1;
         int dev = 0;
         cudaGetDevice(&dev);

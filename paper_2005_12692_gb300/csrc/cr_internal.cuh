@@ -333,9 +333,10 @@ struct H1Bufs {
     unsigned long long *cnt;  // [0] columns, [1] arena top, [2] work counter, [3] pool top
 };
 int h1_stats(int64_t *out, int n);
-// tensor map over one image as an (nx, ny, nz) float32 tensor with the tile box; false if TMA cannot serve it
+// tensor map over one image as an (nx, ny, nz) float32 tensor with the tile box; false if TMA cannot serve it;
+// out-of-image elements of a box read as 0, or as NaN with nan_fill
 bool make_image_map(CUtensorMap *m, const float *img, const Seg &S, int bx = TMA_BX, int by = TMA_BY,
-                    int bz = TMA_BZ);
+                    int bz = TMA_BZ, bool nan_fill = false);
 bool make_u8_map(CUtensorMap *m, const uint8_t *p, const Seg &S, int bx, int by, int bz);
 int run_h1(const float *img, const uint8_t *dd, const uint32_t *extra, const Seg *segs, const Seg *hseg, int nseg,
            int64_t vtot, int64_t ntiles, H1Bufs &B, const PairBuf &pb, uint32_t flags, int *status,

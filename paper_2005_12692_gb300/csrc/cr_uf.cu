@@ -322,7 +322,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // a tensor map over one image as an (nx, ny, nz) float32 tensor; false if TMA cannot serve it
-bool make_image_map(CUtensorMap *m, const float *img, const Seg &S, int bx, int by, int bz) {
+bool make_image_map(CUtensorMap *m, const float *img, const Seg &S, int bx, int by, int bz, bool nan_fill) {
     if (((uintptr_t)img & 15) || (S.nx % 4) != 0) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
@@ -332,7 +332,7 @@ bool make_image_map(CUtensorMap *m, const float *img, const Seg &S, int bx, int 
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)img, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     nan_fill ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
