@@ -887,7 +887,10 @@ __global__ void __launch_bounds__(RED_WARPS * 32, RED_BLOCKS) k_h1_reduce(RedPar
                 continue;
             }
             TMARK(t9);
-            const unsigned long long pe = hkind == 2 ? hver : __ldcg(&R.P[gidx]);
+            // a pivot the lookahead found free is claimed without reading the
+            // table again: if it has been taken since, the claim fails and the
+            // step is retried with a fresh lookup
+            const unsigned long long pe = hkind == 2 ? hver : (hit && hkind == 0 ? PIV_FREE : __ldcg(&R.P[gidx]));
             const int o = hkind == 2 ? hown : piv_owner(pe);
 #ifdef CR_H1_TIMING
             if (hkind != 2) (void)__shfl_sync(0xFFFFFFFFu, (int)pe, 0);  // make the read complete here
