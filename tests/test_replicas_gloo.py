@@ -71,3 +71,23 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
     with redirect_stdout(out):
         assert b.main() == 0
     assert out.getvalue() == ""
+
+
+def test_oracle_sample_sizes():
+    """The reference arm's volume crop shrinks with the number of timed calls
+    (about 150 s of oracle work in all), never above the single-run crop and
+    never below 32; batches and 2D images keep their samples."""
+    import numpy as np
+    b = _bench()
+    sides = [b.volume_sample_side(c) for c in (1, 3, 8, 13, 23, 53, 103, 10 ** 6)]
+    assert sides == sorted(sides, reverse=True)
+    assert sides[0] == b.VOLUME_SAMPLE and sides[-1] == 32
+    vol = np.zeros((64, 64, 64), np.float32)
+    arrs, units, desc = b.oracle_sample("grf512cube", vol, side=40)
+    assert arrs[0].shape == (40, 40, 40) and units == b.num_cells((40, 40, 40)) and "40^3" in desc
+    img = np.zeros((16, 16), np.float32)
+    arrs, units, _ = b.oracle_sample("grf1024", img)
+    assert arrs[0] is img and units == b.num_cells(img.shape)
+    imgs = np.zeros((8, 4, 4), np.float32)
+    arrs, units, _ = b.oracle_sample("batch4096", imgs, batch_images=5)
+    assert len(arrs) == 5 and units == 5
