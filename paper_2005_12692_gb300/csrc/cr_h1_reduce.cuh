@@ -646,34 +646,29 @@ __device__ bool toggle_list(const RedParams &R, Work &W, WarpSmem &sm, const uin
     return true;
 }
 
-// Fill the lookahead cache for the front's next 32 entries in two round
-// trips: the code bytes of the two edges that could pair the face as
-// apparent and its pivot-table entry, then either the apparent edge's vertex
-// values (its column is generated from them) or the head of the owner's
-// version.
-__device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, const WarpSmem &sm, Look &L) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t cand = W.fh + lane < W.fn ? sm.f[W.fb][W.fh + lane] : ~0ull;
-    L.key = cand;
-    L.kind = 0;
-    L.k = 0;
-    if (cand == ~0ull) return;
-    const uint32_t fl = key_L(cand);
-    const int64_t bit = S.loff + fl;
-    // the face's type and anchor voxel need no division (L = type * P + voxel),
-    // so the first loads go out before the anchor's coordinates are decoded
-    const uint32_t P3 = (uint32_t)S.nx * (uint32_t)S.ny * (uint32_t)S.nz;
-    const int fm = (fl >= P3) + (fl >= 2u * P3);
-    // the two edges that could pair this face as apparent (the code bytes of
-    // their voxels): {x,z} (type 1) the x-edges at c (+z) and c+z (-z); {x,y}
-    // (type 0) the x-edges at c (+y) and c+y (-y); {y,z} (type 2) the y-edges
-    // at c (+z) and c+z (-z)
-    const int64_t v0 = S.voff + (int64_t)(fl - (uint32_t)fm * P3);
-    const int64_t v1 = v0 + (fm == 0 ? (int64_t)S.nx : (int64_t)S.nx * S.ny);
-    const uint32_t k0 = R.I.code[v0], k1 = R.I.code[v1];
-    const unsigned long long pe = __ldcg(&R.P[bit]);
-    int fm2, c[3];
-    decode_L(S, fl, fm2, c);  // fm2 == fm
+// Place of cofacet g (0..3) of the edge along axis a at c, in the order the
+// cofacets are formed above (+b1, -b1, +b2, -b2 faces): its type t, its anchor
+// ac and its L; false if it lies outside the image.  No values are needed.
+__device__ __forceinline__ bool edge_cofacet_place(const Seg &S, int a, const int *c, int g, int &t, int *ac,
+                                                   uint32_t &L) {
+    const int b = g < 2 ? (a == 0 ? 1 : 0) : (a == 2 ? 1 : 2);
+    const bool minus = (g & 1) != 0;
+    const int cb = b == 0 ? c[0] : (b == 1 ? c[1] : c[2]);
+    const int nb = b == 0 ? S.nx : (b == 1 ? S.ny : S.nz);
+    ac[0] = c[0] - (minus && b == 0);
+    ac[1] = c[1] - (minus && b == 1);
+    ac[2] = c[2] - (minus && b == 2);
+    t = min(a, b) + max(a, b) - 1;
+    L = cube_L(S, t, ac[0], ac[1], ac[2]);
+    return minus ? cb >= 1 : cb + 1 < nb;
+}
+
+// The lookahead entry of face `cand` (type fm, anchor c) from the results of
+// its first round trip: the code bytes k0, k1 of the two edges that could pair
+// it as apparent and its pivot-table word pe.  L.key, L.kind = 0 and L.k = 0
+// are set by the caller.
+__device__ void look_finish(const RedParams &R, const Seg &S, uint64_t cand, int fm, const int *c, uint32_t k0,
+                            uint32_t k1, unsigned long long pe, Look &L) {
     int ea = -1, ec[3] = {c[0], c[1], c[2]};
     if (fm == 2) {
         if (((k0 >> 3) & 3u) == 1u) ea = 1;
@@ -718,6 +713,38 @@ __device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, con
         L.c3 = vn > 3 ? a3 : ~0ull;
         L.k = (int)vn;
     }
+}
+
+
+// Fill the lookahead cache for the front's next 32 entries in two round
+// trips: the code bytes of the two edges that could pair the face as
+// apparent and its pivot-table entry, then either the apparent edge's vertex
+// values (its column is generated from them) or the head of the owner's
+// version.
+__device__ void look_refill(const RedParams &R, const Seg &S, const Work &W, const WarpSmem &sm, Look &L) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t cand = W.fh + lane < W.fn ? sm.f[W.fb][W.fh + lane] : ~0ull;
+    L.key = cand;
+    L.kind = 0;
+    L.k = 0;
+    if (cand == ~0ull) return;
+    const uint32_t fl = key_L(cand);
+    const int64_t bit = S.loff + fl;
+    // the face's type and anchor voxel need no division (L = type * P + voxel),
+    // so the first loads go out before the anchor's coordinates are decoded
+    const uint32_t P3 = (uint32_t)S.nx * (uint32_t)S.ny * (uint32_t)S.nz;
+    const int fm = (fl >= P3) + (fl >= 2u * P3);
+    // the two edges that could pair this face as apparent (the code bytes of
+    // their voxels): {x,z} (type 1) the x-edges at c (+z) and c+z (-z); {x,y}
+    // (type 0) the x-edges at c (+y) and c+y (-y); {y,z} (type 2) the y-edges
+    // at c (+z) and c+z (-z)
+    const int64_t v0 = S.voff + (int64_t)(fl - (uint32_t)fm * P3);
+    const int64_t v1 = v0 + (fm == 0 ? (int64_t)S.nx : (int64_t)S.nx * S.ny);
+    const uint32_t k0 = R.I.code[v0], k1 = R.I.code[v1];
+    const unsigned long long pe = __ldcg(&R.P[bit]);
+    int fm2, c[3];
+    decode_L(S, fl, fm2, c);  // fm2 == fm
+    look_finish(R, S, cand, fm, c, k0, k1, pe, L);
 }
 
 // publish the working column as column j's current version; *voff is the
@@ -805,10 +832,47 @@ __global__ void __launch_bounds__(RED_WARPS * 32, RED_BLOCKS) k_h1_reduce(RedPar
             // the coboundary of edge j is the front; nothing lies beyond it
             int a, c[3];
             decode_L(S, key_L(jkey), a, c);
+            // lanes 0..3 read the code bytes and pivot-table word of one cofacet
+            // each, in the round trip that reads the vertex values: a cofacet's
+            // place needs no values
+            int gt = 0, gc[3] = {0, 0, 0};
+            uint32_t gL = 0, gk0 = 0, gk1 = 0;
+            unsigned long long gpe = PIV_FREE;
+            int gok = 0;
+            if (lane < 4) {
+                gok = edge_cofacet_place(S, a, c, lane, gt, gc, gL) ? 1 : 0;
+                if (gok) {
+                    const int64_t v0 = S.voff + ((int64_t)gc[2] * S.ny + gc[1]) * S.nx + gc[0];
+                    const int64_t v1 = v0 + (gt == 0 ? (int64_t)S.nx : (int64_t)S.nx * S.ny);
+                    gk0 = R.I.code[v0];
+                    gk1 = R.I.code[v1];
+                    gpe = __ldcg(&R.P[S.loff + gL]);
+                }
+            }
             uint64_t f0, f1, f2, f3;
             const int k = edge_cofacets_sorted(R.I, S, a, c, f0, f1, f2, f3);
-            if (lane < k) sm.f[0][lane] = lane == 0 ? f0 : (lane == 1 ? f1 : (lane == 2 ? f2 : f3));
+            const uint64_t fr = lane == 0 ? f0 : (lane == 1 ? f1 : (lane == 2 ? f2 : f3));
+            if (lane < k) sm.f[0][lane] = fr;
             W.fn = k;
+            // the lookahead of the front: lane r < k takes what was read for the
+            // cofacet that sorts r-th (faces have distinct L)
+            const uint32_t Lr = key_L(fr);
+            int src = 0;
+#pragma unroll
+            for (int g = 0; g < 4; g++) {
+                const uint32_t Lg = __shfl_sync(0xFFFFFFFFu, gL, g);
+                const int okg = __shfl_sync(0xFFFFFFFFu, gok, g);
+                if (okg && Lg == Lr) src = g;
+            }
+            const int rt = __shfl_sync(0xFFFFFFFFu, gt, src);
+            const int rc[3] = {__shfl_sync(0xFFFFFFFFu, gc[0], src), __shfl_sync(0xFFFFFFFFu, gc[1], src),
+                               __shfl_sync(0xFFFFFFFFu, gc[2], src)};
+            const uint32_t rk0 = __shfl_sync(0xFFFFFFFFu, gk0, src), rk1 = __shfl_sync(0xFFFFFFFFu, gk1, src);
+            const unsigned long long rpe = __shfl_sync(0xFFFFFFFFu, gpe, src);
+            look.key = lane < k ? fr : ~0ull;
+            look.kind = 0;
+            look.k = 0;
+            if (lane < k) look_finish(R, S, fr, rt, rc, rk0, rk1, rpe, look);
             __syncwarp();
         } else {
             // the version the earlier pass published becomes the working column
@@ -819,9 +883,9 @@ __global__ void __launch_bounds__(RED_WARPS * 32, RED_BLOCKS) k_h1_reduce(RedPar
                 flush_stats(R, st);
                 return;
             }
+            look.key = ~0ull;
+            look.kind = 0;
         }
-        look.key = ~0ull;
-        look.kind = 0;
         int64_t it = 0;
         bool keep = R.budget <= 0;  // no budget, or no room left to set the column aside
         for (;;) {
