@@ -91,3 +91,25 @@ def test_oracle_sample_sizes():
     imgs = np.zeros((8, 4, 4), np.float32)
     arrs, units, _ = b.oracle_sample("batch4096", imgs, batch_images=5)
     assert len(arrs) == 5 and units == 5
+
+
+def test_traffic_lines_follow_the_source(tmp_path, monkeypatch):
+    """bench.py quotes an ncu traffic figure only while the kernel's source file
+    is the one the capture was taken on (its SHA-256 in the summary line)."""
+    b = _bench()
+    sha = b.kernel_source_sha("h1_scan")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "dram_traffic_demo.md").write_text(
+        "traffic h1_scan 1234 bytes per launch, source sha256 %s\n"
+        "traffic h0_stencil 99 bytes per launch, source sha256 %s\n" % (sha, "0" * 64))
+    src = tmp_path / "paper_2005_12692_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for f in ("cr_h1.cu", "cr_uf.cu"):
+        (src / f).write_bytes(open(os.path.join(ROOT, "paper_2005_12692_gb300", "csrc", f), "rb").read())
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    assert b.measured_traffic("h1_scan", "demo") == (1234, "profiles/dram_traffic_demo.md")
+    val, why = b.measured_traffic("h0_stencil", "demo")
+    assert val is None and why.startswith("stale")
+    assert b.measured_traffic("dual_stencil", "demo") == (None, None)
+    assert b.measured_traffic("h1_scan", "missing") == (None, None)
